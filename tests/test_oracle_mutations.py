@@ -1,0 +1,82 @@
+"""Negative controls: plant one plausible mistake at a time in the oracle (on
+the CPU, through its mutation switch) and check that the pins catch it."""
+import math
+
+import numpy as np
+import pytest
+
+import ratmat as R
+from oracle import oracle as O
+from oracle import theta as TH
+
+WIDE = np.array([[3.0, 1.0, 0.5], [-1.0, 2.5, 0.25], [0.5, -0.75, 3.5]])
+
+
+def _taylor_pins() -> bool:
+    Xf = R.to_frac(WIDE)
+    for m in (8, 12, 18):
+        exact = R.to_float(R.taylor(Xf, m))
+        if np.abs(O.taylor_new(WIDE, m) - exact).max() / np.abs(exact).max() > 1e-12:
+            return False
+    for m in (4, 6, 9, 12, 16):
+        exact = R.to_float(R.taylor(Xf, m))
+        if np.abs(O.taylor_ps(WIDE, m) - exact).max() / np.abs(exact).max() > 1e-12:
+            return False
+    return True
+
+
+def _closed_form_pins() -> bool:
+    for scheme in ("new", "ps", "pade26"):
+        for t in (1.0, 10.0):
+            A = np.array([[0.0, -t], [t, 0.0]])
+            E, info = O.expm(A, scheme)
+            want = np.array([[math.cos(t), -math.sin(t)], [math.sin(t), math.cos(t)]])
+            if np.abs(E - want).max() > 1e-15 * 2 ** (info.s + 2):
+                return False
+    return True
+
+
+def _norm_and_selection_pins() -> bool:
+    if O.norm1(np.array([[1.0, -2.0], [3.0, 4.0]])) != 6.0:
+        return False
+    table = [(0.01, (8, 0)), (0.1, (12, 0)), (5.0, (18, 3)), (100.0, (18, 7))]
+    return all(O.select(n, "new") == w for n, w in table)
+
+
+def _coefficient_pins() -> bool:
+    c = O.coeffs(2).reshape(4, 4)
+    from test_oracle_scheme import _t12_poly  # noqa: E402
+    p, _, _ = _t12_poly(c.tolist())
+    return max(abs(float(p[k] * math.factorial(k)) - 1.0) for k in range(13)) < 1e-14
+
+
+def all_pins_pass() -> bool:
+    return (_taylor_pins() and _closed_form_pins() and _norm_and_selection_pins()
+            and _coefficient_pins())
+
+
+MUTATIONS = {
+    1: "T12 a_{0,4} dropped (looks like noise, is not)",
+    2: "T18 b_{6,3} sign flipped",
+    3: "T8 x5 and x6 swapped",
+    4: "T18 A9 = B1 B5 without + B4",
+    5: "product computes A B^T (transposed operand)",
+    6: "Paterson-Stockmeyer top coefficient dropped",
+    7: "Pade numerator and denominator swapped",
+    8: "one squaring too few",
+    9: "infinity-norm instead of 1-norm",
+}
+
+
+def test_clean_oracle_passes_pins():
+    O.set_mutation(0)
+    assert all_pins_pass()
+
+
+@pytest.mark.parametrize("code", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(code):
+    try:
+        O.set_mutation(code)
+        assert not all_pins_pass(), MUTATIONS[code]
+    finally:
+        O.set_mutation(0)
