@@ -1,0 +1,123 @@
+/*
+ * bbcexpm.h -- C ABI of libbbcexpm.so, a GB300 (sm_103a) matrix exponential.
+ *
+ * Method: Bader, Blanes and Casas, "An improved algorithm to compute the
+ * exponential of a matrix" (arXiv:1710.10989). exp(A) = (T_m(A/2^s))^(2^s)
+ * (Section 1, eq. eses), with the Taylor polynomial T_m evaluated by the
+ * reduced-product scheme of Section 3 (T8 in 3 products, eq. Algorithm83eA;
+ * T12 in 4, eq. poly12; T18 in 5, eq. poly.18; T1, T2, T4 in 0, 1, 2) and
+ * (m, s) chosen from ||A||_1 and the backward-error thresholds theta_m(u)
+ * (eq. theta, Table 2) to minimise the number of products (Table 3).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are square, N x N, row-major, contiguous, IEEE binary64
+ *    (unless a dtype argument says otherwise).
+ *  - "d" pointers are device pointers on the handle's device; "h" pointers
+ *    are host pointers. The caller owns every buffer it passes in.
+ *  - Outputs may not alias inputs (BBC_INVALID_ARG, output untouched).
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default
+ *    stream). Calls that return a host-side result (bbc_info, a norm) wait
+ *    for the stream once at the point that result is needed.
+ *  - Every function returns a bbc_status; nothing throws across the ABI.
+ *  - The library allocates device memory only in bbc_create, and in a call
+ *    whose N needs a larger workspace than the handle holds (it grows then).
+ */
+#ifndef BBCEXPM_H
+#define BBCEXPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BBC_OK = 0,
+  BBC_INVALID_ARG = 1,      /* null pointer, N <= 0, tol out of range, aliasing, bad flags */
+  BBC_NONFINITE_INPUT = 2,  /* A holds a NaN or an infinity (||A||_1 not finite) */
+  BBC_OVERFLOW = 3,         /* the result holds a non-finite value */
+  BBC_CUDA_ERROR = 4,       /* a CUDA call failed; bbc_last_error() has the text */
+  BBC_TIMEOUT = 5,          /* a bounded device-side wait gave up */
+  BBC_UNSUPPORTED = 6       /* valid request this build or device cannot serve */
+} bbc_status;
+
+/* flags: scheme in bits 0-3, product precision in bits 4-11. */
+#define BBC_SCHEME_NEW 0x0     /* reduced-product Taylor, degrees {1,2,4,8,12,18} (Section 3) */
+#define BBC_SCHEME_PS 0x1      /* Paterson-Stockmeyer Taylor, degrees {1,2,4,6,9,12,16} (eq. poli9) */
+#define BBC_SCHEME_MASK 0xF
+#define BBC_PREC_FP64 0x00     /* every product on the FP64 pipe (DFMA) */
+#define BBC_PREC_OZAKI 0x10    /* products as exact BF16 slice products on tcgen05 tensor cores,
+                                  accumulated exactly; bits 8-11 = slice count k (0 -> 7) */
+#define BBC_PREC_MASK 0xF0
+#define BBC_OZAKI_SLICES(k) (((k) & 0xF) << 8)
+
+typedef struct bbc_handle_s* bbc_handle;
+
+typedef struct {
+  int m;          /* Taylor degree used */
+  int s;          /* squarings used */
+  int products;   /* dense N x N products performed */
+  int selector;   /* 0 = theta rule, 1 = caller-fixed (m, s) */
+  double norm1;   /* ||A||_1 as computed on the device */
+  int status;     /* bbc_status of this evaluation */
+} bbc_info;
+
+/* Create a handle bound to CUDA device `device`; allocates its device state.
+ * Returns BBC_CUDA_ERROR when the device cannot be used. */
+int bbc_create(bbc_handle* h, int device);
+
+/* Release a handle and all device memory it owns (NULL is accepted). */
+int bbc_destroy(bbc_handle h);
+
+/* Device bytes the handle needs to serve an N x N call with `flags`
+ * (dtype is reserved: pass 0 for binary64). */
+int bbc_workspace_size(bbc_handle h, int64_t N, int dtype, int flags, size_t* bytes);
+
+/* theta_m(u) for the Taylor polynomial T_m (eq. theta: the root of
+ * f(theta)/theta = u, f the 150-term majorant of log(e^-x T_m(x))).
+ * Host-only; m in 1..30, u in [2^-60, 2^-5]. */
+int bbc_theta(int m, double u, double* theta);
+
+/* (m, s) selection (Section 4, Table 2, Table 3): minimise products(m) + s
+ * subject to norm1 / 2^s <= theta_m(u), ties to the smaller s. Host-only.
+ * `scheme` is BBC_SCHEME_NEW or BBC_SCHEME_PS. */
+int bbc_select(double norm1, double u, int scheme, int* m, int* s);
+
+/* ||A||_1 = max_j sum_i |a_ij| on the device. Writes the result to host
+ * memory *hNorm (waits for the stream). */
+int bbc_norm1(bbc_handle h, const double* dA, int64_t N, void* stream, double* hNorm);
+
+/* dC = dP * dQ (one dense product) with the precision in `flags`. */
+int bbc_gemm(bbc_handle h, const double* dP, const double* dQ, int64_t N, double* dC,
+             int flags, void* stream);
+
+/* dT = T_m(2^-s dA) by the scheme in `flags` (no squaring). m must be a
+ * degree of that scheme. `products` (may be NULL) receives the count. */
+int bbc_taylor(bbc_handle h, const double* dA, int64_t N, int m, int s, double* dT, int flags,
+               void* stream, int* products);
+
+/* dOut = exp(dA). tol is the backward-error target u (eq. theta);
+ * tol <= 0 selects u = 2^-53. info (may be NULL) receives the outcome. */
+int bbc_expm(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol, int flags,
+             void* stream, bbc_info* info);
+
+/* As bbc_expm with (m, s) fixed by the caller instead of selected. */
+int bbc_expm_fixed(bbc_handle h, const double* dA, int64_t N, double* dOut, int m, int s,
+                   int flags, void* stream, bbc_info* info);
+
+/* dOut = exp(A) for HOST buffers hA, hOut (pinned memory recommended): the
+ * input is copied to the device on `stream`, evaluated as by bbc_expm, and
+ * the result copied back; returns after the result is in hOut. The device
+ * copies live in the handle's workspace. */
+int bbc_expm_host(bbc_handle h, const double* hA, int64_t N, double* hOut, double tol, int flags,
+                  void* stream, bbc_info* info);
+
+/* Text of the last error on this thread ("" if none). */
+const char* bbc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BBCEXPM_H */

@@ -1,0 +1,184 @@
+"""Python binding of libbbcexpm.so (include/bbcexpm.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; this module
+converts torch CUDA tensors to device pointers and back. There is no CPU or
+PyTorch fallback: importing fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libbbcexpm.so")
+
+OK, INVALID_ARG, NONFINITE_INPUT, OVERFLOW, CUDA_ERROR, TIMEOUT, UNSUPPORTED = range(7)
+SCHEME_NEW, SCHEME_PS = 0x0, 0x1
+PREC_FP64, PREC_OZAKI = 0x00, 0x10
+U_DOUBLE = 2.0 ** -53
+U_SINGLE = 2.0 ** -24
+
+
+def ozaki_slices(k: int) -> int:
+    return (k & 0xF) << 8
+
+
+class BBCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"bbc status {code}: {msg}")
+        self.code = code
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("s", ctypes.c_int), ("products", ctypes.c_int),
+                ("selector", ctypes.c_int), ("norm1", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1710_10989_gb300.build.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+_SIGS = {
+    "bbc_create": [ctypes.POINTER(_vp), _int],
+    "bbc_destroy": [_vp],
+    "bbc_workspace_size": [_vp, _i64, _int, _int, ctypes.POINTER(ctypes.c_size_t)],
+    "bbc_theta": [_int, _dbl, _dp],
+    "bbc_select": [_dbl, _dbl, _int, _ip, _ip],
+    "bbc_norm1": [_vp, _vp, _i64, _vp, _dp],
+    "bbc_gemm": [_vp, _vp, _vp, _i64, _vp, _int, _vp],
+    "bbc_taylor": [_vp, _vp, _i64, _int, _int, _vp, _int, _vp, _ip],
+    "bbc_expm": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
+    "bbc_expm_fixed": [_vp, _vp, _i64, _vp, _int, _int, _int, _vp, ctypes.POINTER(Info)],
+    "bbc_expm_host": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _int
+_lib.bbc_last_error.argtypes = []
+_lib.bbc_last_error.restype = ctypes.c_char_p
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS) + ["bbc_last_error"]
+
+
+def _check(rc: int) -> None:
+    if rc != OK:
+        raise BBCError(rc, _lib.bbc_last_error().decode())
+
+
+def theta(m: int, u: float = U_DOUBLE) -> float:
+    out = ctypes.c_double()
+    _check(_lib.bbc_theta(m, u, ctypes.byref(out)))
+    return out.value
+
+
+def select(norm1: float, u: float = U_DOUBLE, scheme: int = SCHEME_NEW) -> tuple[int, int]:
+    m, s = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.bbc_select(norm1, u, scheme, ctypes.byref(m), ctypes.byref(s)))
+    return m.value, s.value
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _mat(t, name: str):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.dim() == 2 and t.shape[0] == t.shape[1]
+            and t.is_contiguous()):
+        raise ValueError(f"{name}: need a contiguous square float64 CUDA tensor")
+    return t.data_ptr(), t.shape[0]
+
+
+@dataclasses.dataclass
+class Handle:
+    device: int = 0
+
+    def __post_init__(self):
+        self._h = _vp()
+        _check(_lib.bbc_create(ctypes.byref(self._h), self.device))
+
+    def close(self) -> None:
+        if self._h:
+            _lib.bbc_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_size(self, n: int, flags: int = 0) -> int:
+        b = ctypes.c_size_t()
+        _check(_lib.bbc_workspace_size(self._h, n, 0, flags, ctypes.byref(b)))
+        return b.value
+
+    def norm1(self, A, stream=None) -> float:
+        pa, n = _mat(A, "A")
+        out = ctypes.c_double()
+        _check(_lib.bbc_norm1(self._h, pa, n, _stream(stream), ctypes.byref(out)))
+        return out.value
+
+    def gemm(self, P, Q, C, flags: int = PREC_FP64, stream=None) -> None:
+        pp, n = _mat(P, "P")
+        pq, _ = _mat(Q, "Q")
+        pc, _ = _mat(C, "C")
+        _check(_lib.bbc_gemm(self._h, pp, pq, n, pc, flags, _stream(stream)))
+
+    def taylor(self, A, m: int, s: int, T, flags: int = 0, stream=None) -> int:
+        pa, n = _mat(A, "A")
+        pt, _ = _mat(T, "T")
+        prod = ctypes.c_int()
+        _check(_lib.bbc_taylor(self._h, pa, n, m, s, pt, flags, _stream(stream), ctypes.byref(prod)))
+        return prod.value
+
+    def expm(self, A, out, tol: float = 0.0, flags: int = 0, stream=None) -> Info:
+        pa, n = _mat(A, "A")
+        po, _ = _mat(out, "out")
+        info = Info()
+        _check(_lib.bbc_expm(self._h, pa, n, po, tol, flags, _stream(stream), ctypes.byref(info)))
+        return info
+
+    def expm_fixed(self, A, out, m: int, s: int, flags: int = 0, stream=None) -> Info:
+        pa, n = _mat(A, "A")
+        po, _ = _mat(out, "out")
+        info = Info()
+        _check(_lib.bbc_expm_fixed(self._h, pa, n, po, m, s, flags, _stream(stream), ctypes.byref(info)))
+        return info
+
+    def expm_host(self, A, out, tol: float = 0.0, flags: int = 0, stream=None) -> Info:
+        """A, out: host tensors/arrays (float64, C-contiguous, square)."""
+        pa, n = _host_ptr(A)
+        po, _ = _host_ptr(out)
+        info = Info()
+        _check(_lib.bbc_expm_host(self._h, pa, n, po, tol, flags, _stream(stream), ctypes.byref(info)))
+        return info
+
+
+def _host_ptr(x):
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous() or x.dim() != 2:
+                raise ValueError("need a contiguous float64 host tensor")
+            return x.data_ptr(), x.shape[0]
+    except ImportError:
+        pass
+    import numpy as np
+    if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous and x.ndim == 2):
+        raise ValueError("need a contiguous float64 host array")
+    return x.ctypes.data, x.shape[0]

@@ -1,0 +1,499 @@
+// api.cu -- the C ABI of libbbcexpm.so (include/bbcexpm.h): handle and
+// workspace, backward-error thresholds, (m, s) selection, program execution and
+// the squaring chain of scaling and squaring (eq. eses).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/bbcexpm.h"
+#include "internal.h"
+#include "schemes.h"
+
+using namespace bbc;
+
+struct bbc_handle_s {
+  int device = 0;
+  int64_t slots_n = 0;            // N the work slots are sized for
+  double* work = nullptr;         // NUM_WORK_SLOTS * N * N doubles
+  int64_t partial_len = 0;
+  double* partial = nullptr;      // norm slab sums
+  double* dnorm = nullptr;        // device ||A||_1
+  unsigned int* dflag = nullptr;  // device non-finite flag
+  void* hstage = nullptr;         // pinned host staging: [0] norm, [1] flag
+  void* ozaki = nullptr;          // Ozaki slice workspace
+  size_t ozaki_bytes = 0;
+  int64_t io_n = 0;               // N the host-call staging buffers are sized for
+  double* io = nullptr;           // 2 * N * N doubles: device copies of hA and hOut
+  std::mutex mu;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(BBC_CUDA_ERROR, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define BBC_CUDA(call)                                     \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// theta_m(u), eq. (theta): theta is the root of f(theta)/theta = u where
+// f(x) = sum |c_i| x^i majorises rho(x) = log(e^-x T_m(x)) = sum c_i x^i,
+// truncated to the 150 terms i = m+1 .. m+150.
+// Series of h(x) = e^-x T_m(x): h_0 = 1, h_j = 0 for 1 <= j <= m, and for j > m
+//   h_j = (-1)^(j+m) / (j * m! * (j-1-m)!)
+// (the partial alternating binomial sum identity); rho = log h by the usual
+// recurrence n rho_n = n h_n - sum_{k=1}^{n-1} k rho_k h_{n-k}.
+// ---------------------------------------------------------------------------
+double factorial(int n) {  // n <= 181 stays finite in binary64
+  double f = 1.0;
+  for (int k = 2; k <= n; ++k) f *= k;
+  return f;
+}
+
+double compute_theta(int m, double u) {
+  const int K = m + 151;
+  std::vector<double> h(K, 0.0), g(K, 0.0);
+  h[0] = 1.0;
+  const double mf = factorial(m);
+  for (int j = m + 1; j < K; ++j) {
+    const double mag = 1.0 / ((double)j * mf * factorial(j - 1 - m));
+    h[j] = ((j + m) % 2 == 0) ? mag : -mag;
+  }
+  for (int n = 1; n < K; ++n) {
+    double acc = n * h[n];
+    for (int k = m + 1; k < n; ++k) acc -= k * g[k] * h[n - k];
+    g[n] = acc / n;
+  }
+  auto f_over_x = [&](double x) {
+    double acc = 0.0, p = std::pow(x, m);  // x^(i-1) at i = m+1
+    for (int i = m + 1; i < K; ++i) {
+      acc += std::fabs(g[i]) * p;
+      p *= x;
+    }
+    return acc;
+  };
+  double lo = 0.0, hi = 1.0;
+  while (f_over_x(hi) < u) hi *= 2.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid == lo || mid == hi) break;
+    if (f_over_x(mid) < u) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+std::mutex g_theta_mu;
+std::map<std::pair<int, double>, double> g_theta_cache;
+
+double theta_cached(int m, double u) {
+  std::lock_guard<std::mutex> lk(g_theta_mu);
+  auto key = std::make_pair(m, u);
+  auto it = g_theta_cache.find(key);
+  if (it != g_theta_cache.end()) return it->second;
+  const double t = compute_theta(m, u);
+  g_theta_cache[key] = t;
+  return t;
+}
+
+bool valid_u(double u) { return std::isfinite(u) && u >= std::ldexp(1.0, -60) && u <= std::ldexp(1.0, -5); }
+
+// least s >= 0 with norm / 2^s <= th
+int least_squarings(double norm, double th) {
+  if (!(norm > th)) return 0;
+  int s = (int)std::ceil(std::log2(norm / th));
+  if (s < 0) s = 0;
+  while (std::ldexp(norm, -s) > th) ++s;
+  while (s > 0 && std::ldexp(norm, -(s - 1)) <= th) --s;
+  return s;
+}
+
+int select_ms(double norm, double u, int scheme, int* m, int* s) {
+  const int *deg, *prod;
+  const int cnt = scheme_degrees(scheme, &deg, &prod);
+  int bm = -1, bs = 0, bc = 1 << 30;
+  for (int i = 0; i < cnt; ++i) {
+    const int si = least_squarings(norm, theta_cached(deg[i], u));
+    const int cost = prod[i] + si;
+    if (cost < bc || (cost == bc && si < bs)) { bc = cost; bm = deg[i]; bs = si; }
+  }
+  *m = bm;
+  *s = bs;
+  return BBC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+int ensure_workspace(bbc_handle h, int64_t N, int flags) {
+  BBC_CUDA(cudaSetDevice(h->device));
+  if (N > h->slots_n) {
+    if (h->work) BBC_CUDA(cudaFree(h->work));
+    if (h->partial) BBC_CUDA(cudaFree(h->partial));
+    h->work = nullptr;
+    h->partial = nullptr;
+    h->slots_n = 0;
+    BBC_CUDA(cudaMalloc(&h->work, (size_t)NUM_WORK_SLOTS * N * N * sizeof(double)));
+    h->partial_len = norm1_partial_len(N);
+    BBC_CUDA(cudaMalloc(&h->partial, (size_t)h->partial_len * sizeof(double)));
+    h->slots_n = N;
+  }
+  if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
+    const int k = (flags >> 8) & 0xF;
+    const size_t need = ozaki_workspace_bytes(N, k ? k : 7);
+    if (need > h->ozaki_bytes) {
+      if (h->ozaki) BBC_CUDA(cudaFree(h->ozaki));
+      h->ozaki = nullptr;
+      h->ozaki_bytes = 0;
+      BBC_CUDA(cudaMalloc(&h->ozaki, need));
+      h->ozaki_bytes = need;
+    }
+  }
+  return BBC_OK;
+}
+
+double* slot_ptr(bbc_handle h, int slot, int64_t N, const double* A, double* T) {
+  if (slot == SL_A) return const_cast<double*>(A);
+  if (slot == SL_T) return T;
+  return h->work + (size_t)slot * N * N;
+}
+
+// One product (or linear combination) with its fused epilogue.
+int run_step(bbc_handle h, const StepS& st, int64_t N, const double* A, double* T, int flags,
+             unsigned int* flag, cudaStream_t stream) {
+  Epilogue e{};
+  int ny = 0;
+  e.nout = st.nout;
+  e.flag = flag;
+  for (int o = 0; o < st.nout; ++o) {
+    const OutS& q = st.o[o];
+    e.o[o].out = slot_ptr(h, q.dst, N, A, T);
+    e.o[o].cv = q.cv;
+    e.o[o].cI = q.cI;
+    e.o[o].nt = q.nt;
+    for (int t = 0; t < q.nt; ++t) {
+      const double* y = slot_ptr(h, q.t[t].slot, N, A, T);
+      int k = 0;
+      while (k < ny && e.Y[k] != y) ++k;
+      if (k == ny) {
+        if (ny == MAX_Y) return fail(BBC_INVALID_ARG, "epilogue reads too many matrices");
+        e.Y[ny++] = y;
+      }
+      e.o[o].slot[t] = k;
+      e.o[o].c[t] = q.t[t].c;
+    }
+  }
+  cudaError_t err;
+  if (st.P < 0) {
+    err = lincomb(N, e, stream);
+  } else {
+    const double* P = slot_ptr(h, st.P, N, A, T);
+    const double* Q = slot_ptr(h, st.Q, N, A, T);
+    if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
+      const int k = (flags >> 8) & 0xF;
+      err = gemm_ozaki(P, Q, N, st.alpha, e, k ? k : 7, h->ozaki, stream);
+    } else {
+      err = gemm_f64(P, Q, N, st.alpha, e, stream);
+    }
+  }
+  if (err != cudaSuccess) return cuda_fail(err, "kernel launch");
+  return BBC_OK;
+}
+
+int check_flags(int flags) {
+  const int scheme = flags & BBC_SCHEME_MASK;
+  const int prec = flags & BBC_PREC_MASK;
+  if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS) return fail(BBC_INVALID_ARG, "unknown scheme");
+  if (prec != BBC_PREC_FP64 && prec != BBC_PREC_OZAKI) return fail(BBC_INVALID_ARG, "unknown precision");
+  if (flags & ~0xFFF) return fail(BBC_INVALID_ARG, "unknown flag bits");
+  if (prec == BBC_PREC_OZAKI) {
+    const int k = (flags >> 8) & 0xF;
+    if (k != 0 && (k < 2 || k > 8)) return fail(BBC_INVALID_ARG, "Ozaki slice count must be 2..8");
+  }
+  return BBC_OK;
+}
+
+bool overlaps(const double* a, const double* b, int64_t N) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  const size_t bytes = (size_t)N * N * sizeof(double);
+  return pa < pb + bytes && pb < pa + bytes;
+}
+
+// T_m(2^-s A) into T, then s squarings ending in Out. The final write sets
+// the non-finite flag if any entry of the result is not finite.
+int run_expm(bbc_handle h, const double* A, int64_t N, double* Out, int m, int s, int flags,
+             cudaStream_t stream, bbc_info* info) {
+  Program prog;
+  if (!make_program(flags & BBC_SCHEME_MASK, m, s, &prog))
+    return fail(BBC_INVALID_ARG, "degree not available in this scheme");
+  if (s < 0 || s > 1100) return fail(BBC_INVALID_ARG, "squarings out of range");
+  double* tmp = h->work + (size_t)SL_SQ * N * N;
+  double* T = (s % 2 == 0) ? Out : tmp;  // the ping-pong ends in Out
+  for (size_t i = 0; i < prog.steps.size(); ++i) {
+    const bool last = (s == 0 && i + 1 == prog.steps.size());
+    const int rc = run_step(h, prog.steps[i], N, A, T, flags, last ? h->dflag : nullptr, stream);
+    if (rc) return rc;
+  }
+  double* src = T;
+  for (int k = 0; k < s; ++k) {
+    double* dst = (src == Out) ? tmp : Out;
+    StepS sq{};
+    sq.P = SL_A; sq.Q = SL_A; sq.alpha = 1.0; sq.nout = 1;
+    sq.o[0].dst = SL_T; sq.o[0].cv = 1.0; sq.o[0].cI = 0.0; sq.o[0].nt = 0;
+    // SL_A -> src and SL_T -> dst for this step
+    const int rc = run_step(h, sq, N, src, dst, flags, (k + 1 == s) ? h->dflag : nullptr, stream);
+    if (rc) return rc;
+    src = dst;
+  }
+  if (info) {
+    info->m = m;
+    info->s = s;
+    info->products = prog.products + s;
+  }
+  return BBC_OK;
+}
+
+int begin(bbc_handle h) {
+  if (!h) return fail(BBC_INVALID_ARG, "null handle");
+  g_err.clear();
+  BBC_CUDA(cudaSetDevice(h->device));
+  return BBC_OK;
+}
+
+int read_norm(bbc_handle h, const double* A, int64_t N, cudaStream_t st, double* norm) {
+  cudaError_t e = bbc::norm1(A, N, h->partial, h->dnorm, st);
+  if (e != cudaSuccess) return cuda_fail(e, "norm1");
+  double* hs = (double*)h->hstage;
+  BBC_CUDA(cudaMemcpyAsync(hs, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
+  BBC_CUDA(cudaStreamSynchronize(st));
+  *norm = hs[0];
+  return BBC_OK;
+}
+
+int finish_status(bbc_handle h, cudaStream_t st, int* status) {
+  unsigned int* hf = (unsigned int*)((double*)h->hstage + 1);
+  BBC_CUDA(cudaMemcpyAsync(hf, h->dflag, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  BBC_CUDA(cudaStreamSynchronize(st));
+  *status = (*hf != 0) ? BBC_OVERFLOW : BBC_OK;
+  return BBC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bbc_last_error(void) { return g_err.c_str(); }
+
+int bbc_create(bbc_handle* out, int device) {
+  if (!out) return fail(BBC_INVALID_ARG, "null handle pointer");
+  *out = nullptr;
+  int count = 0;
+  BBC_CUDA(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) return fail(BBC_INVALID_ARG, "no such device");
+  BBC_CUDA(cudaSetDevice(device));
+  bbc_handle h = new bbc_handle_s();
+  h->device = device;
+  cudaError_t e = cudaMalloc(&h->dnorm, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->dflag, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->hstage, 64);
+  if (e != cudaSuccess) {
+    bbc_destroy(h);
+    return cuda_fail(e, "bbc_create");
+  }
+  *out = h;
+  return BBC_OK;
+}
+
+int bbc_destroy(bbc_handle h) {
+  if (!h) return BBC_OK;
+  cudaSetDevice(h->device);
+  cudaFree(h->work);
+  cudaFree(h->partial);
+  cudaFree(h->dnorm);
+  cudaFree(h->dflag);
+  cudaFree(h->ozaki);
+  cudaFree(h->io);
+  if (h->hstage) cudaFreeHost(h->hstage);
+  delete h;
+  return BBC_OK;
+}
+
+int bbc_workspace_size(bbc_handle h, int64_t N, int dtype, int flags, size_t* bytes) {
+  (void)h;
+  if (N <= 0 || !bytes || dtype != 0) return fail(BBC_INVALID_ARG, "bad workspace query");
+  int rc = check_flags(flags);
+  if (rc) return rc;
+  size_t b = (size_t)NUM_WORK_SLOTS * N * N * sizeof(double) + norm1_partial_len(N) * sizeof(double);
+  if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
+    const int k = (flags >> 8) & 0xF;
+    b += ozaki_workspace_bytes(N, k ? k : 7);
+  }
+  *bytes = b;
+  return BBC_OK;
+}
+
+int bbc_theta(int m, double u, double* theta) {
+  if (!theta || m < 1 || m > 30 || !valid_u(u)) return fail(BBC_INVALID_ARG, "bad theta query");
+  *theta = theta_cached(m, u);
+  return BBC_OK;
+}
+
+int bbc_select(double norm1, double u, int scheme, int* m, int* s) {
+  if (!m || !s || !valid_u(u)) return fail(BBC_INVALID_ARG, "bad selection query");
+  if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS) return fail(BBC_INVALID_ARG, "unknown scheme");
+  if (!std::isfinite(norm1) || norm1 < 0) return fail(BBC_NONFINITE_INPUT, "norm not finite");
+  return select_ms(norm1, u, scheme, m, s);
+}
+
+int bbc_norm1(bbc_handle h, const double* dA, int64_t N, void* stream, double* hNorm) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!dA || !hNorm || N <= 0) return fail(BBC_INVALID_ARG, "bad norm1 arguments");
+  std::lock_guard<std::mutex> lk(h->mu);
+  rc = ensure_workspace(h, N, 0);
+  if (rc) return rc;
+  return read_norm(h, dA, N, (cudaStream_t)stream, hNorm);
+}
+
+int bbc_gemm(bbc_handle h, const double* dP, const double* dQ, int64_t N, double* dC, int flags,
+             void* stream) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!dP || !dQ || !dC || N <= 0) return fail(BBC_INVALID_ARG, "bad gemm arguments");
+  if (overlaps(dC, dP, N) || overlaps(dC, dQ, N)) return fail(BBC_INVALID_ARG, "output aliases an input");
+  if ((rc = check_flags(flags))) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if ((rc = ensure_workspace(h, N, flags))) return rc;
+  Epilogue e{};
+  e.nout = 1;
+  e.o[0].out = dC;
+  e.o[0].cv = 1.0;
+  cudaError_t err;
+  if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
+    const int k = (flags >> 8) & 0xF;
+    err = gemm_ozaki(dP, dQ, N, 1.0, e, k ? k : 7, h->ozaki, (cudaStream_t)stream);
+  } else {
+    err = gemm_f64(dP, dQ, N, 1.0, e, (cudaStream_t)stream);
+  }
+  if (err != cudaSuccess) return cuda_fail(err, "gemm");
+  return BBC_OK;
+}
+
+int bbc_taylor(bbc_handle h, const double* dA, int64_t N, int m, int s, double* dT, int flags,
+               void* stream, int* products) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!dA || !dT || N <= 0 || s < 0 || s > 1100) return fail(BBC_INVALID_ARG, "bad taylor arguments");
+  if (overlaps(dA, dT, N)) return fail(BBC_INVALID_ARG, "output aliases the input");
+  if ((rc = check_flags(flags))) return rc;
+  Program prog;
+  if (!make_program(flags & BBC_SCHEME_MASK, m, s, &prog))
+    return fail(BBC_INVALID_ARG, "degree not available in this scheme");
+  std::lock_guard<std::mutex> lk(h->mu);
+  if ((rc = ensure_workspace(h, N, flags))) return rc;
+  for (const StepS& st : prog.steps)
+    if ((rc = run_step(h, st, N, dA, dT, flags, nullptr, (cudaStream_t)stream))) return rc;
+  if (products) *products = prog.products;
+  return BBC_OK;
+}
+
+int bbc_expm_fixed(bbc_handle h, const double* dA, int64_t N, double* dOut, int m, int s, int flags,
+                   void* stream, bbc_info* info) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!dA || !dOut || N <= 0) return fail(BBC_INVALID_ARG, "bad expm arguments");
+  if (overlaps(dA, dOut, N)) return fail(BBC_INVALID_ARG, "output aliases the input");
+  if ((rc = check_flags(flags))) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if ((rc = ensure_workspace(h, N, flags))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  bbc_info loc{};
+  bbc_info* inf = info ? info : &loc;
+  memset(inf, 0, sizeof *inf);
+  inf->selector = 1;
+  if ((rc = read_norm(h, dA, N, st, &inf->norm1))) return rc;
+  if (!std::isfinite(inf->norm1)) {
+    inf->status = BBC_NONFINITE_INPUT;
+    return fail(BBC_NONFINITE_INPUT, "input holds a non-finite value");
+  }
+  BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
+  if ((rc = run_expm(h, dA, N, dOut, m, s, flags, st, inf))) return rc;
+  if ((rc = finish_status(h, st, &inf->status))) return rc;
+  if (inf->status) return fail(inf->status, "result holds a non-finite value");
+  return BBC_OK;
+}
+
+int bbc_expm(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol, int flags,
+             void* stream, bbc_info* info) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!dA || !dOut || N <= 0) return fail(BBC_INVALID_ARG, "bad expm arguments");
+  if (overlaps(dA, dOut, N)) return fail(BBC_INVALID_ARG, "output aliases the input");
+  const double u = tol > 0 ? tol : std::ldexp(1.0, -53);
+  if (!valid_u(u)) return fail(BBC_INVALID_ARG, "tol out of range [2^-60, 2^-5]");
+  if ((rc = check_flags(flags))) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if ((rc = ensure_workspace(h, N, flags))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  bbc_info loc{};
+  bbc_info* inf = info ? info : &loc;
+  memset(inf, 0, sizeof *inf);
+  if ((rc = read_norm(h, dA, N, st, &inf->norm1))) return rc;
+  if (!std::isfinite(inf->norm1)) {
+    inf->status = BBC_NONFINITE_INPUT;
+    return fail(BBC_NONFINITE_INPUT, "input holds a non-finite value");
+  }
+  int m, s;
+  select_ms(inf->norm1, u, flags & BBC_SCHEME_MASK, &m, &s);
+  BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
+  if ((rc = run_expm(h, dA, N, dOut, m, s, flags, st, inf))) return rc;
+  if ((rc = finish_status(h, st, &inf->status))) return rc;
+  if (inf->status) return fail(inf->status, "result holds a non-finite value");
+  return BBC_OK;
+}
+
+int bbc_expm_host(bbc_handle h, const double* hA, int64_t N, double* hOut, double tol, int flags,
+                  void* stream, bbc_info* info) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!hA || !hOut || N <= 0) return fail(BBC_INVALID_ARG, "bad expm arguments");
+  if (overlaps(hA, hOut, N)) return fail(BBC_INVALID_ARG, "output aliases the input");
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (N > h->io_n) {
+      if (h->io) BBC_CUDA(cudaFree(h->io));
+      h->io = nullptr;
+      h->io_n = 0;
+      BBC_CUDA(cudaMalloc(&h->io, (size_t)2 * N * N * sizeof(double)));
+      h->io_n = N;
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)N * N * sizeof(double);
+  double* dA = h->io;
+  double* dOut = h->io + (size_t)N * N;
+  BBC_CUDA(cudaMemcpyAsync(dA, hA, bytes, cudaMemcpyHostToDevice, st));
+  rc = bbc_expm(h, dA, N, dOut, tol, flags, stream, info);
+  if (rc) return rc;
+  BBC_CUDA(cudaMemcpyAsync(hOut, dOut, bytes, cudaMemcpyDeviceToHost, st));
+  BBC_CUDA(cudaStreamSynchronize(st));
+  return BBC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// elementwise.cu -- the O(N^2) steps: ||A||_1 and product-free linear combinations.
+//
+// ||A||_1 = max_j sum_i |a_ij| (the norm that drives the choice of (m, s),
+// Section 4 and eq. theta). Row-major storage puts a column's entries N apart,
+// so each thread owns one column and the 32 threads of a warp read 32 adjacent
+// doubles of a row (256 B, coalesced). Rows are split into slabs across
+// blockIdx.y so a 4096 x 4096 input fills the GPU; the slab partial sums are
+// then added in slab order (deterministic) and the maximum is taken with a warp
+// shuffle and a 64-bit atomicMax on the bit pattern, which orders non-negative
+// doubles (and a positive NaN above +inf) correctly.
+#include "internal.h"
+
+namespace bbc {
+namespace {
+
+constexpr int NORM_THREADS = 256;
+
+int64_t slabs_for(int64_t N) {
+  // ~2 * 152 SMs worth of blocks, at least 64 rows per slab
+  const int64_t colblocks = (N + NORM_THREADS - 1) / NORM_THREADS;
+  int64_t slabs = (304 + colblocks - 1) / colblocks;
+  const int64_t max_slabs = (N + 63) / 64;
+  if (slabs > max_slabs) slabs = max_slabs;
+  return slabs < 1 ? 1 : slabs;
+}
+
+__global__ void __launch_bounds__(NORM_THREADS)
+k_colsum(const double* __restrict__ A, int64_t N, int64_t rows_per, double* __restrict__ partial) {
+  const int64_t j = (int64_t)blockIdx.x * NORM_THREADS + threadIdx.x;
+  if (j >= N) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per;
+  const int64_t r1 = r0 + rows_per < N ? r0 + rows_per : N;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int64_t i = r0;
+  for (; i + 4 <= r1; i += 4) {
+    s0 += fabs(__ldg(A + (i + 0) * N + j));
+    s1 += fabs(__ldg(A + (i + 1) * N + j));
+    s2 += fabs(__ldg(A + (i + 2) * N + j));
+    s3 += fabs(__ldg(A + (i + 3) * N + j));
+  }
+  for (; i < r1; ++i) s0 += fabs(__ldg(A + i * N + j));
+  partial[(int64_t)blockIdx.y * N + j] = (s0 + s1) + (s2 + s3);
+}
+
+__global__ void __launch_bounds__(NORM_THREADS)
+k_colmax(const double* __restrict__ partial, int64_t N, int64_t slabs,
+         unsigned long long* __restrict__ out) {
+  const int64_t j = (int64_t)blockIdx.x * NORM_THREADS + threadIdx.x;
+  double s = 0.0;
+  if (j < N)
+    for (int64_t r = 0; r < slabs; ++r) s += partial[r * N + j];
+  unsigned long long b = (unsigned long long)__double_as_longlong(s);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, b, off);
+    b = o > b ? o : b;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, b);
+}
+
+__global__ void k_lincomb(int64_t N, const Epilogue e) {
+  const int64_t total = N * N;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    apply_epilogue(e, N, idx / N, idx % N, 0.0);
+}
+
+}  // namespace
+
+int64_t norm1_partial_len(int64_t N) { return slabs_for(N) * N; }
+
+cudaError_t norm1(const double* A, int64_t N, double* partial, double* dNorm, cudaStream_t st) {
+  const int64_t slabs = slabs_for(N);
+  const int64_t rows_per = (N + slabs - 1) / slabs;
+  const unsigned colblocks = (unsigned)((N + NORM_THREADS - 1) / NORM_THREADS);
+  cudaError_t err = cudaMemsetAsync(dNorm, 0, sizeof(double), st);
+  if (err != cudaSuccess) return err;
+  k_colsum<<<dim3(colblocks, (unsigned)slabs), NORM_THREADS, 0, st>>>(A, N, rows_per, partial);
+  k_colmax<<<colblocks, NORM_THREADS, 0, st>>>(partial, N, slabs, (unsigned long long*)dNorm);
+  return cudaGetLastError();
+}
+
+cudaError_t lincomb(int64_t N, const Epilogue& e, cudaStream_t st) {
+  const int64_t total = N * N;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_lincomb<<<(unsigned)blocks, 256, 0, st>>>(N, e);
+  return cudaGetLastError();
+}
+
+}  // namespace bbc

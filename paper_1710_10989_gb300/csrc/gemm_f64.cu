@@ -1,0 +1,111 @@
+// gemm_f64.cu -- FP64 dense product with the fused linear-combination epilogue.
+//
+// On GB300 the FP64 pipe issues about 1.6 DFMA per clock per SM (~1.0 TFLOP/s
+// for the chip, measured; DMMA is no faster), roughly 1/70 of the FP32 rate. A
+// product of the method (Section 1: the cost unit of scaling and squaring) is
+// therefore bound by the FP64 pipe, not by HBM: with 64 x 64 tiles each operand
+// element is re-read N/64 times from L2, far below what the FP64 pipe can
+// consume. The kernel keeps the schedule simple: 64 x 64 x 16 tiles (32 x 32 for
+// small N, to spread a 64 x 64 matrix over more SMs), 256 threads, each thread a
+// 4 x 4 (2 x 2) register block with rows/columns strided by 16 so that shared
+// memory reads are conflict-free and epilogue accesses coalesce, and the next
+// K-slab prefetched into registers while the current one is multiplied.
+#include "internal.h"
+
+namespace bbc {
+namespace {
+
+constexpr int BK = 16;
+constexpr int THREADS = 256;
+
+template <int BM, int BN>
+__global__ void __launch_bounds__(THREADS)
+k_gemm_f64(const double* __restrict__ P, const double* __restrict__ Q, int64_t N, double alpha,
+           const Epilogue e) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  constexpr int LP = BM * BK / THREADS;   // P elements per thread per slab
+  constexpr int LQ = BK * BN / THREADS;   // Q elements per thread per slab
+  constexpr int QROWS = THREADS / BN;     // Q rows covered by one pass of the block
+  __shared__ double As[2][BK][BM];
+  __shared__ double Bs[2][BK][BN];
+
+  const int t = threadIdx.x;
+  const int tx = t % 16, ty = t / 16;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+
+  double rp[LP], rq[LQ];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < LP; ++q) {
+      const int64_t r = m0 + t / 16 + 16 * q, c = k0 + t % 16;
+      rp[q] = (r < N && c < N) ? __ldg(P + r * N + c) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < LQ; ++q) {
+      const int64_t r = k0 + t / BN + QROWS * q, c = n0 + t % BN;
+      rq[q] = (r < N && c < N) ? __ldg(Q + r * N + c) : 0.0;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < LP; ++q) As[buf][t % 16][t / 16 + 16 * q] = rp[q];
+#pragma unroll
+    for (int q = 0; q < LQ; ++q) Bs[buf][t / BN + QROWS * q][t % BN] = rq[q];
+  };
+
+  const int64_t nslab = (N + BK - 1) / BK;
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int64_t s = 0; s < nslab; ++s) {
+    const int buf = s & 1;
+    if (s + 1 < nslab) load((s + 1) * BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    if (s + 1 < nslab) store(buf ^ 1);
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t row = m0 + ty + 16 * i;
+    if (row >= N) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t col = n0 + tx + 16 * j;
+      if (col < N) apply_epilogue(e, N, row, col, alpha * acc[i][j]);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t gemm_f64(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
+                     cudaStream_t st) {
+  if (N <= 512) {
+    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((N + 31) / 32));
+    k_gemm_f64<32, 32><<<grid, THREADS, 0, st>>>(P, Q, N, alpha, e);
+  } else {
+    dim3 grid((unsigned)((N + 63) / 64), (unsigned)((N + 63) / 64));
+    k_gemm_f64<64, 64><<<grid, THREADS, 0, st>>>(P, Q, N, alpha, e);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bbc

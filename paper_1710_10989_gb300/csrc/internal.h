@@ -1,0 +1,72 @@
+// internal.h -- declarations shared by the translation units of libbbcexpm.so.
+//
+// The central abstraction is the fused linear-combination epilogue: every dense
+// product of the method is followed by up to MAX_OUT outputs, each a linear
+// combination of the product value v, the identity and up to MAX_TERMS matrices
+// that are already resident (X, X2, X3, B_j, ...). This is how the reduced-product
+// scheme of Section 3 (eq. Algorithm83eA, eq. poly12, eq. poly.18) runs with no
+// standalone linear-combination pass: e.g. for T18 the product X6 = X3 X3 emits
+// B1..B5 directly, and B1 B5 emits both A9 = B1 B5 + B4 and B3 + A9.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bbc {
+
+constexpr int MAX_Y = 6;      // distinct matrices an epilogue may read
+constexpr int MAX_OUT = 6;    // outputs one epilogue may write
+constexpr int MAX_TERMS = 5;  // matrix terms per output
+
+struct EpiOut {
+  double* out;             // destination, N x N row-major
+  double cv;               // coefficient of the product value v
+  double cI;               // coefficient of the identity
+  int nt;                  // number of matrix terms
+  int slot[MAX_TERMS];     // index into Epilogue::Y
+  double c[MAX_TERMS];     // coefficients
+};
+
+struct Epilogue {
+  const double* Y[MAX_Y];  // matrices read element-wise by the epilogue
+  int nout;
+  EpiOut o[MAX_OUT];
+  unsigned int* flag;      // if non-null: set to 1 when any output is not finite
+};
+
+// Element (row, col) of every output of the epilogue, given v = alpha * (P Q)_rc.
+__device__ __forceinline__ void apply_epilogue(const Epilogue& e, int64_t N, int64_t row,
+                                               int64_t col, double v) {
+  const int64_t idx = row * N + col;
+  bool bad = false;
+#pragma unroll 1
+  for (int o = 0; o < e.nout; ++o) {
+    const EpiOut& q = e.o[o];
+    double r = q.cv * v;
+    if (row == col) r += q.cI;
+#pragma unroll 1
+    for (int t = 0; t < q.nt; ++t) r = fma(q.c[t], __ldg(e.Y[q.slot[t]] + idx), r);
+    q.out[idx] = r;
+    bad |= !isfinite(r);
+  }
+  if (bad && e.flag) atomicOr(e.flag, 1u);
+}
+
+// FP64 DFMA product with fused epilogue: v = alpha * (P Q).
+cudaError_t gemm_f64(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
+                     cudaStream_t st);
+
+// Element-wise linear combination (no product): outputs of `e` with v = 0.
+cudaError_t lincomb(int64_t N, const Epilogue& e, cudaStream_t st);
+
+// ||A||_1 into *dNorm (device). `partial` must hold norm1_partial_len(N) doubles.
+int64_t norm1_partial_len(int64_t N);
+cudaError_t norm1(const double* A, int64_t N, double* partial, double* dNorm, cudaStream_t st);
+
+// Ozaki split products on tcgen05 (gemm_ozaki.cu).
+struct OzakiWork;  // opaque, owned by the handle
+size_t ozaki_workspace_bytes(int64_t N, int slices);
+cudaError_t gemm_ozaki(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
+                       int slices, void* work, cudaStream_t st);
+bool ozaki_supported(int64_t N);
+
+}  // namespace bbc

@@ -1,0 +1,191 @@
+// schemes.cu -- coefficient tables and evaluation programs of the Taylor schemes.
+//
+// Reduced-product scheme, Section 3 of Bader, Blanes, Casas (arXiv:1710.10989):
+//   T8  in 3 products, eq. (Algorithm83eA), closed forms in sqrt(177), x3 = 2/3;
+//   T12 in 4 products, eq. (poly12), 16 numeric coefficients a_{i,j};
+//   T18 in 5 products, eq. (poly.18), coefficients a_{i,1} and b_{i,j};
+//   T1, T2, T4 in 0, 1, 2 products (Horner-like, as Paterson-Stockmeyer).
+// Paterson-Stockmeyer comparator, eq. (poli9): T9, T16 as printed, and the
+// analogous T4, T6 (blocks in A2) and T12 (blocks in A3).
+#include <cmath>
+
+#include "../../include/bbcexpm.h"
+#include "schemes.h"
+
+namespace bbc {
+namespace {
+
+// eq. (poly12): T12A[i][j-1] = a_{i,j}, i = power of A (0..3), j = 1..4.
+const double T12A[4][4] = {
+    {9.0198e-16, 5.31597895759871264183, 0.18188869982170434744, -2.0861320e-13},
+    {0.46932117595418237389, 1.19926790417132231573, 0.05502798439925399070, -0.13181061013830184015},
+    {-0.20099424927047284052, 0.01179296240992997031, 0.09351590770535414968, -0.02027855540589259079},
+    {-0.04623946134063071740, 0.01108844528519167989, 0.00610700528898058230, -0.00675951846863086359}};
+
+// eq. (poly.18): a_{i,1}, i = 0..3.
+const double T18A1[4] = {0.0, -0.100365581030144620, -0.0080292464824115696, -0.0008921384980457299};
+// eq. (poly.18): T18B[r][j-1] = b_{i,j} with i = {0, 1, 2, 3, 6}[r], j = 1..4.
+const double T18B[5][4] = {
+    {0.0, -10.967639605296206259, -0.0904316832390810561, 0.0},
+    {0.39784974949964507614, 1.68015813878906197182, -0.0676404519071381907, 0.0},
+    {1.36783778460411719922, 0.05717798464788655127, 0.06759613017704596460, -0.0923364619367118592},
+    {0.49828962252538267755, -0.0069821012248805208, 0.02955525704293155274, -0.0169364939002081717},
+    {-0.0006378981945947233, 0.00003349750170860705, -0.0000139180257516060, -0.0000140086798182036}};
+
+const int NEW_DEG[6] = {1, 2, 4, 8, 12, 18};
+const int NEW_PROD[6] = {0, 1, 2, 3, 4, 5};
+const int PS_DEG[7] = {1, 2, 4, 6, 9, 12, 16};
+const int PS_PROD[7] = {0, 1, 2, 3, 4, 5, 6};
+
+double inv_factorial(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= i;
+  return 1.0 / f;
+}
+
+// Small builder so that programs read like the paper's sequences.
+struct Out {
+  OutS o{};
+  Out(int dst, double cv, double cI = 0.0) { o.dst = dst; o.cv = cv; o.cI = cI; o.nt = 0; }
+  Out& t(int slot, double c) {
+    if (c != 0.0) o.t[o.nt++] = TermS{slot, c};
+    return *this;
+  }
+};
+struct Step {
+  StepS s{};
+  Step(int P, int Q, double alpha) { s.P = P; s.Q = Q; s.alpha = alpha; s.nout = 0; }
+  Step& out(const Out& o) { s.o[s.nout++] = o.o; return *this; }
+};
+
+void add(Program* p, const Step& st) {
+  p->steps.push_back(st.s);
+  if (st.s.P >= 0) p->products++;
+}
+
+enum { W0 = 0, W1, W2, W3, W4, W5, W6, W7, W8 };
+
+// Paterson-Stockmeyer Horner tail: given block power Y = A_q in slot `ys`,
+// powers A (scaled by sig), A2 in W0 and A3 in W1 (if q > 3), and the innermost
+// block already in slot `acc`, emit the remaining r - 1 Horner products.
+void ps_tail(Program* p, int q, int r, int ys, int acc, int spare, double sig) {
+  for (int i = r - 2; i >= 0; --i) {
+    const int dst = (i == 0) ? SL_T : spare;
+    Out o(dst, 1.0, inv_factorial(q * i));
+    o.t(SL_A, inv_factorial(q * i + 1) * sig);
+    if (q >= 3) o.t(W0, inv_factorial(q * i + 2));
+    if (q >= 4) o.t(W1, inv_factorial(q * i + 3));
+    add(p, Step(acc, ys, 1.0).out(o));
+    const int t = acc; acc = spare; spare = t;
+  }
+}
+
+}  // namespace
+
+int scheme_degrees(int scheme, const int** deg, const int** products) {
+  if (scheme == BBC_SCHEME_PS) { *deg = PS_DEG; *products = PS_PROD; return 7; }
+  *deg = NEW_DEG; *products = NEW_PROD; return 6;
+}
+
+bool make_program(int scheme, int m, int s, Program* p) {
+  p->m = m;
+  p->products = 0;
+  p->steps.clear();
+  const double sig = std::ldexp(1.0, -s);     // X = sig * A
+  const double sig2 = sig * sig;
+  if (m == 1) {                                // T1 = I + X
+    add(p, Step(-1, -1, 0.0).out(Out(SL_T, 0.0, 1.0).t(SL_A, sig)));
+    return true;
+  }
+  if (m == 2) {                                // T2 = I + X + X^2/2
+    add(p, Step(SL_A, SL_A, sig2).out(Out(SL_T, 0.5, 1.0).t(SL_A, sig)));
+    return true;
+  }
+  if (scheme == BBC_SCHEME_NEW) {
+    if (m == 4) {                              // T4 = I + X + A2 (I/2 + X/6 + A2/24)
+      add(p, Step(SL_A, SL_A, sig2).out(Out(W0, 1.0)).out(Out(W1, 1.0 / 24, 0.5).t(SL_A, sig / 6)));
+      add(p, Step(W0, W1, 1.0).out(Out(SL_T, 1.0, 1.0).t(SL_A, sig)));
+      return true;
+    }
+    if (m == 8) {                              // eq. (Algorithm83eA)
+      const double r = std::sqrt(177.0);
+      const double x3 = 2.0 / 3.0;
+      const double x1 = x3 * (1.0 + r) / 88.0, x2 = x3 * (1.0 + r) / 352.0;
+      const double x4 = (-271.0 + 29.0 * r) / (315.0 * x3);
+      const double x5 = 11.0 * (-1.0 + r) / (1260.0 * x3);
+      const double x6 = 11.0 * (-9.0 + r) / (5040.0 * x3);
+      const double x7 = (89.0 - r) / (5040.0 * x3 * x3);
+      const double y0 = 1.0, y1 = 1.0, y2 = (857.0 - 58.0 * r) / 630.0;
+      // A2 = X^2; also x1 X + x2 A2
+      add(p, Step(SL_A, SL_A, sig2).out(Out(W0, 1.0)).out(Out(W1, x2).t(SL_A, x1 * sig)));
+      // A4 = A2 (x1 X + x2 A2); emits x3 A2 + A4 and x4 I + x5 X + x6 A2 + x7 A4
+      add(p, Step(W0, W1, 1.0)
+                 .out(Out(W2, 1.0).t(W0, x3))
+                 .out(Out(W3, x7, x4).t(SL_A, x5 * sig).t(W0, x6)));
+      // A8 = (x3 A2 + A4)(x4 I + ...); T8 = y0 I + y1 X + y2 A2 + A8
+      add(p, Step(W2, W3, 1.0).out(Out(SL_T, 1.0, y0).t(SL_A, y1 * sig).t(W0, y2)));
+      return true;
+    }
+    if (m == 12) {                             // eq. (poly12)
+      add(p, Step(SL_A, SL_A, sig2).out(Out(W0, 1.0)));           // A2
+      Step st(W0, SL_A, sig);                                       // v = A3; B_j -> W1..W4
+      for (int j = 0; j < 4; ++j)
+        st.out(Out(W1 + j, T12A[3][j], T12A[0][j]).t(SL_A, T12A[1][j] * sig).t(W0, T12A[2][j]));
+      add(p, st);
+      // A6 = B3 + B4^2 -> W5;  B2 + A6 -> W6
+      add(p, Step(W4, W4, 1.0).out(Out(W5, 1.0).t(W3, 1.0)).out(Out(W6, 1.0).t(W3, 1.0).t(W2, 1.0)));
+      // T12 = B1 + (B2 + A6) A6
+      add(p, Step(W6, W5, 1.0).out(Out(SL_T, 1.0).t(W1, 1.0)));
+      return true;
+    }
+    if (m == 18) {                             // eq. (poly.18)
+      add(p, Step(SL_A, SL_A, sig2).out(Out(W0, 1.0)));           // A2
+      add(p, Step(W0, SL_A, sig).out(Out(W1, 1.0)));              // A3
+      // v = A6 = A3^2; B1 -> W2, B2..B5 -> W3..W6
+      Step st(W1, W1, 1.0);
+      st.out(Out(W2, 0.0, T18A1[0]).t(SL_A, T18A1[1] * sig).t(W0, T18A1[2]).t(W1, T18A1[3]));
+      for (int j = 0; j < 4; ++j)
+        st.out(Out(W3 + j, T18B[4][j], T18B[0][j]).t(SL_A, T18B[1][j] * sig).t(W0, T18B[2][j]).t(W1, T18B[3][j]));
+      add(p, st);
+      // A9 = B1 B5 + B4 -> W7;  B3 + A9 -> W8
+      add(p, Step(W2, W6, 1.0).out(Out(W7, 1.0).t(W5, 1.0)).out(Out(W8, 1.0).t(W5, 1.0).t(W4, 1.0)));
+      // T18 = B2 + (B3 + A9) A9
+      add(p, Step(W8, W7, 1.0).out(Out(SL_T, 1.0).t(W3, 1.0)));
+      return true;
+    }
+    return false;
+  }
+  if (scheme == BBC_SCHEME_PS) {
+    auto c = inv_factorial;
+    if (m == 4 || m == 6) {                    // blocks in A2: g_i = c_{2i} I + c_{2i+1} X
+      const int r = m / 2;
+      add(p, Step(SL_A, SL_A, sig2)
+                 .out(Out(W0, 1.0))
+                 .out(Out(W1, c(m), c(m - 2)).t(SL_A, c(m - 1) * sig)));
+      ps_tail(p, 2, r, W0, W1, W2, sig);
+      return true;
+    }
+    if (m == 9 || m == 12) {                   // blocks in A3: f_i = sum_{k<3} c_{3i+k} A_k
+      const int r = m / 3;
+      add(p, Step(SL_A, SL_A, sig2).out(Out(W0, 1.0)));           // A2
+      add(p, Step(W0, SL_A, sig)
+                 .out(Out(W1, 1.0))                                   // A3
+                 .out(Out(W2, c(m), c(m - 3)).t(SL_A, c(m - 2) * sig).t(W0, c(m - 1))));
+      ps_tail(p, 3, r, W1, W2, W3, sig);
+      return true;
+    }
+    if (m == 16) {                             // blocks in A4: g_i = sum_{k<4} c_{4i+k} A_k
+      add(p, Step(SL_A, SL_A, sig2).out(Out(W0, 1.0)));           // A2
+      add(p, Step(W0, SL_A, sig).out(Out(W1, 1.0)));              // A3
+      add(p, Step(W0, W0, 1.0)
+                 .out(Out(W2, 1.0))                                   // A4
+                 .out(Out(W3, c(16), c(12)).t(SL_A, c(13) * sig).t(W0, c(14)).t(W1, c(15))));
+      ps_tail(p, 4, 4, W2, W3, W4, sig);
+      return true;
+    }
+    return false;
+  }
+  return false;
+}
+
+}  // namespace bbc

@@ -1,0 +1,69 @@
+"""The C-ABI library loads on a machine without a GPU and exports every symbol
+that include/*.h declares; host-only entry points (theta, selection) agree with
+the oracle. No GPU compute is called here."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from oracle import theta as TH
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(bbc_\w+)\s*\(", text, re.M))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1710_10989_gb300 import build
+    return ctypes.CDLL(build.build())
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1710_10989_gb300 import api
+    assert set(declared_symbols()) <= set(api.exported_symbols())
+
+
+@pytest.mark.parametrize("u", [2.0 ** -53, 2.0 ** -24])
+def test_library_theta_matches_oracle(u):
+    from paper_1710_10989_gb300 import api
+    for m in (1, 2, 4, 6, 8, 9, 12, 16, 18):
+        assert api.theta(m, u) == pytest.approx(TH.theta_taylor(m, u), rel=1e-13)
+
+
+def test_library_selection_matches_oracle():
+    from oracle import oracle as O
+    from paper_1710_10989_gb300 import api
+    import numpy as np
+    norms = np.concatenate([[0.0, 1e-30, 1e-10], np.logspace(-6, 3, 400)])
+    for scheme, name in ((api.SCHEME_NEW, "new"), (api.SCHEME_PS, "ps")):
+        for u, uu in ((api.U_DOUBLE, 2.0 ** -53), (api.U_SINGLE, 2.0 ** -24)):
+            for nrm in norms:
+                assert api.select(float(nrm), u, scheme) == O.select(float(nrm), name, uu), (nrm, name)
+
+
+def test_host_argument_errors():
+    from paper_1710_10989_gb300 import api
+    with pytest.raises(api.BBCError) as e:
+        api.theta(0)
+    assert e.value.code == api.INVALID_ARG
+    with pytest.raises(api.BBCError) as e:
+        api.select(float("nan"))
+    assert e.value.code == api.NONFINITE_INPUT
+    with pytest.raises(api.BBCError):
+        api.select(1.0, u=0.5)

@@ -1,0 +1,156 @@
+"""GPU parity, FP64 path: every step of the hot path through the C-ABI against
+the CPU oracle on the same seeded inputs (relative Frobenius tolerances:
+1e-13 for the 64 x 64 workload, 1e-12 for the 4096 x 4096 workload and the
+mid-size cases)."""
+import numpy as np
+import pytest
+
+from gpu_util import empty_like_dev, rel_fro, to_dev, to_host
+from oracle import oracle as O
+from paper_1710_10989_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_10989_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def h(api):
+    hh = api.Handle(0)
+    yield hh
+    hh.close()
+
+
+# ---- a1: 1-norm ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 255, 257, 1000])
+def test_norm1(h, n):
+    A = W.gaussian(n, 100 + n, None)
+    got = h.norm1(to_dev(A))
+    assert got == pytest.approx(O.norm1(A), rel=1e-14)
+
+
+def test_norm1_nonfinite(h, api):
+    A = np.eye(33)
+    A[5, 7] = np.inf
+    assert not np.isfinite(h.norm1(to_dev(A)))
+    A[5, 7] = np.nan
+    assert np.isnan(h.norm1(to_dev(A)))
+
+
+# ---- product --------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 7, 16, 64, 65, 200, 512, 513, 640])
+def test_gemm_fp64(h, n):
+    P = W.gaussian(n, 1 + n, None)
+    Q = W.gaussian(n, 2 + n, None)
+    C = empty_like_dev(n)
+    h.gemm(to_dev(P), to_dev(Q), C)
+    assert rel_fro(to_host(C), O.gemm(P, Q)) < 1e-15 * max(8, np.sqrt(n))
+
+
+# ---- a3-a8: scaled Taylor polynomial by each program -----------------------------------------
+
+@pytest.mark.parametrize("scheme,m", [("new", 1), ("new", 2), ("new", 4), ("new", 8), ("new", 12),
+                                      ("new", 18), ("ps", 4), ("ps", 6), ("ps", 9), ("ps", 12),
+                                      ("ps", 16)])
+@pytest.mark.parametrize("n", [5, 130])
+def test_taylor_programs(h, api, scheme, m, n):
+    s = 3
+    A = W.gaussian(n, 40 + m, 6.0)
+    T = empty_like_dev(n)
+    flags = api.SCHEME_NEW if scheme == "new" else api.SCHEME_PS
+    prods = h.taylor(to_dev(A), m, s, T, flags)
+    X = np.ldexp(A, -s)
+    c0 = O.product_count()
+    want = O.taylor_new(X, m) if scheme == "new" else O.taylor_ps(X, m)
+    assert prods == O.product_count() - c0          # Table 3 counts, both sides
+    assert rel_fro(to_host(T), want) < 1e-14
+
+
+# ---- whole path, fixed (m, s) and selected -----------------------------------------------------
+
+def test_small_workload_all_schemes(h, api):
+    """64 x 64, N(0,1) from seed 0, ||A||_1 = 1: NEW (18, 0) and PS (16, 1)."""
+    A = W.small_case()
+    for flags, name in ((api.SCHEME_NEW, "new"), (api.SCHEME_PS, "ps")):
+        out = empty_like_dev(64)
+        info = h.expm(to_dev(A), out, 0.0, flags)
+        want, oi = O.expm(A, name)
+        assert (info.m, info.s, info.products) == (oi.m, oi.s, oi.products)
+        assert rel_fro(to_host(out), want) < 1e-13
+    assert (info.m, info.s) == (16, 1)
+
+
+@pytest.mark.parametrize("idx", range(6))
+@pytest.mark.parametrize("n,nonnormal", [(96, False), (257, False), (300, True)])
+def test_expm_selected_matches_oracle(h, api, idx, n, nonnormal):
+    A = W.dense_case(idx, n=n, nonnormal=nonnormal)
+    out = empty_like_dev(n)
+    info = h.expm(to_dev(A), out)
+    want, oi = O.expm(A, "new")
+    assert (info.m, info.s, info.products) == (oi.m, oi.s, oi.products)
+    assert info.norm1 == pytest.approx(oi.norm1, rel=1e-14)
+    assert rel_fro(to_host(out), want) < 1e-12
+
+
+@pytest.mark.parametrize("m,s", [(1, 0), (2, 1), (4, 2), (8, 0), (12, 5), (18, 9)])
+def test_expm_fixed_matches_oracle(h, api, m, s):
+    A = W.gaussian(77, 5 + m, 2.0)
+    out = empty_like_dev(77)
+    info = h.expm_fixed(to_dev(A), out, m, s)
+    want, oi = O.expm(A, "new", m=m, s=s)
+    assert info.products == oi.products and info.selector == 1
+    assert rel_fro(to_host(out), want) < 1e-13
+
+
+def test_expm_host_buffers(h, api):
+    A = W.gaussian(150, 9, 3.0)
+    out = np.empty_like(A)
+    info = h.expm_host(A, out)
+    want, oi = O.expm(A, "new")
+    assert (info.m, info.s) == (oi.m, oi.s)
+    assert rel_fro(out, want) < 1e-12
+
+
+# ---- status codes -------------------------------------------------------------------------------
+
+def test_status_codes(h, api):
+    A = np.eye(9)
+    A[2, 3] = np.nan
+    out = empty_like_dev(9)
+    with pytest.raises(api.BBCError) as e:
+        h.expm(to_dev(A), out)
+    assert e.value.code == api.NONFINITE_INPUT
+    with pytest.raises(api.BBCError) as e:
+        h.expm(to_dev(np.eye(4) * 800.0), empty_like_dev(4))
+    assert e.value.code == api.OVERFLOW
+    Ad = to_dev(np.eye(4))
+    with pytest.raises(api.BBCError) as e:
+        h.expm(Ad, Ad)
+    assert e.value.code == api.INVALID_ARG
+    with pytest.raises(api.BBCError) as e:
+        h.expm_fixed(Ad, empty_like_dev(4), 7, 0)
+    assert e.value.code == api.INVALID_ARG
+    z = empty_like_dev(6)
+    info = h.expm(to_dev(np.zeros((6, 6))), z)
+    assert (to_host(z) == np.eye(6)).all() and info.m == 1
+
+
+# ---- the 4096 x 4096 dense workload at full size -----------------------------------------------
+
+@pytest.mark.parametrize("idx,nonnormal", [(2, False), (5, False), (3, True)])
+def test_dense_4096_full_size(h, api, idx, nonnormal):
+    A = W.dense_case(idx, nonnormal=nonnormal)
+    out = empty_like_dev(A.shape[0])
+    info = h.expm(to_dev(A), out)
+    want, oi = O.expm(A, "new")
+    assert (info.m, info.s) == (oi.m, oi.s)
+    assert rel_fro(to_host(out), want) < 1e-12
