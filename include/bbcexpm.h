@@ -113,6 +113,23 @@ int bbc_expm_fixed(bbc_handle h, const double* dA, int64_t N, double* dOut, int 
 int bbc_expm_host(bbc_handle h, const double* hA, int64_t N, double* hOut, double tol, int flags,
                   void* stream, bbc_info* info);
 
+/* Kernel classes for bbc_profile_read. */
+#define BBC_KERNEL_PRODUCT 0   /* dense products (with fused epilogues) */
+#define BBC_KERNEL_NORM 1      /* the two 1-norm kernels, counted as one class */
+#define BBC_KERNEL_LINCOMB 2   /* product-free linear combinations */
+#define BBC_KERNEL_SPLIT 3     /* Ozaki slice extraction */
+#define BBC_KERNEL_ALL -1
+
+/* Start (enable != 0) or stop per-kernel timing on this handle and reset its
+ * counters. While enabled, every kernel launch of the handle is bracketed by a
+ * pair of CUDA events recorded on the launch's stream. */
+int bbc_profile_enable(bbc_handle h, int enable);
+
+/* Launch count and summed event-measured duration (ms) of one kernel class
+ * since bbc_profile_enable; waits for the recorded events. total_ms may be
+ * NULL. Launches are counted whether or not timing is enabled. */
+int bbc_profile_read(bbc_handle h, int kind, int64_t* launches, double* total_ms);
+
 /* Text of the last error on this thread ("" if none). */
 const char* bbc_last_error(void);
 

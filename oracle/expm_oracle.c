@@ -19,6 +19,9 @@
  * invariants, an independent library). Nothing here is "parity unpinned".
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -40,6 +43,15 @@ enum { ORC_NEW = 0, ORC_PS = 1, ORC_PADE26 = 2 };
 static int g_mutation = 0;
 void orc_set_mutation(int code) { g_mutation = code; }
 int orc_get_mutation(void) { return g_mutation; }
+
+/* threads the products run on (the CPU-baseline leg reports it) */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 static long long g_products = 0;
 long long orc_product_count(void) { return g_products; }

@@ -52,6 +52,7 @@ def lib() -> ctypes.CDLL:
         L.orc_coeffs.argtypes = [ctypes.c_int, dp]
         L.orc_set_mutation.argtypes = [ctypes.c_int]
         L.orc_product_count.restype = ctypes.c_longlong
+        L.orc_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -143,3 +144,7 @@ def set_mutation(code: int) -> None:
 
 def product_count() -> int:
     return lib().orc_product_count()
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()

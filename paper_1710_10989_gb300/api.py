@@ -58,7 +58,10 @@ _SIGS = {
     "bbc_expm": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_fixed": [_vp, _vp, _i64, _vp, _int, _int, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_host": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
+    "bbc_profile_enable": [_vp, _int],
+    "bbc_profile_read": [_vp, _int, ctypes.POINTER(ctypes.c_int64), _dp],
 }
+KERNEL_PRODUCT, KERNEL_NORM, KERNEL_LINCOMB, KERNEL_SPLIT, KERNEL_ALL = 0, 1, 2, 3, -1
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
@@ -121,6 +124,15 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+    def profile_enable(self, enable: bool = True) -> None:
+        _check(_lib.bbc_profile_enable(self._h, int(enable)))
+
+    def profile_read(self, kind: int = KERNEL_ALL) -> tuple[int, float]:
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        _check(_lib.bbc_profile_read(self._h, kind, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
 
     def workspace_size(self, n: int, flags: int = 0) -> int:
         b = ctypes.c_size_t()

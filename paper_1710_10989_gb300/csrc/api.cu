@@ -27,6 +27,12 @@ struct bbc_handle_s {
   void* hstage = nullptr;         // pinned host staging: [0] norm, [1] flag
   void* ozaki = nullptr;          // Ozaki slice workspace
   size_t ozaki_bytes = 0;
+  // profiling: launch counters per kernel class and, when enabled, event pairs
+  int64_t launches[4] = {0, 0, 0, 0};
+  bool prof = false;
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> recs;       // recorded in this profiling window
+  std::vector<cudaEvent_t> pool;
   int64_t io_n = 0;               // N the host-call staging buffers are sized for
   double* io = nullptr;           // 2 * N * N doubles: device copies of hA and hOut
   std::mutex mu;
@@ -167,6 +173,36 @@ int ensure_workspace(bbc_handle h, int64_t N, int flags) {
   return BBC_OK;
 }
 
+cudaEvent_t take_event(bbc_handle h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Brackets one kernel launch: counts it and, if profiling, records events.
+struct LaunchScope {
+  bbc_handle h;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  LaunchScope(bbc_handle h_, int kind_, cudaStream_t st_) : h(h_), kind(kind_), st(st_) {
+    h->launches[kind] += (kind == BBC_KERNEL_NORM) ? 2 : 1;
+    if (h->prof && (a = take_event(h))) cudaEventRecord(a, st);
+  }
+  ~LaunchScope() {
+    if (!a) return;
+    cudaEvent_t b = take_event(h);
+    if (!b) { h->pool.push_back(a); return; }
+    cudaEventRecord(b, st);
+    h->recs.push_back({kind, a, b});
+  }
+};
+
 double* slot_ptr(bbc_handle h, int slot, int64_t N, const double* A, double* T) {
   if (slot == SL_A) return const_cast<double*>(A);
   if (slot == SL_T) return T;
@@ -199,6 +235,7 @@ int run_step(bbc_handle h, const StepS& st, int64_t N, const double* A, double* 
     }
   }
   cudaError_t err;
+  LaunchScope scope(h, st.P < 0 ? BBC_KERNEL_LINCOMB : BBC_KERNEL_PRODUCT, stream);
   if (st.P < 0) {
     err = lincomb(N, e, stream);
   } else {
@@ -277,7 +314,11 @@ int begin(bbc_handle h) {
 }
 
 int read_norm(bbc_handle h, const double* A, int64_t N, cudaStream_t st, double* norm) {
-  cudaError_t e = bbc::norm1(A, N, h->partial, h->dnorm, st);
+  cudaError_t e;
+  {
+    LaunchScope scope(h, BBC_KERNEL_NORM, st);
+    e = bbc::norm1(A, N, h->partial, h->dnorm, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "norm1");
   double* hs = (double*)h->hstage;
   BBC_CUDA(cudaMemcpyAsync(hs, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -329,6 +370,8 @@ int bbc_destroy(bbc_handle h) {
   cudaFree(h->dflag);
   cudaFree(h->ozaki);
   cudaFree(h->io);
+  for (auto& r : h->recs) { h->pool.push_back(r.a); h->pool.push_back(r.b); }
+  for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   if (h->hstage) cudaFreeHost(h->hstage);
   delete h;
   return BBC_OK;
@@ -345,6 +388,40 @@ int bbc_workspace_size(bbc_handle h, int64_t N, int dtype, int flags, size_t* by
     b += ozaki_workspace_bytes(N, k ? k : 7);
   }
   *bytes = b;
+  return BBC_OK;
+}
+
+int bbc_profile_enable(bbc_handle h, int enable) {
+  int rc = begin(h);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  for (auto& r : h->recs) { h->pool.push_back(r.a); h->pool.push_back(r.b); }
+  h->recs.clear();
+  for (auto& l : h->launches) l = 0;
+  h->prof = enable != 0;
+  return BBC_OK;
+}
+
+int bbc_profile_read(bbc_handle h, int kind, int64_t* launches, double* total_ms) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!launches || kind < -1 || kind > 3) return fail(BBC_INVALID_ARG, "bad profile query");
+  std::lock_guard<std::mutex> lk(h->mu);
+  int64_t n = 0;
+  for (int k = 0; k < 4; ++k)
+    if (kind == -1 || kind == k) n += h->launches[k];
+  *launches = n;
+  if (total_ms) {
+    double ms = 0.0;
+    for (auto& r : h->recs) {
+      if (kind != -1 && r.kind != kind) continue;
+      BBC_CUDA(cudaEventSynchronize(r.b));
+      float t = 0.f;
+      BBC_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+      ms += t;
+    }
+    *total_ms = ms;
+  }
   return BBC_OK;
 }
 
@@ -385,6 +462,7 @@ int bbc_gemm(bbc_handle h, const double* dP, const double* dQ, int64_t N, double
   e.o[0].out = dC;
   e.o[0].cv = 1.0;
   cudaError_t err;
+  LaunchScope scope(h, BBC_KERNEL_PRODUCT, (cudaStream_t)stream);
   if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
     const int k = (flags >> 8) & 0xF;
     err = gemm_ozaki(dP, dQ, N, 1.0, e, k ? k : 7, h->ozaki, (cudaStream_t)stream);

@@ -1,0 +1,50 @@
+"""Run one kernel class of libbbcexpm.so on a synthetic case, for profilers.
+
+    python -m paper_1710_10989_gb300.profile_case --kernel gemm --n 4096 --reps 2
+    python -m paper_1710_10989_gb300.profile_case --kernel expm --n 1024 --norm 5
+
+Inputs are seeded Gaussians; nothing is checked (the test suite does that).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel", choices=("gemm", "expm", "norm"), default="gemm")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--norm", type=float, default=1.0)
+    ap.add_argument("--precision", choices=("fp64", "ozaki"), default="fp64")
+    ap.add_argument("--slices", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=1)
+    a = ap.parse_args()
+
+    import torch
+
+    from paper_1710_10989_gb300 import api
+    from paper_1710_10989_gb300 import workloads as W
+
+    flags = api.PREC_FP64 if a.precision == "fp64" else api.PREC_OZAKI | api.ozaki_slices(a.slices)
+    h = api.Handle(0)
+    A = torch.from_numpy(W.gaussian(a.n, 1, a.norm)).cuda()
+    B = torch.from_numpy(W.gaussian(a.n, 2, a.norm)).cuda()
+    C = torch.empty_like(A)
+    for _ in range(a.reps):
+        if a.kernel == "gemm":
+            h.gemm(A, B, C, flags)
+        elif a.kernel == "norm":
+            h.norm1(A)
+        else:
+            h.expm(A, C, 0.0, api.SCHEME_NEW | flags)
+    torch.cuda.synchronize()
+    h.close()
+    print("done", a)
+
+
+if __name__ == "__main__":
+    main()
