@@ -73,8 +73,20 @@ class ClockSampler:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
+        self.others_before = -1
+
+    def other_compute_apps(self) -> int:
+        """Compute processes on this GPU other than this one (GPU sharing check)."""
+        try:
+            out = subprocess.run(["nvidia-smi", "--query-compute-apps=pid", "--format=csv,noheader",
+                                  "-i", str(self.device)], capture_output=True, text=True, timeout=10).stdout
+        except (FileNotFoundError, OSError, subprocess.TimeoutExpired):
+            return -1
+        pids = [p.strip() for p in out.splitlines() if p.strip().isdigit()]
+        return sum(1 for p in pids if int(p) != os.getpid())
 
     def start(self):
+        self.others_before = self.other_compute_apps()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
@@ -108,7 +120,8 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+                "reasons": sorted(reasons),
+                "other_compute_apps": max(self.others_before, self.other_compute_apps())}
 
 
 def peaks():
