@@ -88,7 +88,9 @@ int bbc_select(double norm1, double u, int scheme, int* m, int* s);
  * memory *hNorm (waits for the stream). */
 int bbc_norm1(bbc_handle h, const double* dA, int64_t N, void* stream, double* hNorm);
 
-/* dC = dP * dQ (one dense product) with the precision in `flags`. */
+/* dC = dP * dQ (one dense product) with the precision in `flags`. With
+ * BBC_PREC_OZAKI the call waits for the stream and reports a non-finite
+ * operand (BBC_OVERFLOW) or an expired device wait (BBC_TIMEOUT). */
 int bbc_gemm(bbc_handle h, const double* dP, const double* dQ, int64_t N, double* dC,
              int flags, void* stream);
 

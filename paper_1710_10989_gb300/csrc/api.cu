@@ -243,7 +243,7 @@ int run_step(bbc_handle h, const StepS& st, int64_t N, const double* A, double* 
     const double* Q = slot_ptr(h, st.Q, N, A, T);
     if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
       const int k = (flags >> 8) & 0xF;
-      err = gemm_ozaki(P, Q, N, st.alpha, e, k ? k : 7, h->ozaki, stream);
+      err = gemm_ozaki(P, Q, N, st.alpha, e, k ? k : 7, h->ozaki, h->dflag, stream);
     } else {
       err = gemm_f64(P, Q, N, st.alpha, e, stream);
     }
@@ -331,7 +331,7 @@ int finish_status(bbc_handle h, cudaStream_t st, int* status) {
   unsigned int* hf = (unsigned int*)((double*)h->hstage + 1);
   BBC_CUDA(cudaMemcpyAsync(hf, h->dflag, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   BBC_CUDA(cudaStreamSynchronize(st));
-  *status = (*hf != 0) ? BBC_OVERFLOW : BBC_OK;
+  *status = (*hf & 2u) ? BBC_TIMEOUT : (*hf != 0) ? BBC_OVERFLOW : BBC_OK;
   return BBC_OK;
 }
 
@@ -462,14 +462,24 @@ int bbc_gemm(bbc_handle h, const double* dP, const double* dQ, int64_t N, double
   e.o[0].out = dC;
   e.o[0].cv = 1.0;
   cudaError_t err;
-  LaunchScope scope(h, BBC_KERNEL_PRODUCT, (cudaStream_t)stream);
-  if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
-    const int k = (flags >> 8) & 0xF;
-    err = gemm_ozaki(dP, dQ, N, 1.0, e, k ? k : 7, h->ozaki, (cudaStream_t)stream);
-  } else {
-    err = gemm_f64(dP, dQ, N, 1.0, e, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool ozaki = (flags & BBC_PREC_MASK) == BBC_PREC_OZAKI;
+  if (ozaki) BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
+  {
+    LaunchScope scope(h, BBC_KERNEL_PRODUCT, st);
+    if (ozaki) {
+      const int k = (flags >> 8) & 0xF;
+      err = gemm_ozaki(dP, dQ, N, 1.0, e, k ? k : 7, h->ozaki, h->dflag, st);
+    } else {
+      err = gemm_f64(dP, dQ, N, 1.0, e, st);
+    }
   }
   if (err != cudaSuccess) return cuda_fail(err, "gemm");
+  if (ozaki) {  // report a non-finite operand or an expired device wait
+    int status = BBC_OK;
+    if ((rc = finish_status(h, st, &status))) return rc;
+    if (status) return fail(status, status == BBC_TIMEOUT ? "device wait timed out" : "non-finite operand");
+  }
   return BBC_OK;
 }
 

@@ -62,11 +62,12 @@ cudaError_t lincomb(int64_t N, const Epilogue& e, cudaStream_t st);
 int64_t norm1_partial_len(int64_t N);
 cudaError_t norm1(const double* A, int64_t N, double* partial, double* dNorm, cudaStream_t st);
 
-// Ozaki split products on tcgen05 (gemm_ozaki.cu).
-struct OzakiWork;  // opaque, owned by the handle
+// Ozaki split products on tcgen05 (gemm_ozaki.cu). `flag` is the handle's
+// status word: bit 0 = an operand held a non-finite value, bit 1 = a bounded
+// device wait expired.
 size_t ozaki_workspace_bytes(int64_t N, int slices);
 cudaError_t gemm_ozaki(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
-                       int slices, void* work, cudaStream_t st);
+                       int slices, void* work, unsigned int* flag, cudaStream_t st);
 bool ozaki_supported(int64_t N);
 
 }  // namespace bbc

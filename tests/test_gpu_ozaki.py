@@ -1,0 +1,112 @@
+"""GPU parity, split-precision path: products rebuilt exactly from BF16 slices on
+the tcgen05 tensor cores, checked against the oracle's FP64 products and, for
+small-integer operands, against the exact integer product."""
+import numpy as np
+import pytest
+
+from gpu_util import empty_like_dev, rel_fro, to_dev, to_host
+from oracle import oracle as O
+from paper_1710_10989_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_10989_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def h(api):
+    hh = api.Handle(0)
+    yield hh
+    hh.close()
+
+
+def oz(api, k=7):
+    return api.PREC_OZAKI | api.ozaki_slices(k)
+
+
+@pytest.mark.parametrize("n", [128, 1, 5, 64, 200, 256, 257, 1100, 2048])
+def test_integer_operands_are_exact(h, api, n):
+    # entries in [-127, 127] times a power of two per row / column: two slices hold
+    # them exactly, so the product must be exact (it fits FP64 exactly as well)
+    rng = np.random.default_rng(n)
+    P = rng.integers(-127, 128, size=(n, n)).astype(np.float64) * np.ldexp(1.0, rng.integers(-5, 5, size=(n, 1)))
+    Q = rng.integers(-127, 128, size=(n, n)).astype(np.float64) * np.ldexp(1.0, rng.integers(-5, 5, size=(1, n)))
+    C = empty_like_dev(n)
+    h.gemm(to_dev(P), to_dev(Q), C, oz(api, 2))
+    exact = O.gemm(P, Q)  # every partial sum is an exact binary64 value here
+    assert np.array_equal(to_host(C), exact)
+
+
+@pytest.mark.parametrize("n", [1, 7, 64, 128, 255, 256, 300, 1025])
+def test_gemm_matches_oracle(h, api, n):
+    P = W.gaussian(n, 3 + n, None)
+    Q = W.gaussian(n, 4 + n, None)
+    C = empty_like_dev(n)
+    h.gemm(to_dev(P), to_dev(Q), C, oz(api, 7))
+    assert rel_fro(to_host(C), O.gemm(P, Q)) < 4e-16 * max(4, np.sqrt(n))
+
+
+def test_error_falls_with_slices(h, api):
+    n = 384
+    P = W.gaussian(n, 31, None)
+    Q = W.gaussian(n, 32, None)
+    ref = O.gemm(P, Q)
+    errs = []
+    for k in (2, 3, 4, 5, 6, 7, 8):
+        C = empty_like_dev(n)
+        h.gemm(to_dev(P), to_dev(Q), C, oz(api, k))
+        errs.append(rel_fro(to_host(C), ref))
+    # about 8 bits per extra slice until FP64 rounding is reached
+    for k, (a, b) in enumerate(zip(errs, errs[1:]), start=2):
+        if a > 1e-13:
+            assert b < a / 50, (k, errs)
+    assert errs[-2] < 1e-15 and errs[-1] < 1e-15, errs
+
+
+def test_wide_dynamic_range_rows(h, api):
+    n = 200
+    rng = np.random.default_rng(5)
+    rs = rng.integers(-300, 300, size=(n, 1))
+    cs = rng.integers(-300, 300, size=(1, n))
+    P0 = rng.standard_normal((n, n))
+    Q0 = rng.standard_normal((n, n))
+    C = empty_like_dev(n)
+    h.gemm(to_dev(np.ldexp(P0, rs)), to_dev(np.ldexp(Q0, cs)), C, oz(api, 7))
+    # row i / column j scales are exact powers of two: remove them and compare
+    got = np.ldexp(to_host(C), -(rs + cs))
+    assert rel_fro(got, O.gemm(P0, Q0)) < 4e-15
+
+
+def test_nonfinite_operand_reported(h, api):
+    P = np.eye(130)
+    P[3, 4] = np.inf
+    C = empty_like_dev(130)
+    with pytest.raises(api.BBCError) as e:
+        h.gemm(to_dev(P), to_dev(np.eye(130)), C, oz(api, 7))
+    assert e.value.code == api.OVERFLOW
+
+
+@pytest.mark.parametrize("idx", range(6))
+@pytest.mark.parametrize("n,nonnormal", [(192, False), (300, True)])
+def test_expm_split_matches_oracle(h, api, idx, n, nonnormal):
+    A = W.dense_case(idx, n=n, nonnormal=nonnormal)
+    out = empty_like_dev(n)
+    info = h.expm(to_dev(A), out, 0.0, api.SCHEME_NEW | oz(api, 7))
+    want, oi = O.expm(A, "new")
+    assert (info.m, info.s, info.products) == (oi.m, oi.s, oi.products)
+    assert rel_fro(to_host(out), want) < 1e-12
+
+
+def test_small_workload_split(h, api):
+    A = W.small_case()
+    out = empty_like_dev(64)
+    h.expm(to_dev(A), out, 0.0, api.SCHEME_NEW | oz(api, 7))
+    want, _ = O.expm(A, "new")
+    assert rel_fro(to_host(out), want) < 1e-13
