@@ -36,6 +36,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("fp64", "ozaki"), default="fp64")
+    ap.add_argument("--slices", type=int, default=0, help="BF16 slices for --precision ozaki (0 = 7)")
     ap.add_argument("--n", type=int, default=W.DENSE_N, help="matrix size (default: the 4096 workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -197,7 +198,8 @@ def main():
         dist.barrier()
     from paper_1710_10989_gb300 import api
 
-    flags = api.SCHEME_NEW | (api.PREC_FP64 if args.precision == "fp64" else api.PREC_OZAKI)
+    flags = api.SCHEME_NEW | (api.PREC_FP64 if args.precision == "fp64"
+                              else api.PREC_OZAKI | api.ozaki_slices(args.slices))
     mats, names = workload(args.n)
     n = args.n
     prods = products_per_matrix(mats)
@@ -234,6 +236,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     launches, _ = h.profile_read(api.KERNEL_ALL)
     prod_launches, prod_ms = h.profile_read(api.KERNEL_PRODUCT)
+    split_launches, split_ms = h.profile_read(api.KERNEL_SPLIT)
+    norm_launches, norm_ms = h.profile_read(api.KERNEL_NORM)
     h.profile_enable(False)
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -274,9 +278,19 @@ def main():
                 "peak_source": "FP64 pipe, 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
                 "avg_launch_ms": avg_ms, "launches": prod_launches}
     else:
-        peak = pk.get("bf16_tflops", 1900.0)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_ms, "launches": prod_launches}
+        # the tcgen05 kernel executes k(k+1)/2 BF16 slice products per FP64 product
+        slices = args.slices or 7
+        pairs = slices * (slices + 1) // 2
+        executed = pairs * flops_per_product / (avg_ms / 1e3) / 1e12
+        peak = pk.get("bf16_tflops", 1899.1)
+        roof = {"bound": "tensor", "achieved": executed, "peak": peak, "unit": "TFLOP/s",
+                "frac": executed / peak, "traffic": None,
+                "kernel": f"k_ozaki_gemm ({slices} BF16 slices, {pairs} slice products per FP64 product)",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS)" if "bf16_tflops" in pk
+                               else "fallback 1.9 PFLOP/s bf16",
+                "flops_per_launch": pairs * flops_per_product, "avg_launch_ms": avg_ms,
+                "launches": prod_launches, "logical_fp64_tflops": achieved,
+                "split_kernels_ms_per_product": split_ms / max(1, split_launches / 3)}
 
     if rank == 0:
         cpu = None
@@ -296,6 +310,8 @@ def main():
                        "l2": "inputs larger than L2 (each exp(A) streams ~10 N^2 FP64 buffers of "
                              f"{n * n * 8 / 2 ** 20:.0f} MiB)"},
             "tflops_logical": sum(prods) * flops_per_product * args.steps * world / (ms_max / 1e3) / 1e12,
+            "time_share": {"product_ms": prod_ms, "split_ms": split_ms, "norm_ms": norm_ms,
+                           "timed_ms": ms},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk,
         }

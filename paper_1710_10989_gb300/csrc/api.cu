@@ -10,7 +10,7 @@
 #include <utility>
 #include <vector>
 
-#include "../../include/bbcexpm.h"
+#include "bbcexpm.h"
 #include "internal.h"
 #include "schemes.h"
 
@@ -191,7 +191,8 @@ struct LaunchScope {
   cudaStream_t st;
   cudaEvent_t a = nullptr;
   LaunchScope(bbc_handle h_, int kind_, cudaStream_t st_) : h(h_), kind(kind_), st(st_) {
-    h->launches[kind] += (kind == BBC_KERNEL_NORM) ? 2 : 1;
+    // the 1-norm is two kernels; a split is three (row split, column maxima, column split)
+    h->launches[kind] += (kind == BBC_KERNEL_NORM) ? 2 : (kind == BBC_KERNEL_SPLIT) ? 3 : 1;
     if (h->prof && (a = take_event(h))) cudaEventRecord(a, st);
   }
   ~LaunchScope() {
@@ -207,6 +208,27 @@ double* slot_ptr(bbc_handle h, int slot, int64_t N, const double* A, double* T) 
   if (slot == SL_A) return const_cast<double*>(A);
   if (slot == SL_T) return T;
   return h->work + (size_t)slot * N * N;
+}
+
+// One dense product alpha * (P Q) with its fused epilogue, at the precision in flags.
+int launch_product(bbc_handle h, const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
+                   int flags, cudaStream_t stream) {
+  cudaError_t err;
+  if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
+    const int k = ((flags >> 8) & 0xF) ? ((flags >> 8) & 0xF) : 7;
+    {
+      LaunchScope scope(h, BBC_KERNEL_SPLIT, stream);
+      err = ozaki_split(P, Q, N, k, h->ozaki, h->dflag, stream);
+    }
+    if (err != cudaSuccess) return cuda_fail(err, "split launch");
+    LaunchScope scope(h, BBC_KERNEL_PRODUCT, stream);
+    err = ozaki_product(N, alpha, e, k, h->ozaki, h->dflag, stream);
+  } else {
+    LaunchScope scope(h, BBC_KERNEL_PRODUCT, stream);
+    err = gemm_f64(P, Q, N, alpha, e, stream);
+  }
+  if (err != cudaSuccess) return cuda_fail(err, "product launch");
+  return BBC_OK;
 }
 
 // One product (or linear combination) with its fused epilogue.
@@ -234,22 +256,15 @@ int run_step(bbc_handle h, const StepS& st, int64_t N, const double* A, double* 
       e.o[o].c[t] = q.t[t].c;
     }
   }
-  cudaError_t err;
-  LaunchScope scope(h, st.P < 0 ? BBC_KERNEL_LINCOMB : BBC_KERNEL_PRODUCT, stream);
   if (st.P < 0) {
-    err = lincomb(N, e, stream);
-  } else {
-    const double* P = slot_ptr(h, st.P, N, A, T);
-    const double* Q = slot_ptr(h, st.Q, N, A, T);
-    if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
-      const int k = (flags >> 8) & 0xF;
-      err = gemm_ozaki(P, Q, N, st.alpha, e, k ? k : 7, h->ozaki, h->dflag, stream);
-    } else {
-      err = gemm_f64(P, Q, N, st.alpha, e, stream);
-    }
+    LaunchScope scope(h, BBC_KERNEL_LINCOMB, stream);
+    const cudaError_t err = lincomb(N, e, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "lincomb launch");
+    return BBC_OK;
   }
-  if (err != cudaSuccess) return cuda_fail(err, "kernel launch");
-  return BBC_OK;
+  const double* P = slot_ptr(h, st.P, N, A, T);
+  const double* Q = slot_ptr(h, st.Q, N, A, T);
+  return launch_product(h, P, Q, N, st.alpha, e, flags, stream);
 }
 
 int check_flags(int flags) {
@@ -461,20 +476,10 @@ int bbc_gemm(bbc_handle h, const double* dP, const double* dQ, int64_t N, double
   e.nout = 1;
   e.o[0].out = dC;
   e.o[0].cv = 1.0;
-  cudaError_t err;
   cudaStream_t st = (cudaStream_t)stream;
   const bool ozaki = (flags & BBC_PREC_MASK) == BBC_PREC_OZAKI;
   if (ozaki) BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
-  {
-    LaunchScope scope(h, BBC_KERNEL_PRODUCT, st);
-    if (ozaki) {
-      const int k = (flags >> 8) & 0xF;
-      err = gemm_ozaki(dP, dQ, N, 1.0, e, k ? k : 7, h->ozaki, h->dflag, st);
-    } else {
-      err = gemm_f64(dP, dQ, N, 1.0, e, st);
-    }
-  }
-  if (err != cudaSuccess) return cuda_fail(err, "gemm");
+  if ((rc = launch_product(h, dP, dQ, N, 1.0, e, flags, st))) return rc;
   if (ozaki) {  // report a non-finite operand or an expired device wait
     int status = BBC_OK;
     if ((rc = finish_status(h, st, &status))) return rc;

@@ -631,37 +631,57 @@ size_t ozaki_workspace_bytes(int64_t N, int slices) {
   return 256 + 3 * (size_t)Rp * sizeof(int) + 256 + 2 * (size_t)slices * Rp * Rp * 2;
 }
 
-cudaError_t gemm_ozaki(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e, int slices,
-                       void* work, unsigned int* flag, cudaStream_t st) {
-  if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
-  const int64_t Rp = padded(N);
+namespace {
+struct OzLayout {
+  int64_t Rp;
+  int* erow;
+  int* fcol;
+  int* fexp;
+  uint16_t* Ps;
+  uint16_t* Qs;
+};
+OzLayout layout(void* work, int64_t N, int slices) {
+  OzLayout L;
+  L.Rp = padded(N);
   uint8_t* w = static_cast<uint8_t*>(work);
-  int* erow = reinterpret_cast<int*>(w + 256);
-  int* fcol = erow + Rp;
-  int* fexp = fcol + Rp;
-  size_t off = 256 + 3 * (size_t)Rp * sizeof(int);
+  L.erow = reinterpret_cast<int*>(w + 256);
+  L.fcol = L.erow + L.Rp;
+  L.fexp = L.fcol + L.Rp;
+  size_t off = 256 + 3 * (size_t)L.Rp * sizeof(int);
   off = (off + 255) / 256 * 256;
-  uint16_t* Ps = reinterpret_cast<uint16_t*>(w + off);
-  uint16_t* Qs = Ps + (size_t)slices * Rp * Rp;
-  cudaError_t err;
-  switch (slices) {
-    case 2: err = split_both<2>(P, Q, N, Rp, Ps, Qs, erow, fcol, fexp, flag, st); break;
-    case 3: err = split_both<3>(P, Q, N, Rp, Ps, Qs, erow, fcol, fexp, flag, st); break;
-    case 4: err = split_both<4>(P, Q, N, Rp, Ps, Qs, erow, fcol, fexp, flag, st); break;
-    case 5: err = split_both<5>(P, Q, N, Rp, Ps, Qs, erow, fcol, fexp, flag, st); break;
-    case 6: err = split_both<6>(P, Q, N, Rp, Ps, Qs, erow, fcol, fexp, flag, st); break;
-    case 7: err = split_both<7>(P, Q, N, Rp, Ps, Qs, erow, fcol, fexp, flag, st); break;
-    default: err = split_both<8>(P, Q, N, Rp, Ps, Qs, erow, fcol, fexp, flag, st); break;
-  }
-  if (err != cudaSuccess) return err;
+  L.Ps = reinterpret_cast<uint16_t*>(w + off);
+  L.Qs = L.Ps + (size_t)slices * L.Rp * L.Rp;
+  return L;
+}
+}  // namespace
 
+cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices, void* work, unsigned int* flag,
+                        cudaStream_t st) {
+  if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
+  const OzLayout L = layout(work, N, slices);
+  switch (slices) {
+    case 2: return split_both<2>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
+    case 3: return split_both<3>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
+    case 4: return split_both<4>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
+    case 5: return split_both<5>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
+    case 6: return split_both<6>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
+    case 7: return split_both<7>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
+    default: return split_both<8>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
+  }
+}
+
+cudaError_t ozaki_product(int64_t N, double alpha, const Epilogue& e, int slices, void* work, unsigned int* flag,
+                          cudaStream_t st) {
+  if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
+  const OzLayout L = layout(work, N, slices);
   CUtensorMap ta, tb;
-  if (!make_map(&ta, Ps, Rp, Rp, slices) || !make_map(&tb, Qs, Rp, Rp, slices)) return cudaErrorNotSupported;
-  err = cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  if (!make_map(&ta, L.Ps, L.Rp, L.Rp, slices) || !make_map(&tb, L.Qs, L.Rp, L.Rp, slices))
+    return cudaErrorNotSupported;
+  cudaError_t err = cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   if (err != cudaSuccess) return err;
-  const dim3 grid((unsigned)(Rp / TILE), (unsigned)(Rp / TILE));
-  k_ozaki_gemm<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ta, tb, erow, fcol, N, alpha, slices, (int)(Rp / KSTEP), e,
-                                                      flag);
+  const dim3 grid((unsigned)(L.Rp / TILE), (unsigned)(L.Rp / TILE));
+  k_ozaki_gemm<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ta, tb, L.erow, L.fcol, N, alpha, slices, (int)(L.Rp / KSTEP),
+                                                      e, flag);
   return cudaGetLastError();
 }
 

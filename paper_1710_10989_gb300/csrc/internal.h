@@ -65,9 +65,14 @@ cudaError_t norm1(const double* A, int64_t N, double* partial, double* dNorm, cu
 // Ozaki split products on tcgen05 (gemm_ozaki.cu). `flag` is the handle's
 // status word: bit 0 = an operand held a non-finite value, bit 1 = a bounded
 // device wait expired.
+// ozaki_split writes the slice planes and scales of P (rows) and Q (columns)
+// into `work`; ozaki_product then forms alpha * (P Q) from them with the
+// fused epilogue.
 size_t ozaki_workspace_bytes(int64_t N, int slices);
-cudaError_t gemm_ozaki(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
-                       int slices, void* work, unsigned int* flag, cudaStream_t st);
+cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices, void* work,
+                        unsigned int* flag, cudaStream_t st);
+cudaError_t ozaki_product(int64_t N, double alpha, const Epilogue& e, int slices, void* work,
+                          unsigned int* flag, cudaStream_t st);
 bool ozaki_supported(int64_t N);
 
 }  // namespace bbc

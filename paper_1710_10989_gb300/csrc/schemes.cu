@@ -9,7 +9,7 @@
 // analogous T4, T6 (blocks in A2) and T12 (blocks in A3).
 #include <cmath>
 
-#include "../../include/bbcexpm.h"
+#include "bbcexpm.h"
 #include "schemes.h"
 
 namespace bbc {
