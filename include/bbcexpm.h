@@ -88,6 +88,23 @@ int bbc_select(double norm1, double u, int scheme, int* m, int* s);
  * memory *hNorm (waits for the stream). */
 int bbc_norm1(bbc_handle h, const double* dA, int64_t N, void* stream, double* hNorm);
 
+/* ||A||_1 into device memory, allocating nothing. The paper has no
+ * counterpart: this is a service entry point for callers that must not
+ * allocate device memory at call time, for instance a service whose device
+ * memory is entirely reserved up front by its own pool, or a latency-critical
+ * path where cudaMalloc's implicit synchronisation, or its failure under
+ * memory pressure, cannot be tolerated. It needs no handle.
+ *  dA     device, N x N row-major binary64 (read only)
+ *  dNorm  device, one double; receives ||A||_1 (cleared by the call itself)
+ *  N      1 <= N <= 65536; larger N returns BBC_INVALID_ARG before any work
+ * Scratch: a fixed 1 MiB array compiled into the library (held on every GPU
+ * that loads it until the process exits). The first call on each device looks
+ * up that array's device address (with the device current), so make the first
+ * call on a device before any stream capture. All calls share the array:
+ * calls that may overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller. Returns without waiting for the stream. */
+int bbc_norm1_noalloc(const double* dA, int64_t N, double* dNorm, void* stream);
+
 /* dC = dP * dQ (one dense product) with the precision in `flags`. With
  * BBC_PREC_OZAKI the call waits for the stream and reports a non-finite
  * operand (BBC_OVERFLOW) or an expired device wait (BBC_TIMEOUT). */

@@ -53,6 +53,7 @@ _SIGS = {
     "bbc_theta": [_int, _dbl, _dp],
     "bbc_select": [_dbl, _dbl, _int, _ip, _ip],
     "bbc_norm1": [_vp, _vp, _i64, _vp, _dp],
+    "bbc_norm1_noalloc": [_vp, _i64, _vp, _vp],
     "bbc_gemm": [_vp, _vp, _vp, _i64, _vp, _int, _vp],
     "bbc_taylor": [_vp, _vp, _i64, _int, _int, _vp, _int, _vp, _ip],
     "bbc_expm": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
@@ -89,6 +90,22 @@ def select(norm1: float, u: float = U_DOUBLE, scheme: int = SCHEME_NEW) -> tuple
     m, s = ctypes.c_int(), ctypes.c_int()
     _check(_lib.bbc_select(norm1, u, scheme, ctypes.byref(m), ctypes.byref(s)))
     return m.value, s.value
+
+
+def norm1_noalloc(A, out, stream=None) -> None:
+    """||A||_1 into the one-element float64 CUDA tensor `out`, allocating no
+    device memory (no handle needed). For callers that must not allocate at
+    call time; see bbc_norm1_noalloc in include/bbcexpm.h for the limits."""
+    pa, n = _mat(A, "A")
+    import torch
+    if not (out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1):
+        raise ValueError("out: need a float64 CUDA tensor with at least one element")
+    _check(_lib.bbc_norm1_noalloc(pa, n, out.data_ptr(), _stream(stream)))
+
+
+def norm1_noalloc_raw(a_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None:
+    """Same entry point with raw device pointers (no tensor checks)."""
+    _check(_lib.bbc_norm1_noalloc(a_ptr, n, out_ptr, stream))
 
 
 def _stream(stream) -> int:

@@ -463,6 +463,16 @@ int bbc_norm1(bbc_handle h, const double* dA, int64_t N, void* stream, double* h
   return read_norm(h, dA, N, (cudaStream_t)stream, hNorm);
 }
 
+int bbc_norm1_noalloc(const double* dA, int64_t N, double* dNorm, void* stream) {
+  g_err.clear();
+  if (N <= 0 || !norm1_noalloc_fits(N))
+    return fail(BBC_INVALID_ARG, "bbc_norm1_noalloc: N must be in 1..65536 (fixed 1 MiB scratch)");
+  if (!dA || !dNorm) return fail(BBC_INVALID_ARG, "bbc_norm1_noalloc: null pointer");
+  const cudaError_t e = norm1_noalloc(dA, N, dNorm, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bbc_norm1_noalloc");
+  return BBC_OK;
+}
+
 int bbc_gemm(bbc_handle h, const double* dP, const double* dQ, int64_t N, double* dC, int flags,
              void* stream) {
   int rc = begin(h);

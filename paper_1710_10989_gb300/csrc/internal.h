@@ -62,6 +62,11 @@ cudaError_t lincomb(int64_t N, const Epilogue& e, cudaStream_t st);
 int64_t norm1_partial_len(int64_t N);
 cudaError_t norm1(const double* A, int64_t N, double* partial, double* dNorm, cudaStream_t st);
 
+// ||A||_1 with the slab sums in a static device array instead of a workspace
+// (no allocation); false / cudaErrorInvalidValue when N exceeds its capacity.
+bool norm1_noalloc_fits(int64_t N);
+cudaError_t norm1_noalloc(const double* A, int64_t N, double* dNorm, cudaStream_t st);
+
 // Ozaki split products on tcgen05 (gemm_ozaki.cu). `flag` is the handle's
 // status word: bit 0 = an operand held a non-finite value, bit 1 = a bounded
 // device wait expired.
