@@ -132,11 +132,42 @@ int bbc_expm_fixed(bbc_handle h, const double* dA, int64_t N, double* dOut, int 
 int bbc_expm_host(bbc_handle h, const double* hA, int64_t N, double* hOut, double tol, int flags,
                   void* stream, bbc_info* info);
 
+/* Element types of bbc_expm_batched. */
+#define BBC_DTYPE_F64 0
+#define BBC_DTYPE_F32 1
+
+/* Reserve the device workspace bbc_expm_batched needs for matrices up to
+ * max_n x max_n (1 <= max_n <= 256) with `flags`. Allocates; call it before
+ * any stream capture of bbc_expm_batched. */
+int bbc_batch_reserve(bbc_handle h, int64_t max_n, int flags);
+
+/* Host helper: an order of the `count` matrices with sizes hNs (host array)
+ * that puts the largest first (cost grows as N^3), for the work queue of
+ * bbc_expm_batched (longest-processing-time-first). hOrder: host, count entries. */
+int bbc_batch_order(const int64_t* hNs, int64_t count, int64_t* hOrder);
+
+/* exp(A_i) for `count` independent matrices in one persistent launch (Section 1,
+ * eq. eses, per matrix; (m, s) chosen on the device as in bbc_expm).
+ *  dA, dOut  DEVICE arrays of `count` device pointers; A_i and Out_i are
+ *            N_i x N_i row-major of type dtype (BBC_DTYPE_F32 / F64); the
+ *            work runs in binary64 whatever the storage type.
+ *  dNs       DEVICE array of the `count` sizes N_i (1 <= N_i <= reserved max_n).
+ *  dInfo     DEVICE array of `count` bbc_info (may be NULL): per-matrix m, s,
+ *            products, ||A_i||_1 and status (BBC_INVALID_ARG for an N_i beyond
+ *            the reservation, BBC_NONFINITE_INPUT, BBC_OVERFLOW).
+ * Matrices are taken in array order by whichever CTA is free: put expensive
+ * ones first (bbc_batch_order). Needs bbc_batch_reserve first; performs no
+ * allocation and no host synchronisation (one memset and one kernel on
+ * `stream`), so it can be captured in a CUDA graph. Scheme NEW only. */
+int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, int64_t count, void* const* dOut,
+                     int dtype, double tol, int flags, void* stream, bbc_info* dInfo);
+
 /* Kernel classes for bbc_profile_read. */
 #define BBC_KERNEL_PRODUCT 0   /* dense products (with fused epilogues) */
 #define BBC_KERNEL_NORM 1      /* the two 1-norm kernels, counted as one class */
 #define BBC_KERNEL_LINCOMB 2   /* product-free linear combinations */
 #define BBC_KERNEL_SPLIT 3     /* Ozaki slice extraction */
+#define BBC_KERNEL_BATCHED 4   /* the persistent batched kernel */
 #define BBC_KERNEL_ALL -1
 
 /* Start (enable != 0) or stop per-kernel timing on this handle and reset its

@@ -59,10 +59,14 @@ _SIGS = {
     "bbc_expm": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_fixed": [_vp, _vp, _i64, _vp, _int, _int, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_host": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
+    "bbc_batch_reserve": [_vp, _i64, _int],
+    "bbc_batch_order": [ctypes.POINTER(ctypes.c_int64), _i64, ctypes.POINTER(ctypes.c_int64)],
+    "bbc_expm_batched": [_vp, _vp, _vp, _i64, _vp, _int, _dbl, _int, _vp, _vp],
     "bbc_profile_enable": [_vp, _int],
     "bbc_profile_read": [_vp, _int, ctypes.POINTER(ctypes.c_int64), _dp],
 }
-KERNEL_PRODUCT, KERNEL_NORM, KERNEL_LINCOMB, KERNEL_SPLIT, KERNEL_ALL = 0, 1, 2, 3, -1
+KERNEL_PRODUCT, KERNEL_NORM, KERNEL_LINCOMB, KERNEL_SPLIT, KERNEL_BATCHED, KERNEL_ALL = 0, 1, 2, 3, 4, -1
+DTYPE_F64, DTYPE_F32 = 0, 1
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
@@ -151,6 +155,14 @@ class Handle:
         _check(_lib.bbc_profile_read(self._h, kind, ctypes.byref(n), ctypes.byref(ms)))
         return n.value, ms.value
 
+    def batch_reserve(self, max_n: int, flags: int = 0) -> None:
+        _check(_lib.bbc_batch_reserve(self._h, max_n, flags))
+
+    def expm_batched(self, batch: "Batch", tol: float = 0.0, flags: int = 0, stream=None) -> None:
+        _check(_lib.bbc_expm_batched(self._h, batch.a_ptrs.data_ptr(), batch.ns.data_ptr(), batch.count,
+                                     batch.o_ptrs.data_ptr(), batch.dtype, tol, flags, _stream(stream),
+                                     batch.info.data_ptr()))
+
     def workspace_size(self, n: int, flags: int = 0) -> int:
         b = ctypes.c_size_t()
         _check(_lib.bbc_workspace_size(self._h, n, 0, flags, ctypes.byref(b)))
@@ -196,6 +208,45 @@ class Handle:
         info = Info()
         _check(_lib.bbc_expm_host(self._h, pa, n, po, tol, flags, _stream(stream), ctypes.byref(info)))
         return info
+
+
+def batch_order(ns) -> list[int]:
+    """Largest-first order of matrix sizes (host helper of the batched call)."""
+    import numpy as np
+    a = np.ascontiguousarray(ns, dtype=np.int64)
+    out = np.empty_like(a)
+    _check(_lib.bbc_batch_order(a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(a),
+                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return out.tolist()
+
+
+class Batch:
+    """Device-side descriptor arrays for bbc_expm_batched, built from lists of
+    CUDA tensors (inputs and outputs stay owned by the caller)."""
+
+    def __init__(self, inputs, outputs):
+        import torch
+        if len(inputs) != len(outputs):
+            raise ValueError("inputs and outputs differ in length")
+        dt = inputs[0].dtype if inputs else torch.float32
+        for a, o in zip(inputs, outputs):
+            if not (a.is_cuda and o.is_cuda and a.dtype == dt and o.dtype == dt and a.is_contiguous()
+                    and o.is_contiguous() and a.dim() == 2 and a.shape[0] == a.shape[1] and o.shape == a.shape):
+                raise ValueError("need matching contiguous square CUDA tensors of one dtype")
+        if dt not in (torch.float32, torch.float64):
+            raise ValueError("float32 or float64 only")
+        self.dtype = DTYPE_F32 if dt == torch.float32 else DTYPE_F64
+        self.count = len(inputs)
+        self.ns = torch.tensor([a.shape[0] for a in inputs], dtype=torch.int64, device="cuda")
+        self.a_ptrs = torch.tensor([a.data_ptr() for a in inputs], dtype=torch.int64, device="cuda")
+        self.o_ptrs = torch.tensor([o.data_ptr() for o in outputs], dtype=torch.int64, device="cuda")
+        self.info = torch.zeros((max(1, self.count), ctypes.sizeof(Info) // 8), dtype=torch.float64,
+                                device="cuda")
+
+    def infos(self) -> list[dict]:
+        raw = self.info.cpu().numpy().tobytes()
+        n = ctypes.sizeof(Info)
+        return [Info.from_buffer_copy(raw[i * n:(i + 1) * n]).as_dict() for i in range(self.count)]
 
 
 def _host_ptr(x):

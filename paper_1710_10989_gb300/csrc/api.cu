@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -28,11 +29,14 @@ struct bbc_handle_s {
   void* ozaki = nullptr;          // Ozaki slice workspace
   size_t ozaki_bytes = 0;
   // profiling: launch counters per kernel class and, when enabled, event pairs
-  int64_t launches[4] = {0, 0, 0, 0};
+  int64_t launches[5] = {0, 0, 0, 0, 0};
   bool prof = false;
   struct Rec { int kind; cudaEvent_t a, b; };
   std::vector<Rec> recs;       // recorded in this profiling window
   std::vector<cudaEvent_t> pool;
+  int64_t batch_nmax = 0;         // reservation of the batched workspace
+  int batch_ctas = 0;
+  void* batch_work = nullptr;
   int64_t io_n = 0;               // N the host-call staging buffers are sized for
   double* io = nullptr;           // 2 * N * N doubles: device copies of hA and hOut
   std::mutex mu;
@@ -385,6 +389,7 @@ int bbc_destroy(bbc_handle h) {
   cudaFree(h->dflag);
   cudaFree(h->ozaki);
   cudaFree(h->io);
+  cudaFree(h->batch_work);
   for (auto& r : h->recs) { h->pool.push_back(r.a); h->pool.push_back(r.b); }
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   if (h->hstage) cudaFreeHost(h->hstage);
@@ -420,10 +425,10 @@ int bbc_profile_enable(bbc_handle h, int enable) {
 int bbc_profile_read(bbc_handle h, int kind, int64_t* launches, double* total_ms) {
   int rc = begin(h);
   if (rc) return rc;
-  if (!launches || kind < -1 || kind > 3) return fail(BBC_INVALID_ARG, "bad profile query");
+  if (!launches || kind < -1 || kind > 4) return fail(BBC_INVALID_ARG, "bad profile query");
   std::lock_guard<std::mutex> lk(h->mu);
   int64_t n = 0;
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 5; ++k)
     if (kind == -1 || kind == k) n += h->launches[k];
   *launches = n;
   if (total_ms) {
@@ -596,6 +601,61 @@ int bbc_expm_host(bbc_handle h, const double* hA, int64_t N, double* hOut, doubl
   if (rc) return rc;
   BBC_CUDA(cudaMemcpyAsync(hOut, dOut, bytes, cudaMemcpyDeviceToHost, st));
   BBC_CUDA(cudaStreamSynchronize(st));
+  return BBC_OK;
+}
+
+int bbc_batch_reserve(bbc_handle h, int64_t max_n, int flags) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (max_n < 1 || max_n > 256) return fail(BBC_INVALID_ARG, "batched max_n must be in 1..256");
+  if ((rc = check_flags(flags))) return rc;
+  if ((flags & BBC_SCHEME_MASK) != BBC_SCHEME_NEW || (flags & BBC_PREC_MASK) != BBC_PREC_FP64)
+    return fail(BBC_UNSUPPORTED, "batched path: scheme NEW with FP64 products only");
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (max_n > h->batch_nmax) {
+    if (h->batch_work) BBC_CUDA(cudaFree(h->batch_work));
+    h->batch_work = nullptr;
+    h->batch_nmax = 0;
+    const int ctas = batched_ctas(h->device);
+    BBC_CUDA(cudaMalloc(&h->batch_work, batched_workspace_bytes(max_n, ctas)));
+    BBC_CUDA(batched_upload_programs());
+    h->batch_ctas = ctas;
+    h->batch_nmax = max_n;
+  }
+  return BBC_OK;
+}
+
+int bbc_batch_order(const int64_t* hNs, int64_t count, int64_t* hOrder) {
+  if (count < 0 || (count > 0 && (!hNs || !hOrder))) return fail(BBC_INVALID_ARG, "bad batch order arguments");
+  std::vector<int64_t> idx((size_t)count);
+  for (int64_t i = 0; i < count; ++i) idx[(size_t)i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return hNs[a] > hNs[b]; });
+  for (int64_t i = 0; i < count; ++i) hOrder[i] = idx[(size_t)i];
+  return BBC_OK;
+}
+
+int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, int64_t count, void* const* dOut,
+                     int dtype, double tol, int flags, void* stream, bbc_info* dInfo) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (count < 0 || (count > 0 && (!dA || !dNs || !dOut))) return fail(BBC_INVALID_ARG, "bad batched arguments");
+  if (dtype != BBC_DTYPE_F32 && dtype != BBC_DTYPE_F64) return fail(BBC_INVALID_ARG, "unknown dtype");
+  const double u = tol > 0 ? tol : std::ldexp(1.0, -53);
+  if (!valid_u(u)) return fail(BBC_INVALID_ARG, "tol out of range [2^-60, 2^-5]");
+  if ((rc = check_flags(flags))) return rc;
+  if ((flags & BBC_SCHEME_MASK) != BBC_SCHEME_NEW || (flags & BBC_PREC_MASK) != BBC_PREC_FP64)
+    return fail(BBC_UNSUPPORTED, "batched path: scheme NEW with FP64 products only");
+  if (count == 0) return BBC_OK;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (!h->batch_work) return fail(BBC_INVALID_ARG, "call bbc_batch_reserve first");
+  static const int deg[6] = {1, 2, 4, 8, 12, 18};
+  double theta[6];
+  for (int i = 0; i < 6; ++i) theta[i] = theta_cached(deg[i], u);
+  cudaStream_t st = (cudaStream_t)stream;
+  LaunchScope scope(h, BBC_KERNEL_BATCHED, st);
+  const cudaError_t e = batched_launch(dA, dOut, dNs, count, h->batch_nmax, dtype, theta, h->batch_work,
+                                       h->batch_ctas, dInfo, st);
+  if (e != cudaSuccess) return cuda_fail(e, "batched launch");
   return BBC_OK;
 }
 

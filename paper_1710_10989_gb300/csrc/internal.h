@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bbcexpm.h"
+
 namespace bbc {
 
 constexpr int MAX_Y = 6;      // distinct matrices an epilogue may read
@@ -79,5 +81,13 @@ cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices,
 cudaError_t ozaki_product(int64_t N, double alpha, const Epilogue& e, int slices, void* work,
                           unsigned int* flag, cudaStream_t st);
 bool ozaki_supported(int64_t N);
+
+// Persistent batched exp(A) (batched.cu).
+size_t batched_workspace_bytes(int64_t nmax, int ctas);
+int batched_ctas(int device);
+cudaError_t batched_upload_programs();
+cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t* Ns, int64_t count,
+                           int64_t nmax, int dtype, const double* theta, void* work, int ctas,
+                           bbc_info* info, cudaStream_t st);
 
 }  // namespace bbc

@@ -1,0 +1,112 @@
+"""GPU parity, batched path: one persistent launch over many matrices of uneven
+sizes, each checked against the oracle at the same (m, s). Tolerances: 1e-12
+relative Frobenius with binary64 storage; 1e-6 with binary32 storage (the
+batched workload's tolerance; the oracle runs on the binary32-rounded input)."""
+import numpy as np
+import pytest
+
+from gpu_util import rel_fro
+from oracle import oracle as O
+from paper_1710_10989_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_10989_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def h(api):
+    hh = api.Handle(0)
+    hh.batch_reserve(256)
+    yield hh
+    hh.close()
+
+
+def _run(h, api, mats, dtype):
+    import torch
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    ins = [torch.from_numpy(A.astype(dtype)).cuda() for A in mats]
+    outs = [torch.full_like(a, float("nan")) for a in ins]
+    b = api.Batch(ins, outs)
+    h.expm_batched(b)
+    torch.cuda.synchronize()
+    return [o.cpu().numpy().astype(np.float64) for o in outs], b.infos()
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_batch_matches_oracle(h, api, dtype):
+    ns, norms = W.batch_spec(count=40, seed=3)
+    ns[:6] = [1, 7, 8, 65, 255, 256]           # edge sizes, ragged tails
+    mats = [W.batch_matrix(i, int(n), float(v), seed=3) for i, (n, v) in enumerate(zip(ns, norms))]
+    outs, infos = _run(h, api, mats, dtype)
+    tol = 1e-12 if dtype == np.float64 else 1e-6
+    for A, E, inf in zip(mats, outs, infos):
+        A = A.astype(dtype).astype(np.float64)
+        want, oi = O.expm(A, "new")
+        assert inf["status"] == 0, inf
+        assert (inf["m"], inf["s"], inf["products"]) == (oi.m, oi.s, oi.products), (inf, oi)
+        assert rel_fro(E, want) < tol, (A.shape, inf, rel_fro(E, want))
+
+
+def test_batch_order_largest_first(api):
+    assert api.batch_order([8, 256, 64, 256, 1]) == [1, 3, 2, 0, 4]
+
+
+def test_batch_statuses(h, api):
+    import torch
+    bad = np.eye(12)
+    bad[3, 3] = np.nan
+    big = np.eye(9) * 900.0  # e^900 overflows binary32 and binary64
+    mats = [np.eye(5) * 0.5, bad, big]
+    ins = [torch.from_numpy(m.astype(np.float32)).cuda() for m in mats]
+    outs = [torch.zeros_like(a) for a in ins]
+    b = api.Batch(ins, outs)
+    h.expm_batched(b)
+    torch.cuda.synchronize()
+    st = [i["status"] for i in b.infos()]
+    assert st == [api.OK, api.NONFINITE_INPUT, api.OVERFLOW], st
+    assert np.allclose(outs[0].cpu().numpy(), np.eye(5) * np.exp(0.5), rtol=1e-6)
+
+
+def test_batch_rejects_oversize_per_matrix(api):
+    import torch
+    hh = api.Handle(0)
+    hh.batch_reserve(32)
+    ins = [torch.eye(16, dtype=torch.float64, device="cuda"), torch.eye(40, dtype=torch.float64, device="cuda")]
+    outs = [torch.zeros_like(a) for a in ins]
+    b = api.Batch(ins, outs)
+    hh.expm_batched(b)
+    torch.cuda.synchronize()
+    st = [i["status"] for i in b.infos()]
+    assert st == [api.OK, api.INVALID_ARG]
+    assert torch.allclose(outs[0], torch.eye(16, dtype=torch.float64, device="cuda") * np.e)
+    hh.close()
+
+
+def test_batch_graph_capture_replay(h, api):
+    import torch
+    ns, norms = W.batch_spec(count=12, seed=4)
+    mats = [W.batch_matrix(i, int(n), float(v), seed=4) for i, (n, v) in enumerate(zip(ns, norms))]
+    ins = [torch.from_numpy(A).cuda() for A in mats]
+    outs = [torch.zeros_like(a) for a in ins]
+    b = api.Batch(ins, outs)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        h.expm_batched(b, stream=s)   # warm-up outside the capture
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            h.expm_batched(b, stream=s)
+    for o in outs:
+        o.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for A, o in zip(mats, outs):
+        want, _ = O.expm(A, "new")
+        assert rel_fro(o.cpu().numpy(), want) < 1e-12
