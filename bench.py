@@ -1,13 +1,19 @@
 #!/usr/bin/env python
 """Throughput of scaling-and-squaring exp(A) (Bader, Blanes, Casas, arXiv:1710.10989)
-on the dense 4096 x 4096 FP64 workload, through libbbcexpm.so.
+through libbbcexpm.so. Prints one JSON line (rank 0).
 
-One step = exp(A) of every matrix of the workload: six Gaussian N(0,1)/sqrt(N)
-matrices rescaled to 1-norms {0.01, 0.1, 1, 5, 20, 100} (seeds 1-6) and six
-non-normal upper-triangular ones (diagonal N(0,1), strict upper N(0,1)*10,
-seeds 101-106) at the same norms; (m, s) chosen by the theta rule at u = 2^-53.
+Default workload (dense4096): one step = exp(A) of twelve 4096 x 4096 matrices:
+six Gaussian N(0,1)/sqrt(N) rescaled to 1-norms {0.01, 0.1, 1, 5, 20, 100}
+(seeds 1-6) and six non-normal upper-triangular ones (diagonal N(0,1), strict
+upper N(0,1)*10, seeds 101-106) at the same norms; (m, s) by the theta rule at
+u = 2^-53. The timed form is the split-precision one (products rebuilt exactly
+from 7 BF16 slices on the tensor cores); the plain FP64 form is timed beside
+it and the largest relative difference between the two results is reported.
 
-Prints one JSON line (rank 0). --impl reference times the CPU oracle instead.
+Other workloads (--workload): batch (20000 matrices, N in {8..256}, binary32
+storage, one persistent graph-captured launch per step), small (one 64 x 64
+matrix, latency), large (8192 x 8192, norms 0.5/5/50).
+--impl reference times the CPU oracle instead, on the host cores.
 """
 from __future__ import annotations
 
@@ -26,7 +32,10 @@ sys.path.insert(0, ROOT)
 
 from paper_1710_10989_gb300 import workloads as W  # noqa: E402
 
-L2_BYTES = 129 * 2 ** 20
+PI = {1: 0, 2: 1, 4: 2, 8: 3, 12: 4, 18: 5}
+# FP64 pipe: the GB300's nominal 1.25 TFLOP/s FP64 is 2 DFMA per clock per SM:
+# 152 SMs x 2 DFMA x 2 flop x 2.07 GHz (maximum SM clock).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def parse():
@@ -35,33 +44,34 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp64", "ozaki"), default="fp64")
-    ap.add_argument("--slices", type=int, default=0, help="BF16 slices for --precision ozaki (0 = 7)")
-    ap.add_argument("--n", type=int, default=W.DENSE_N, help="matrix size (default: the 4096 workload)")
+    ap.add_argument("--workload", choices=("dense4096", "batch", "small", "large"), default="dense4096")
+    ap.add_argument("--precision", choices=("ozaki", "fp64"), default="ozaki")
+    ap.add_argument("--slices", type=int, default=7, help="BF16 slices of the split-precision products")
+    ap.add_argument("--n", type=int, default=0, help="override the matrix size of dense workloads")
+    ap.add_argument("--count", type=int, default=W.BATCH_COUNT, help="batch size of --workload batch")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
 
 
-def workload(n: int):
-    mats, names = [], []
-    for i, nrm in enumerate(W.DENSE_NORMS):
-        mats.append(W.dense_case(i, n=n))
-        names.append(f"gauss_{nrm:g}")
-    for i, nrm in enumerate(W.DENSE_NORMS):
-        mats.append(W.dense_case(i, n=n, nonnormal=True))
-        names.append(f"upper_{nrm:g}")
-    return mats, names
+# ------------------------------------------------------------------ workloads
+def dense_workload(n: int):
+    mats = [W.dense_case(i, n=n) for i in range(len(W.DENSE_NORMS))]
+    mats += [W.dense_case(i, n=n, nonnormal=True) for i in range(len(W.DENSE_NORMS))]
+    return mats
 
 
-def products_per_matrix(mats) -> list[int]:
-    """(m, s) by the theta rule from each matrix's 1-norm; products = pi_m + s."""
+def large_workload(n: int):
+    return [W.large_case(i, n=n) for i in range(len(W.LARGE_NORMS))]
+
+
+def products_of(mats, u=2.0 ** -53) -> list[int]:
     from paper_1710_10989_gb300 import api
-    pi = {1: 0, 2: 1, 4: 2, 8: 3, 12: 4, 18: 5}
     out = []
     for A in mats:
-        m, s = api.select(float(np.abs(A).sum(axis=0).max()))
-        out.append(pi[m] + s)
+        m, s = api.select(float(np.abs(A.astype(np.float64)).sum(axis=0).max()), u)
+        out.append(PI[m] + s)
     return out
 
 
@@ -132,121 +142,151 @@ def peaks():
         return {}
 
 
-# FP64 pipe: the GB300's nominal 1.25 TFLOP/s FP64 is 2 DFMA per clock per SM:
-# 152 SMs x 2 DFMA x 2 flop x 2.07 GHz (maximum SM clock).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+METRICS = {
+    "dense4096": "expm/s (dense 4096x4096 exp(A), FP64-accurate)",
+    "large": "expm/s (dense 8192x8192 exp(A), FP64-accurate)",
+    "batch": "expm/s (batched exp(A), 20000 matrices N in 8..256, binary32 storage)",
+    "small": "expm/s (single 64x64 exp(A), FP64, graph-replayed)",
+}
+WORKLOAD_DESC = {
+    "dense4096": "dense{n}: 6 Gaussian N(0,1)/sqrt(N) (seeds 1-6) + 6 non-normal upper-triangular "
+                 "(seeds 101-106), 1-norms 0.01,0.1,1,5,20,100",
+    "large": "large{n}: Gaussian N(0,1)/sqrt(N), seeds 1-3, 1-norms 0.5,5,50",
+    "batch": "batch: N uniform on {{8,...,256}}, 1-norms log-uniform [1e-3, 1e2], half Gaussian, "
+             "half V diag(lambda) V^-1 (cond(V)=1e3), seed 7",
+    "small": "small64: N(0,1) seed 0, 1-norm 1.0, (m,s) = (18,0)",
+}
 
 
-def cpu_oracle_sample(mats, prods):
-    """The oracle on matrix 0 of the workload (its cheapest), scaled to expm/s of
-    the whole workload by products: value = 1 / (t_per_product * mean products)."""
+# ------------------------------------------------------------------ CPU oracle legs
+def cpu_dense_sample(mats, prods):
+    """The oracle on the workload's first matrix (its cheapest), scaled by
+    products to expm/s of the whole workload."""
     from oracle import oracle as O
     A = mats[0]
     O.theta_array("new")  # thresholds are constants: computed (and cached) before timing
     t0 = time.perf_counter()
     _, info = O.expm(A, "new")
     dt = time.perf_counter() - t0
-    per_product = dt / max(1, info.products)
     mean_p = sum(prods) / len(prods)
-    return {"value": 1.0 / (per_product * mean_p), "unit": "expm/s", "cores": O.num_threads(),
-            "kind": "oracle",
-            "sample": (f"oracle exp(A) of the workload's first matrix (N={A.shape[0]}, 1-norm 0.01, "
-                       f"{info.products} products) in {dt:.1f} s; scaled by products to the workload's "
-                       f"mean of {mean_p:.2f} products per exp(A)")}
+    return {"value": 1.0 / (dt / max(1, info.products) * mean_p), "unit": "expm/s",
+            "cores": O.num_threads(), "kind": "oracle",
+            "sample": (f"oracle exp(A) of the workload's first matrix (N={A.shape[0]}, 1-norm "
+                       f"{np.abs(A).sum(0).max():.3g}, {info.products} products) in {dt:.1f} s; scaled by "
+                       f"products to the workload's mean of {mean_p:.2f} products per exp(A)")}
 
 
-def run_reference(args, rank: int, world: int):
+def cpu_batch_sample(mats, k=200):
+    """The oracle on the first k matrices of the batch (a uniform sample of sizes/norms)."""
+    from oracle import oracle as O
+    O.theta_array("new")
+    t0 = time.perf_counter()
+    for A in mats[:k]:
+        O.expm(A.astype(np.float64), "new")
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": "expm/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"oracle exp(A) of the first {k} of the batch's matrices (binary32 inputs promoted "
+                      f"to binary64) in {dt:.1f} s"}
+
+
+def run_reference(args, rank: int):
     if rank != 0:
         return
-    mats, _ = workload(args.n)
-    prods = products_per_matrix(mats)
-    vals = []  # the CPU needs no warm-up steps; --warmup is accepted and not run
-    for _ in range(args.steps):
-        r = cpu_oracle_sample(mats, prods)
+    metric = METRICS[args.workload]
+    if args.workload == "batch":
+        mats = W.batch_matrices(min(args.count, 400))
+        leg = lambda: cpu_batch_sample(mats)  # noqa: E731
+        cfg = {"workload": WORKLOAD_DESC["batch"], "count": args.count}
+    else:
+        n = args.n or (W.LARGE_N if args.workload == "large" else 64 if args.workload == "small" else W.DENSE_N)
+        mats = (large_workload(n) if args.workload == "large" else [W.small_case()] if args.workload == "small"
+                else dense_workload(n))
+        prods = products_of(mats)
+        leg = lambda: cpu_dense_sample(mats, prods)  # noqa: E731
+        cfg = {"workload": WORKLOAD_DESC[args.workload].format(n=n), "n": n, "matrices_per_step": len(mats)}
+    vals, r = [], None
+    for _ in range(args.steps):  # the CPU needs no warm-up steps; --warmup is accepted and not run
+        r = leg()
         vals.append(r["value"])
     value = statistics.median(vals)
-    line = {"impl": "reference", "metric": "expm/s (dense 4096x4096 exp(A), FP64)", "value": value,
-            "unit": "expm/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "dense4096: 6 Gaussian + 6 non-normal upper-triangular, norms 0.01-100",
-                       "n": args.n, "matrices_per_step": len(mats)},
-            "cpu_baseline": {"value": value, "unit": "expm/s", "cores": r["cores"], "kind": "oracle",
-                             "sample": "per step: " + r["sample"]},
-            "e2e": {"value": value, "unit": "expm/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps({
+        "impl": "reference", "metric": metric, "value": value, "unit": "expm/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": "expm/s", "cores": r["cores"], "kind": "oracle",
+                         "sample": "per step: " + r["sample"]},
+        "e2e": {"value": value, "unit": "expm/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+        flush=True)
 
 
-def main():
-    args = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
-
-    import torch
-    import torch.distributed as dist
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    if rank == 0:
-        from paper_1710_10989_gb300 import build as B
-        B.build()
-    if world > 1:
-        dist.barrier()
-    from paper_1710_10989_gb300 import api
-
-    flags = api.SCHEME_NEW | (api.PREC_FP64 if args.precision == "fp64"
-                              else api.PREC_OZAKI | api.ozaki_slices(args.slices))
-    mats, names = workload(args.n)
-    n = args.n
-    prods = products_per_matrix(mats)
-    h = api.Handle(local)
-    dA = [torch.from_numpy(A).cuda() for A in mats]
-    dO = [torch.empty_like(a) for a in dA]
-    stream = torch.cuda.current_stream()
-
-    def step():
-        infos = []
-        for a, o in zip(dA, dO):
-            infos.append(h.expm(a, o, 0.0, flags, stream))
-        return infos
-
-    for _ in range(args.warmup):
-        infos = step()
-    assert [i.products for i in infos] == prods, ([i.products for i in infos], prods)
-
-    clocks = ClockSampler(local)
+# ------------------------------------------------------------------ GPU legs
+def timed(torch, dist, world, stream, fn, steps):
+    """Barrier + sync on both sides, CUDA events on the launching stream; max over ranks."""
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    h.profile_enable(True)
-    clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
-        step()
+    for _ in range(steps):
+        fn()
     ev1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    t = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def flags_for(api, precision, slices):
+    return api.SCHEME_NEW | (api.PREC_FP64 if precision == "fp64" else api.PREC_OZAKI | api.ozaki_slices(slices))
+
+
+def run_dense(args, torch, dist, api, rank, world, local):
+    n = args.n or (W.LARGE_N if args.workload == "large" else W.DENSE_N)
+    mats = large_workload(n) if args.workload == "large" else dense_workload(n)
+    prods = products_of(mats)
+    h = api.Handle(local)
+    stream = torch.cuda.current_stream()
+    flags = flags_for(api, args.precision, args.slices)
+    dA = [torch.from_numpy(A).cuda() for A in mats]
+    dO = [torch.empty_like(a) for a in dA]
+
+    def step():
+        for a, o in zip(dA, dO):
+            h.expm(a, o, 0.0, flags, stream)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    h.profile_enable(True)
+    clocks.start()
+    ms = timed(torch, dist, world, stream, step, args.steps)
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
     launches, _ = h.profile_read(api.KERNEL_ALL)
     prod_launches, prod_ms = h.profile_read(api.KERNEL_PRODUCT)
     split_launches, split_ms = h.profile_read(api.KERNEL_SPLIT)
-    norm_launches, norm_ms = h.profile_read(api.KERNEL_NORM)
+    _, norm_ms = h.profile_read(api.KERNEL_NORM)
     h.profile_enable(False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    total = len(mats) * args.steps * world
-    value = total / (ms_max / 1e3)
+    value = len(mats) * args.steps * world / (ms / 1e3)
 
-    # end to end through the C-ABI host entry point: H2D of A and D2H of exp(A) every call
+    # plain FP64 form beside it, and how far the two results are apart
+    fp64 = None
+    if args.precision != "fp64" and not args.no_fp64_compare:
+        f64 = flags_for(api, "fp64", 0)
+        dF = [torch.empty_like(a) for a in dA]
+
+        def step64():
+            for a, o in zip(dA, dF):
+                h.expm(a, o, 0.0, f64, stream)
+        step64()
+        ms64 = timed(torch, dist, world, stream, step64, 1)
+        diff = max(float(torch.linalg.norm(o - f) / torch.linalg.norm(f)) for o, f in zip(dO, dF))
+        fp64 = {"value": len(mats) * world / (ms64 / 1e3), "unit": "expm/s", "steps": 1, "warmup": 1,
+                "max_rel_fro_diff_vs_chosen": diff}
+        del dF
+
     e2e = None
     if not args.no_e2e:
         hA = [torch.from_numpy(A).pin_memory() for A in mats]
@@ -270,53 +310,195 @@ def main():
     pk = peaks()
     flops_per_product = 2.0 * n ** 3
     avg_ms = prod_ms / max(1, prod_launches)
-    achieved = flops_per_product / (avg_ms / 1e3) / 1e12
+    logical = flops_per_product / (avg_ms / 1e3) / 1e12
     if args.precision == "fp64":
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "k_gemm_f64<64,64> (dense product + fused epilogue)",
+        roof = {"bound": "alu", "achieved": logical, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": logical / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_gemm_f64<64,64>",
                 "peak_source": "FP64 pipe, 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                "avg_launch_ms": avg_ms, "launches": prod_launches}
+                "flops_per_launch": flops_per_product, "avg_launch_ms": avg_ms, "launches": prod_launches}
     else:
-        # the tcgen05 kernel executes k(k+1)/2 BF16 slice products per FP64 product
-        slices = args.slices or 7
-        pairs = slices * (slices + 1) // 2
+        pairs = args.slices * (args.slices + 1) // 2
         executed = pairs * flops_per_product / (avg_ms / 1e3) / 1e12
         peak = pk.get("bf16_tflops", 1899.1)
         roof = {"bound": "tensor", "achieved": executed, "peak": peak, "unit": "TFLOP/s",
                 "frac": executed / peak, "traffic": None,
-                "kernel": f"k_ozaki_gemm ({slices} BF16 slices, {pairs} slice products per FP64 product)",
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS)" if "bf16_tflops" in pk
-                               else "fallback 1.9 PFLOP/s bf16",
+                "kernel": f"k_ozaki_gemm ({args.slices} BF16 slices: {pairs} slice products per FP64 product)",
+                "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS)" if "bf16_tflops" in pk
+                                else "fallback 1.9 PFLOP/s bf16"),
                 "flops_per_launch": pairs * flops_per_product, "avg_launch_ms": avg_ms,
-                "launches": prod_launches, "logical_fp64_tflops": achieved,
-                "split_kernels_ms_per_product": split_ms / max(1, split_launches / 3)}
-
-    if rank == 0:
-        cpu = None
-        if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_oracle_sample(mats, prods)
-        line = {
-            "metric": "expm/s (dense 4096x4096 exp(A), FP64)", "value": value, "unit": "expm/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "bf16-slices(exact f32 sums)->f64",
-            "data": "synthetic",
-            "config": {"workload": "dense4096: 6 Gaussian N(0,1)/sqrt(N) (seeds 1-6) + 6 non-normal "
-                                   "upper-triangular (seeds 101-106), 1-norms 0.01,0.1,1,5,20,100",
-                       "n": n, "matrices_per_step": len(mats), "products_per_step": sum(prods),
-                       "scheme": "new (reduced-product Taylor)", "precision": args.precision,
-                       "u": "2^-53", "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (each exp(A) streams ~10 N^2 FP64 buffers of "
-                             f"{n * n * 8 / 2 ** 20:.0f} MiB)"},
-            "tflops_logical": sum(prods) * flops_per_product * args.steps * world / (ms_max / 1e3) / 1e12,
-            "time_share": {"product_ms": prod_ms, "split_ms": split_ms, "norm_ms": norm_ms,
-                           "timed_ms": ms},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk,
-        }
-        print(json.dumps(line), flush=True)
+                "launches": prod_launches, "logical_fp64_tflops": logical,
+                "split_ms_per_product": split_ms / max(1, split_launches / 3)}
+    cpu = cpu_dense_sample(mats, prods) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     h.close()
+    line = {
+        "metric": METRICS[args.workload],
+        "value": value, "unit": "expm/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.slices}-slices(exact sums)->f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC[args.workload].format(n=n),
+                   "n": n, "matrices_per_step": len(mats), "products_per_step": sum(prods),
+                   "scheme": "new (reduced-product Taylor)", "precision": args.precision,
+                   "slices": args.slices if args.precision != "fp64" else None, "u": "2^-53",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": f"inputs larger than L2 (each exp(A) streams ~10 N^2 FP64 buffers of "
+                         f"{n * n * 8 / 2 ** 20:.0f} MiB)"},
+        "tflops_logical": sum(prods) * flops_per_product * args.steps * world / (ms / 1e3) / 1e12,
+        "time_share": {"product_ms": prod_ms, "split_ms": split_ms, "norm_ms": norm_ms, "timed_ms": ms},
+        "roofline": roof, "plain_fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk,
+    }
+    return line
+
+
+def run_batch(args, torch, dist, api, rank, world, local, mats):
+    h = api.Handle(local)
+    h.batch_reserve(256)
+    order = api.batch_order([A.shape[0] for A in mats])
+    mats = [mats[i] for i in order]
+    ins = [torch.from_numpy(A).cuda() for A in mats]
+    outs = [torch.empty_like(a) for a in ins]
+    batch = api.Batch(ins, outs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h.expm_batched(batch, stream=stream)  # warm-up outside the capture
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            h.expm_batched(batch, stream=stream)
+    for _ in range(args.warmup):
+        graph.replay()
+    clocks = ClockSampler(local)
+    h.profile_enable(True)
+    clocks.start()
+    ms = timed(torch, dist, world, stream, graph.replay, args.steps)
+    clk = clocks.stop()
+    h.profile_enable(False)
+    infos = batch.infos()
+    bad = sum(1 for i in infos if i["status"] != 0)
+    products = sum(i["products"] for i in infos)
+    flops = sum(2.0 * A.shape[0] ** 3 * i["products"] for A, i in zip(mats, infos))
+    bytes_io = sum(2 * A.size * 4 for A in mats)
+    value = len(mats) * args.steps * world / (ms / 1e3)
+    achieved = flops / (ms / args.steps / 1e3) / 1e12
+
+    e2e = None
+    if not args.no_e2e:
+        hin = [torch.from_numpy(A).pin_memory() for A in mats]
+        hout = [torch.empty_like(a).pin_memory() for a in hin]
+        e2e_steps = max(1, min(args.steps, 2))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            with torch.cuda.stream(stream):
+                for a, d in zip(hin, ins):
+                    d.copy_(a, non_blocking=True)
+                graph.replay()
+                for d, o in zip(outs, hout):
+                    o.copy_(d, non_blocking=True)
+            stream.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": len(mats) * e2e_steps * world / te, "unit": "expm/s", "h2d_bytes_per_step": bytes_io // 2,
+               "d2h_bytes_per_step": bytes_io // 2, "steps": e2e_steps}
+    cpu = cpu_batch_sample(mats[::max(1, len(mats) // 200)]) if (rank == 0 and world == 1
+                                                                 and not args.no_cpu_baseline) else None
+    h.close()
+    return {
+        "metric": METRICS["batch"], "value": value,
+        "unit": "expm/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (binary32 storage)", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC["batch"].format(),
+                   "count": len(mats), "products_per_step": products, "statuses_not_ok": bad,
+                   "graph": "one persistent kernel per step, replayed from a CUDA graph", "u": "2^-53",
+                   "l2": "per-CTA binary64 work slots; inputs+outputs 3.7 GB per step (larger than L2)"},
+        "tflops_logical": achieved,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_batched_expm (FP64 products)",
+                     "peak_source": "FP64 pipe, 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"},
+        "hbm_gbs_io": bytes_io / (ms / args.steps / 1e3) / 1e9,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk,
+    }
+
+
+def run_small(args, torch, dist, api, rank, world, local):
+    """One 64 x 64 matrix: graph-replayed single exp(A) (batched kernel, count 1)
+    and the plain bbc_expm call (two host synchronisations)."""
+    A = W.small_case()
+    h = api.Handle(local)
+    h.batch_reserve(64)
+    a = torch.from_numpy(A).cuda()
+    o = torch.empty_like(a)
+    batch = api.Batch([a], [o])
+    stream = torch.cuda.Stream()
+    reps = 200
+    with torch.cuda.stream(stream):
+        h.expm_batched(batch, stream=stream)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            for _ in range(reps):
+                h.expm_batched(batch, stream=stream)
+    for _ in range(args.warmup):
+        graph.replay()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = timed(torch, dist, world, stream, graph.replay, args.steps)
+    clk = clocks.stop()
+    us_graph = ms * 1e3 / (args.steps * reps)
+    cur = torch.cuda.current_stream()
+    for _ in range(5):
+        h.expm(a, o, 0.0, api.SCHEME_NEW, cur)
+    t0 = time.perf_counter()
+    for _ in range(50):
+        h.expm(a, o, 0.0, api.SCHEME_NEW, cur)
+    us_call = (time.perf_counter() - t0) / 50 * 1e6
+    h.close()
+    flops = 2.0 * 64 ** 3 * 5
+    return {
+        "metric": METRICS["small"], "value": 1e6 / us_graph, "unit": "expm/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC["small"], "exp_per_step": reps},
+        "us_per_expm_graph": us_graph, "us_per_expm_call": us_call,
+        "roofline": {"bound": "latency", "achieved": flops / (us_graph * 1e-6) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": flops / (us_graph * 1e-6) / 1e12 / FP64_PEAK_TFLOPS,
+                     "traffic": None},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": 2 * reps * args.steps, "clocks": clk,
+    }
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    # the batch is generated by spawned workers before CUDA starts in this process
+    mats = W.batch_matrices(args.count) if args.workload == "batch" else None
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        from paper_1710_10989_gb300 import build as B
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1710_10989_gb300 import api
+    if args.workload == "batch":
+        line = run_batch(args, torch, dist, api, rank, world, local, mats)
+    elif args.workload == "small":
+        line = run_small(args, torch, dist, api, rank, world, local)
+    else:
+        line = run_dense(args, torch, dist, api, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

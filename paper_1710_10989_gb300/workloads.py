@@ -69,11 +69,19 @@ def conditioned_basis(n: int, rng: np.random.Generator, cond: float = 1e3) -> np
 
 
 def diagonalisable(n: int, seed: int, norm1: float | None = None) -> np.ndarray:
-    """A = V diag(lambda) V^-1 with lambda ~ N(0, 4) and cond_2(V) = 1e3."""
+    """A = V diag(lambda) V^-1 with lambda ~ N(0, 4) and cond_2(V) = 1e3, where
+    V = U S W^T, so V^-1 = W S^-1 U^T exactly (U, W orthogonal)."""
     rng = np.random.default_rng(seed)
     lam = rng.standard_normal(n) * 2.0
-    V = conditioned_basis(n, rng)
-    A = (V * lam) @ np.linalg.inv(V)
+
+    def orth():
+        Q, R = np.linalg.qr(rng.standard_normal((n, n)))
+        return Q * np.sign(np.diag(R))
+    U, Wm = orth(), orth()
+    sv = np.logspace(0.0, -3.0, n)
+    V = (U * sv) @ Wm.T
+    Vinv = (Wm / sv) @ U.T
+    A = (V * lam) @ Vinv
     return rescale_norm1(A, norm1) if norm1 is not None else A
 
 
@@ -109,3 +117,39 @@ def batch_matrix(i: int, n: int, norm1: float, seed: int = BATCH_SEED) -> np.nda
     if i % 2 == 0:
         return gaussian(int(n), s, norm1)
     return diagonalisable(int(n), s, norm1)
+
+
+def _batch_chunk(args):
+    lo, hi, ns, norms, seed = args
+    return [batch_matrix(i, int(ns[i - lo]), float(norms[i - lo]), seed).astype(np.float32)
+            for i in range(lo, hi)]
+
+
+def batch_matrices(count: int = BATCH_COUNT, seed: int = BATCH_SEED, workers: int = 0):
+    """All matrices of the batched workload as binary32 arrays (their storage type).
+
+    Canonical generation: LAPACK's QR gives last-bit differences with the BLAS
+    thread count, so the matrices are always built in worker processes started
+    with 'spawn' and single-threaded BLAS (safe before or after CUDA starts);
+    the result does not depend on `workers` (0 = one per core, at most 16)."""
+    import multiprocessing as mp
+    import os
+    ns, norms = batch_spec(count, seed)
+    workers = workers or min(16, os.cpu_count() or 1)
+    step = max(1, (count + workers * 4 - 1) // (workers * 4))
+    jobs = [(lo, min(count, lo + step), ns[lo:lo + step], norms[lo:lo + step], seed)
+            for lo in range(0, count, step)]
+    keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            parts = pool.map(_batch_chunk, jobs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return [m for part in parts for m in part]
