@@ -16,25 +16,27 @@
 // Exact products. Pairs (p, q) with g = p + q <= k - 1 are kept (the triangle),
 // C_ij = 2^(e_i + f_j - 16) sum_g 2^(-8g) S_g with S_g = sum_{p+q=g} sum_k d^P d^Q,
 // an error of order 2^(-8k) relative to the row and column scales.
-//  * High groups g <= 3 carry weights down to 2^-24 and must be summed exactly.
+//  * High groups g <= 4 carry weights down to 2^-32 and are summed exactly.
 //    A product of digits is at most 2^14, so a sum of up to 1024 of them is an
 //    integer below 2^24 and FP32 holds it exactly: the K loop of these pairs is
 //    cut into 1024-wide chunks, and after each chunk the FP32 tile is drained from
-//    TMEM, converted to int32 and added, shifted by 2^(8(3-g)), into an integer
-//    accumulator R (two 32-bit TMEM planes; |R| < 2^53 for N <= 16384).
-//  * Low groups g >= 4 weigh at most 2^-32, so FP32 rounding of their sum costs
-//    about 2^-56 of the result: they accumulate in a second FP32 TMEM tile over the
-//    whole K, Horner-style from the smallest weight up, the MMA scaling the running
-//    sum by 2^-8 (scale-input-d) at each change of group.
-//  C_ij = 2^(e_i + f_j - 40) (R + 2^-8 LOW).
+//    TMEM, converted to int32 and added, shifted by 2^(8(4-g)), into an integer
+//    accumulator R (two 32-bit TMEM planes; |R| < 2^60 for N <= 16384).
+//  * Low groups g >= 5 weigh at most 2^-40. They accumulate in a second FP32 TMEM
+//    tile over the whole K, Horner-style from the smallest weight up, the MMA
+//    scaling the running sum by 2^-8 (scale-input-d) at each change of group.
+//    That FP32 sum of up to ~10^5 terms loses roughly 2^-16 of itself, i.e. about
+//    2^-56 of the result. (With the exact/FP32 boundary one group lower, at g = 4,
+//    the same loss showed up as ~1e-14 relative error per product at N = 4096.)
+//  C_ij = 2^(e_i + f_j - 48) (R + 2^-8 LOW).
 //
 // Kernel shape (one CTA per 128 x 128 output tile, 6 warps):
 //   warp 0: TMA producer (3-D tensor maps over the slice planes, 128B swizzle),
 //           6-stage ring of 128x64 BF16 A and B tiles;
 //   warp 1: tcgen05.mma issuer (M=128, N=128, K=16, BF16 -> FP32 in TMEM). High
 //           and low chunks are interleaved so each drain overlaps low-group MMAs;
-//           with no low groups (k <= 4) the high accumulator is double-buffered;
 //   warps 2-5: drain (tcgen05.ld / st) and the final FP64 epilogue.
+//           with no low groups (k <= 5) the high accumulator is double-buffered;
 // TMEM: [0,128) high accumulator, [128,256) low accumulator (or the second high
 // buffer), [256,384) low and [384,512) high words of R.
 // Every mbarrier wait is bounded in time; on expiry the kernel records a
@@ -58,7 +60,7 @@ constexpr int STAGES = 6;
 constexpr int STAGE_BYTES = TILE * KSTEP * 2;  // 16 KB per operand tile
 constexpr int NUM_THREADS = 192;
 constexpr int NUM_EPI = 128;
-constexpr int G_EXACT = 4;         // groups 0..3 are summed exactly
+constexpr int G_EXACT = 5;         // groups 0..4 are summed exactly
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;  // 2 s per wait
 constexpr unsigned int STATUS_NONFINITE = 1u;  // bits of the handle's status word
 constexpr unsigned int STATUS_TIMEOUT = 2u;
@@ -548,7 +550,7 @@ k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             const int64_t col = n0 + 32 * c4 + i;
             if (col >= N) break;
             const long long r = (long long)(((unsigned long long)hi[i] << 32) | lo[i]);
-            double v = (double)r;  // exact: |R| < 2^53
+            double v = (double)r;  // rounds to 53 bits when |R| >= 2^53
             if (sc.nL > 0) v = fma((double)__uint_as_float(lw[i]), 0.00390625, v);
             const int ex = er + fcol[col] - 16 - 8 * (G_EXACT - 1);
             const double scl = (ex >= -1022 && ex <= 1023) ? __longlong_as_double((long long)(ex + 1023) << 52)

@@ -110,3 +110,28 @@ def test_small_workload_split(h, api):
     h.expm(to_dev(A), out, 0.0, api.SCHEME_NEW | oz(api, 7))
     want, _ = O.expm(A, "new")
     assert rel_fro(to_host(out), want) < 1e-13
+
+
+def test_identity_dominated_operands(h, api):
+    # T = I + X + ... and the B_j of the scheme are dominated by their diagonal;
+    # row scales then leave the off-diagonal entries fewer bits, which is why the
+    # default is 8 slices
+    n = 1024
+    P = np.eye(n) + 0.05 * W.gaussian(n, 41, None)
+    Q = np.eye(n) + 0.05 * W.gaussian(n, 42, None)
+    C = empty_like_dev(n)
+    h.gemm(to_dev(P), to_dev(Q), C, api.PREC_OZAKI)      # default slice count
+    C64 = empty_like_dev(n)
+    h.gemm(to_dev(P), to_dev(Q), C64, api.PREC_FP64)
+    assert rel_fro(to_host(C), to_host(C64)) < 1e-14
+
+
+@pytest.mark.parametrize("idx,nonnormal", [(5, False), (5, True)])
+def test_dense_4096_split_full_size(h, api, idx, nonnormal):
+    """The dense 4096 workload at norm 100 (s = 7, the largest error amplification)."""
+    A = W.dense_case(idx, nonnormal=nonnormal)
+    out = empty_like_dev(A.shape[0])
+    info = h.expm(to_dev(A), out, 0.0, api.SCHEME_NEW | api.PREC_OZAKI)
+    want, oi = O.expm(A, "new")
+    assert (info.m, info.s, info.products) == (oi.m, oi.s, oi.products)
+    assert rel_fro(to_host(out), want) < 1e-12
