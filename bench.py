@@ -7,7 +7,7 @@ six Gaussian N(0,1)/sqrt(N) rescaled to 1-norms {0.01, 0.1, 1, 5, 20, 100}
 (seeds 1-6) and six non-normal upper-triangular ones (diagonal N(0,1), strict
 upper N(0,1)*10, seeds 101-106) at the same norms; (m, s) by the theta rule at
 u = 2^-53. The timed form is the split-precision one (products rebuilt exactly
-from 8 BF16 slices on the tensor cores); the plain FP64 form is timed beside
+from 7 BF16 slices on the tensor cores); the plain FP64 form is timed beside
 it and the largest relative difference between the two results is reported.
 
 Other workloads (--workload): batch (20000 matrices, N in {8..256}, binary32
@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=("dense4096", "batch", "small", "large"), default="dense4096")
     ap.add_argument("--precision", choices=("ozaki", "fp64"), default="ozaki")
-    ap.add_argument("--slices", type=int, default=8, help="BF16 slices of the split-precision products")
+    ap.add_argument("--slices", type=int, default=7, help="BF16 slices of the split-precision products")
     ap.add_argument("--n", type=int, default=0, help="override the matrix size of dense workloads")
     ap.add_argument("--count", type=int, default=W.BATCH_COUNT, help="batch size of --workload batch")
     ap.add_argument("--no-e2e", action="store_true")

@@ -48,7 +48,7 @@ typedef enum {
 #define BBC_SCHEME_MASK 0xF
 #define BBC_PREC_FP64 0x00     /* every product on the FP64 pipe (DFMA) */
 #define BBC_PREC_OZAKI 0x10    /* products as exact BF16 slice products on tcgen05 tensor cores,
-                                  accumulated exactly; bits 8-11 = slice count k (0 -> 8) */
+                                  accumulated exactly; bits 8-11 = slice count k (0 -> 7) */
 #define BBC_PREC_MASK 0xF0
 #define BBC_OZAKI_SLICES(k) (((k) & 0xF) << 8)
 

@@ -165,7 +165,7 @@ int ensure_workspace(bbc_handle h, int64_t N, int flags) {
   }
   if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
     const int k = (flags >> 8) & 0xF;
-    const size_t need = ozaki_workspace_bytes(N, k ? k : 8);
+    const size_t need = ozaki_workspace_bytes(N, k ? k : 7);
     if (need > h->ozaki_bytes) {
       if (h->ozaki) BBC_CUDA(cudaFree(h->ozaki));
       h->ozaki = nullptr;
@@ -219,14 +219,14 @@ int launch_product(bbc_handle h, const double* P, const double* Q, int64_t N, do
                    int flags, cudaStream_t stream) {
   cudaError_t err;
   if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
-    const int k = ((flags >> 8) & 0xF) ? ((flags >> 8) & 0xF) : 8;
+    const int k = ((flags >> 8) & 0xF) ? ((flags >> 8) & 0xF) : 7;
     {
       LaunchScope scope(h, BBC_KERNEL_SPLIT, stream);
       err = ozaki_split(P, Q, N, k, h->ozaki, h->dflag, stream);
     }
     if (err != cudaSuccess) return cuda_fail(err, "split launch");
     LaunchScope scope(h, BBC_KERNEL_PRODUCT, stream);
-    err = ozaki_product(N, alpha, e, k, h->ozaki, h->dflag, stream);
+    err = ozaki_product(P, Q, N, alpha, e, k, h->ozaki, h->dflag, stream);
   } else {
     LaunchScope scope(h, BBC_KERNEL_PRODUCT, stream);
     err = gemm_f64(P, Q, N, alpha, e, stream);
@@ -405,7 +405,7 @@ int bbc_workspace_size(bbc_handle h, int64_t N, int dtype, int flags, size_t* by
   size_t b = (size_t)NUM_WORK_SLOTS * N * N * sizeof(double) + norm1_partial_len(N) * sizeof(double);
   if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
     const int k = (flags >> 8) & 0xF;
-    b += ozaki_workspace_bytes(N, k ? k : 8);
+    b += ozaki_workspace_bytes(N, k ? k : 7);
   }
   *bytes = b;
   return BBC_OK;

@@ -13,6 +13,13 @@
 // Digits are small integers, exact in BF16. The extraction is pure integer work
 // on the FP64 bit pattern (no FP64 arithmetic: the FP64 pipe is the slow one).
 //
+// Diagonal deflation. The scheme's operands (B_j = b_0j I + ..., T = I + X + ...)
+// are dominated by their diagonal, which would set the row and column scales
+// and leave the off-diagonal entries ~10 fewer bits. So the diagonals are taken
+// out before slicing (P = D_P + P', Q = D_Q + Q') and added back exactly in the
+// epilogue: P Q = P'Q' + D_P Q + P D_Q - D_P D_Q (elementwise: P_ii Q_ij +
+// P_ij Q_jj - [i = j] P_ii Q_jj).
+//
 // Exact products. Pairs (p, q) with g = p + q <= k - 1 are kept (the triangle),
 // C_ij = 2^(e_i + f_j - 16) sum_g 2^(-8g) S_g with S_g = sum_{p+q=g} sum_k d^P d^Q,
 // an error of order 2^(-8k) relative to the row and column scales.
@@ -232,7 +239,7 @@ __device__ __forceinline__ void digits(long long X, uint32_t (&out)[K]) {
 template <int K>
 __global__ void __launch_bounds__(256)
 k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, uint16_t* __restrict__ planes,
-             int* __restrict__ erow, unsigned int* __restrict__ status) {
+             int* __restrict__ erow, double* __restrict__ pdiag, unsigned int* __restrict__ status) {
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= Rp) return;
@@ -242,7 +249,7 @@ k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, ui
   bool bad = false;
   if (row < N) {
     for (int64_t j = lane; j < N; j += 32) {
-      const int E = exp_field(__ldg(P + row * N + j));
+      const int E = (j == row) ? 0 : exp_field(__ldg(P + row * N + j));
       bad |= (E == 0x7FF);
       Emax = max(Emax, E);
     }
@@ -250,13 +257,20 @@ k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, ui
     for (int off = 16; off > 0; off >>= 1) Emax = max(Emax, __shfl_xor_sync(0xffffffffu, Emax, off));
     bad = __any_sync(0xffffffffu, bad);
   }
+  if (bad == false && row < N) {  // the diagonal itself may be non-finite
+    const int Ed = (lane == 0) ? exp_field(__ldg(P + row * N + row)) : 0;
+    bad = __any_sync(0xffffffffu, Ed == 0x7FF);
+  }
   if (bad && lane == 0) atomicOr(status, STATUS_NONFINITE);
-  if (lane == 0) erow[row] = (row < N && !bad) ? Emax - 1021 : 0;
+  if (lane == 0) {
+    erow[row] = (row < N && !bad) ? Emax - 1021 : 0;
+    pdiag[row] = (row < N && !bad) ? __ldg(P + row * N + row) : 0.0;
+  }
   Emax = max(Emax, 1);
   for (int64_t j = 2 * lane; j < Kp; j += 64) {
     uint32_t d0[K], d1[K];
-    const double x0 = (row < N && j < N && !bad) ? __ldg(P + row * N + j) : 0.0;
-    const double x1 = (row < N && j + 1 < N && !bad) ? __ldg(P + row * N + j + 1) : 0.0;
+    const double x0 = (row < N && j < N && j != row && !bad) ? __ldg(P + row * N + j) : 0.0;
+    const double x1 = (row < N && j + 1 < N && j + 1 != row && !bad) ? __ldg(P + row * N + j + 1) : 0.0;
     digits<K>(fixed_point(x0, Emax, K), d0);
     digits<K>(fixed_point(x1, Emax, K), d1);
     const size_t idx = ((size_t)row * Kp + j) >> 1;
@@ -273,7 +287,10 @@ k_col_maxexp(const double* __restrict__ Q, int64_t N, int64_t rows_per, int* __r
   const int64_t r0 = (int64_t)blockIdx.y * rows_per;
   const int64_t r1 = min(N, r0 + rows_per);
   int m = 0;
-  for (int64_t i = r0; i < r1; ++i) m = max(m, exp_field(__ldg(Q + i * N + j)));
+  for (int64_t i = r0; i < r1; ++i) {
+    const int E = exp_field(__ldg(Q + i * N + j));
+    m = max(m, (i == j && E != 0x7FF) ? 0 : E);  // the diagonal is deflated (but still checked)
+  }
   atomicMax(fexp + j, m);
 }
 
@@ -282,7 +299,8 @@ k_col_maxexp(const double* __restrict__ Q, int64_t N, int64_t rows_per, int* __r
 template <int K>
 __global__ void __launch_bounds__(256)
 k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, const int* __restrict__ fexp,
-             uint16_t* __restrict__ planes, int* __restrict__ fcol, unsigned int* __restrict__ status) {
+             uint16_t* __restrict__ planes, int* __restrict__ fcol, double* __restrict__ qdiag,
+             unsigned int* __restrict__ status) {
   __shared__ uint16_t tile[K][32][34];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t i0 = (int64_t)blockIdx.x * 32;  // rows of Q (the K dimension)
@@ -292,6 +310,7 @@ k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, co
   const bool bad = (Ej == 0x7FF);
   if (blockIdx.x == 0 && ty == 0 && j < Rp) {
     fcol[j] = (j < N && !bad) ? Ej - 1021 : 0;
+    qdiag[j] = (j < N && !bad) ? __ldg(Q + j * N + j) : 0.0;
     if (bad) atomicOr(status, STATUS_NONFINITE);
   }
   const int Emax = max(Ej, 1);
@@ -299,7 +318,7 @@ k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, co
   for (int r = 0; r < 4; ++r) {
     const int il = ty + 8 * r;
     const int64_t i = i0 + il;
-    const double x = (i < N && j < N && !bad) ? __ldg(Q + i * N + j) : 0.0;
+    const double x = (i < N && j < N && i != j && !bad) ? __ldg(Q + i * N + j) : 0.0;
     uint32_t d[K];
     digits<K>(fixed_point(x, Emax, K), d);
 #pragma unroll
@@ -365,8 +384,10 @@ struct Sched {
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-             const int* __restrict__ erow, const int* __restrict__ fcol, int64_t N, double alpha, int nslices,
-             int nksteps, const Epilogue e, unsigned int* __restrict__ status) {
+             const int* __restrict__ erow, const int* __restrict__ fcol, const double* __restrict__ P,
+             const double* __restrict__ Q, const double* __restrict__ pdiag, const double* __restrict__ qdiag,
+             int64_t N, double alpha, int nslices, int nksteps, const Epilogue e,
+             unsigned int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   uint8_t* smA = smem;
@@ -537,6 +558,7 @@ k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     if (__all_sync(0xffffffffu, ok && !*cta_err)) {
       const int64_t row = m0 + row_in_tile;
       const int er = (row < N) ? erow[row] : 0;
+      const double pii = (row < N) ? pdiag[row] : 0.0;
 #pragma unroll 1
       for (int c4 = 0; c4 < 4; ++c4) {
         uint32_t lo[32], hi[32], lw[32];
@@ -555,7 +577,12 @@ k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             const int ex = er + fcol[col] - 16 - 8 * (G_EXACT - 1);
             const double scl = (ex >= -1022 && ex <= 1023) ? __longlong_as_double((long long)(ex + 1023) << 52)
                                                           : ldexp(1.0, ex);
-            apply_epilogue(e, N, row, col, alpha * (v * scl));
+            // the deflated diagonals: + P_ii Q_ij + P_ij Q_jj - [i = j] P_ii Q_jj
+            const double qjj = qdiag[col];
+            double d = fma(pii, __ldg(Q + row * N + col), (v * scl));
+            d = fma(__ldg(P + row * N + col), qjj, d);
+            if (row == col) d = fma(-pii, qjj, d);
+            apply_epilogue(e, N, row, col, alpha * d);
           }
         }
       }
@@ -608,8 +635,9 @@ constexpr size_t SMEM_BYTES = 2 * STAGES * STAGE_BYTES + sizeof(Shared) + 1024;
 
 template <int K>
 cudaError_t split_both(const double* P, const double* Q, int64_t N, int64_t Rp, uint16_t* Ps, uint16_t* Qs,
-                       int* erow, int* fcol, int* fexp, unsigned int* status, cudaStream_t st) {
-  k_split_rows<K><<<(unsigned)((Rp + 7) / 8), 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, status);
+                       int* erow, int* fcol, int* fexp, double* pdiag, double* qdiag, unsigned int* status,
+                       cudaStream_t st) {
+  k_split_rows<K><<<(unsigned)((Rp + 7) / 8), 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
   cudaError_t err = cudaMemsetAsync(fexp, 0, (size_t)N * sizeof(int), st);
   if (err != cudaSuccess) return err;
   const int64_t colblocks = (N + 255) / 256;
@@ -618,7 +646,7 @@ cudaError_t split_both(const double* P, const double* Q, int64_t N, int64_t Rp, 
   const int64_t rows_per = (N + slabs - 1) / slabs;
   k_col_maxexp<<<dim3((unsigned)colblocks, (unsigned)slabs), 256, 0, st>>>(Q, N, rows_per, fexp);
   k_split_cols<K><<<dim3((unsigned)(Rp / 32), (unsigned)(Rp / 32)), 256, 0, st>>>(Q, N, Rp, Rp, fexp, Qs, fcol,
-                                                                                   status);
+                                                                                   qdiag, status);
   return cudaGetLastError();
 }
 
@@ -626,11 +654,13 @@ cudaError_t split_both(const double* P, const double* Q, int64_t N, int64_t Rp, 
 
 bool ozaki_supported(int64_t N) { return N >= 1 && N <= 16384; }
 
-// Layout of the workspace: 256 reserved bytes, erow[Rp], fcol[Rp], fexp[Rp], then the
-// P planes and the Q^T planes, each k x Rp x Rp BF16.
+// Layout of the workspace: 256 reserved bytes, erow[Rp], fcol[Rp], fexp[Rp], the
+// deflated diagonals pdiag[Rp], qdiag[Rp], then the P planes and the Q^T planes,
+// each k x Rp x Rp BF16.
 size_t ozaki_workspace_bytes(int64_t N, int slices) {
   const int64_t Rp = padded(N);
-  return 256 + 3 * (size_t)Rp * sizeof(int) + 256 + 2 * (size_t)slices * Rp * Rp * 2;
+  return 256 + 3 * (size_t)Rp * sizeof(int) + 256 + 2 * (size_t)Rp * sizeof(double) + 256 +
+         2 * (size_t)slices * Rp * Rp * 2;
 }
 
 namespace {
@@ -639,6 +669,8 @@ struct OzLayout {
   int* erow;
   int* fcol;
   int* fexp;
+  double* pdiag;
+  double* qdiag;
   uint16_t* Ps;
   uint16_t* Qs;
 };
@@ -651,6 +683,10 @@ OzLayout layout(void* work, int64_t N, int slices) {
   L.fexp = L.fcol + L.Rp;
   size_t off = 256 + 3 * (size_t)L.Rp * sizeof(int);
   off = (off + 255) / 256 * 256;
+  L.pdiag = reinterpret_cast<double*>(w + off);
+  L.qdiag = L.pdiag + L.Rp;
+  off += 2 * (size_t)L.Rp * sizeof(double);
+  off = (off + 255) / 256 * 256;
   L.Ps = reinterpret_cast<uint16_t*>(w + off);
   L.Qs = L.Ps + (size_t)slices * L.Rp * L.Rp;
   return L;
@@ -662,18 +698,18 @@ cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices,
   if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
   const OzLayout L = layout(work, N, slices);
   switch (slices) {
-    case 2: return split_both<2>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
-    case 3: return split_both<3>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
-    case 4: return split_both<4>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
-    case 5: return split_both<5>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
-    case 6: return split_both<6>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
-    case 7: return split_both<7>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
-    default: return split_both<8>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, flag, st);
+    case 2: return split_both<2>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 3: return split_both<3>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 4: return split_both<4>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 5: return split_both<5>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 6: return split_both<6>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 7: return split_both<7>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    default: return split_both<8>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
   }
 }
 
-cudaError_t ozaki_product(int64_t N, double alpha, const Epilogue& e, int slices, void* work, unsigned int* flag,
-                          cudaStream_t st) {
+cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e, int slices,
+                          void* work, unsigned int* flag, cudaStream_t st) {
   if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
   const OzLayout L = layout(work, N, slices);
   CUtensorMap ta, tb;
@@ -682,8 +718,8 @@ cudaError_t ozaki_product(int64_t N, double alpha, const Epilogue& e, int slices
   cudaError_t err = cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   if (err != cudaSuccess) return err;
   const dim3 grid((unsigned)(L.Rp / TILE), (unsigned)(L.Rp / TILE));
-  k_ozaki_gemm<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ta, tb, L.erow, L.fcol, N, alpha, slices, (int)(L.Rp / KSTEP),
-                                                      e, flag);
+  k_ozaki_gemm<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ta, tb, L.erow, L.fcol, P, Q, L.pdiag, L.qdiag, N, alpha,
+                                                      slices, (int)(L.Rp / KSTEP), e, flag);
   return cudaGetLastError();
 }
 

@@ -78,8 +78,8 @@ cudaError_t norm1_noalloc(const double* A, int64_t N, double* dNorm, cudaStream_
 size_t ozaki_workspace_bytes(int64_t N, int slices);
 cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices, void* work,
                         unsigned int* flag, cudaStream_t st);
-cudaError_t ozaki_product(int64_t N, double alpha, const Epilogue& e, int slices, void* work,
-                          unsigned int* flag, cudaStream_t st);
+cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
+                          int slices, void* work, unsigned int* flag, cudaStream_t st);
 bool ozaki_supported(int64_t N);
 
 // Persistent batched exp(A) (batched.cu).

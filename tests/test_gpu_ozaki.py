@@ -114,16 +114,16 @@ def test_small_workload_split(h, api):
 
 def test_identity_dominated_operands(h, api):
     # T = I + X + ... and the B_j of the scheme are dominated by their diagonal;
-    # row scales then leave the off-diagonal entries fewer bits, which is why the
-    # default is 8 slices
+    # the diagonal is deflated before slicing, so 7 slices keep full accuracy
     n = 1024
-    P = np.eye(n) + 0.05 * W.gaussian(n, 41, None)
-    Q = np.eye(n) + 0.05 * W.gaussian(n, 42, None)
-    C = empty_like_dev(n)
-    h.gemm(to_dev(P), to_dev(Q), C, api.PREC_OZAKI)      # default slice count
+    P = np.eye(n) * 1.5 + 0.05 * W.gaussian(n, 41, None)
+    Q = np.eye(n) * -0.75 + 0.05 * W.gaussian(n, 42, None)
     C64 = empty_like_dev(n)
     h.gemm(to_dev(P), to_dev(Q), C64, api.PREC_FP64)
-    assert rel_fro(to_host(C), to_host(C64)) < 1e-14
+    for k in (7, 8):
+        C = empty_like_dev(n)
+        h.gemm(to_dev(P), to_dev(Q), C, oz(api, k))
+        assert rel_fro(to_host(C), to_host(C64)) < 5e-15, k
 
 
 @pytest.mark.parametrize("idx,nonnormal", [(5, False), (5, True)])
@@ -135,3 +135,26 @@ def test_dense_4096_split_full_size(h, api, idx, nonnormal):
     want, oi = O.expm(A, "new")
     assert (info.m, info.s, info.products) == (oi.m, oi.s, oi.products)
     assert rel_fro(to_host(out), want) < 1e-12
+
+
+def test_split_product_is_closer_to_exact_than_fp64(h, api):
+    """Sampled entries of P Q computed exactly (rational arithmetic on the binary64
+    inputs): the split product (exact slice sums) lands closer to them than the
+    FP64 product, whose k-sum rounds at every step."""
+    from fractions import Fraction
+    n = 2048
+    P = W.gaussian(n, 51, None)
+    Q = W.gaussian(n, 52, None)
+    Cs, Cf = empty_like_dev(n), empty_like_dev(n)
+    h.gemm(to_dev(P), to_dev(Q), Cs, oz(api, 7))
+    h.gemm(to_dev(P), to_dev(Q), Cf, api.PREC_FP64)
+    Cs, Cf = to_host(Cs), to_host(Cf)
+    rng = np.random.default_rng(0)
+    es, ef = [], []
+    for i, j in rng.integers(0, n, size=(24, 2)):
+        exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(P[i], Q[:, j]))
+        scale = float(np.abs(P[i]) @ np.abs(Q[:, j]))
+        es.append(abs(float(Fraction(float(Cs[i, j])) - exact)) / scale)
+        ef.append(abs(float(Fraction(float(Cf[i, j])) - exact)) / scale)
+    assert max(es) < 1e-16                   # ~ the final rounding only
+    assert max(es) < max(ef)
