@@ -511,6 +511,52 @@ int orc_select(double norm, int scheme, const double* theta, int* m_out, int* s_
 }
 
 /* ------------------------------------------------------------------------ */
+/* Certified selection with power norms (an extension the paper does not    */
+/* use; it cites the work it comes from). A choice (m, s) is certified when */
+/* the paper's bound holds, ||A||_1 / 2^s <= theta_m, or when               */
+/* alpha_2 / 2^s <= theta_m with alpha_2 = max(||A^2||^(1/2), ||A^3||^(1/3)), */
+/* which bounds the same backward-error majorant because its Taylor series  */
+/* starts at degree m + 1 >= 2.                                             */
+/* ------------------------------------------------------------------------ */
+
+/* out[0..3] = ||A||_1, ||A^2||_1, ||A^3||_1, ||A^4||_1 (oracle products). */
+void orc_power_norms(int64_t n, const double* A, double* out) {
+  double *A2 = mat(n), *A3 = mat(n), *A4 = mat(n);
+  orc_gemm(n, A, A, A2);
+  orc_gemm(n, A2, A, A3);
+  orc_gemm(n, A2, A2, A4);
+  out[0] = orc_norm1(n, A);
+  out[1] = orc_norm1(n, A2);
+  out[2] = orc_norm1(n, A3);
+  out[3] = orc_norm1(n, A4);
+  free(A2); free(A3); free(A4);
+}
+
+/* Minimal products + s over (m, s) certified by either bound; ties to the
+ * smaller s. norms = {||A||, ||A^2||, ||A^3||}. */
+int orc_select_certified(const double* norms, int scheme, const double* theta, int* m_out, int* s_out) {
+  for (int k = 0; k < 3; ++k)
+    if (!isfinite(norms[k]) || norms[k] < 0.0) return 2;
+  const double alpha2 = fmax(sqrt(norms[1]), cbrt(norms[2]));
+  const int* deg = scheme == ORC_NEW ? NEW_DEG : PS_DEG;
+  const int* pi = scheme == ORC_NEW ? NEW_PI : PS_PI;
+  const int cnt = scheme == ORC_NEW ? 6 : 7;
+  int best_m = -1, best_s = 0, best_cost = 1 << 30;
+  for (int i = 0; i < cnt; ++i) {
+    const int s1 = min_squarings(norms[0], theta[deg[i]]);
+    const int s2 = min_squarings(alpha2, theta[deg[i]]);
+    const int s = s1 < s2 ? s1 : s2;
+    const int cost = pi[i] + s;
+    if (cost < best_cost || (cost == best_cost && s < best_s)) {
+      best_cost = cost; best_m = deg[i]; best_s = s;
+    }
+  }
+  *m_out = best_m;
+  *s_out = best_s;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Scaling and squaring, eq. (eses)                                          */
 /* m_force > 0 together with s_force >= 0 bypasses the selection (for       */
 /* comparing two implementations at the same (m, s)).                        */

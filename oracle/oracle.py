@@ -53,6 +53,9 @@ def lib() -> ctypes.CDLL:
         L.orc_set_mutation.argtypes = [ctypes.c_int]
         L.orc_product_count.restype = ctypes.c_longlong
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_power_norms.argtypes = [i64, dp, dp]
+        L.orc_select_certified.argtypes = [dp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]
         _lib = L
     return _lib
 
@@ -148,3 +151,21 @@ def product_count() -> int:
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def power_norms(A) -> np.ndarray:
+    """[||A||_1, ||A^2||_1, ||A^3||_1, ||A^4||_1] from oracle products."""
+    A = _sq(A)
+    out = np.zeros(4)
+    lib().orc_power_norms(A.shape[0], _p(A), _p(out))
+    return out
+
+
+def select_certified(norms, scheme: str = "new", u: float = 2.0 ** -53) -> tuple[int, int]:
+    """Cheapest (m, s) certified by ||A||_1 or by alpha_2 = max(||A^2||^(1/2), ||A^3||^(1/3))."""
+    nv = np.ascontiguousarray(np.asarray(norms, dtype=np.float64)[:3])
+    th = theta_array(scheme, u)
+    m, s = ctypes.c_int(), ctypes.c_int()
+    if lib().orc_select_certified(_p(nv), SCHEMES[scheme], _p(th), ctypes.byref(m), ctypes.byref(s)):
+        raise ValueError("non-finite norms")
+    return m.value, s.value
