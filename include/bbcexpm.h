@@ -162,6 +162,29 @@ int bbc_batch_order(const int64_t* hNs, int64_t count, int64_t* hOrder);
 int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, int64_t count, void* const* dOut,
                      int dtype, double tol, int flags, void* stream, bbc_info* dInfo);
 
+/* ---- the (m, s)-proposing network (SURVEY-level extension: the paper selects
+ * (m, s) from ||A||_1 alone; a proposal is only ever used once the backward-error
+ * bound certifies it). A 2-hidden-layer ReLU MLP in FP32 with parameters as one
+ * flat device array: W1[hid][in], b1[hid], W2[hid][hid], b2[hid], W3[out][hid],
+ * b3[out], row-major. Inputs X are [B][in] row-major; labels are class indices. */
+
+/* Number of floats of the parameter array, and of the activation workspace a
+ * batch of B needs (device, caller-owned). */
+int bbc_mlp_sizes(int in, int hid, int out, int64_t B, int64_t* n_params, int64_t* ws_floats);
+
+/* dLogits[B][out] = network(dX). dWs: workspace of bbc_mlp_sizes' ws_floats. */
+int bbc_mlp_forward(const float* dParams, int in, int hid, int out, const float* dX, int64_t B, float* dLogits,
+                    float* dWs, void* stream);
+
+/* Mean softmax cross-entropy over the batch: dGrad (n_params floats) receives its
+ * gradient, dLoss[B] the per-sample losses. */
+int bbc_mlp_grad(const float* dParams, int in, int hid, int out, const float* dX, const int* dLabels, int64_t B,
+                 float* dGrad, float* dLoss, float* dWs, void* stream);
+
+/* One Adam step (bias-corrected, step >= 1) on n parameters in place. */
+int bbc_mlp_adam(float* dParams, const float* dGrad, float* dM, float* dV, int64_t n, float lr, float beta1,
+                 float beta2, float eps, int step, void* stream);
+
 /* Kernel classes for bbc_profile_read. */
 #define BBC_KERNEL_PRODUCT 0   /* dense products (with fused epilogues) */
 #define BBC_KERNEL_NORM 1      /* the two 1-norm kernels, counted as one class */

@@ -62,6 +62,11 @@ _SIGS = {
     "bbc_batch_reserve": [_vp, _i64, _int],
     "bbc_batch_order": [ctypes.POINTER(ctypes.c_int64), _i64, ctypes.POINTER(ctypes.c_int64)],
     "bbc_expm_batched": [_vp, _vp, _vp, _i64, _vp, _int, _dbl, _int, _vp, _vp],
+    "bbc_mlp_sizes": [_int, _int, _int, _i64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "bbc_mlp_forward": [_vp, _int, _int, _int, _vp, _i64, _vp, _vp, _vp],
+    "bbc_mlp_grad": [_vp, _int, _int, _int, _vp, _vp, _i64, _vp, _vp, _vp, _vp],
+    "bbc_mlp_adam": [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                     _int, _vp],
     "bbc_profile_enable": [_vp, _int],
     "bbc_profile_read": [_vp, _int, ctypes.POINTER(ctypes.c_int64), _dp],
 }
@@ -247,6 +252,73 @@ class Batch:
         raw = self.info.cpu().numpy().tobytes()
         n = ctypes.sizeof(Info)
         return [Info.from_buffer_copy(raw[i * n:(i + 1) * n]).as_dict() for i in range(self.count)]
+
+
+class MLP:
+    """Device-side (m, s)-proposing network: parameters, Adam state and an
+    activation workspace as torch CUDA tensors; compute in the library's kernels."""
+
+    def __init__(self, n_in: int, hidden: int, n_out: int, params=None, seed: int = 0):
+        import torch
+        self.n_in, self.hidden, self.n_out = n_in, hidden, n_out
+        n, _ = self.sizes(0)
+        if params is None:
+            g = torch.Generator().manual_seed(seed)
+            chunks = []
+            for shp, fan_in in (((hidden, n_in), n_in), ((hidden,), 0), ((hidden, hidden), hidden), ((hidden,), 0),
+                                ((n_out, hidden), hidden), ((n_out,), 0)):
+                if fan_in:
+                    chunks.append(torch.randn(shp, generator=g).flatten() * (2.0 / fan_in) ** 0.5)
+                else:
+                    chunks.append(torch.zeros(shp).flatten())
+            params = torch.cat(chunks)
+        self.params = torch.as_tensor(params, dtype=torch.float32).cuda().contiguous()
+        assert self.params.numel() == n
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step = 0
+        self._ws = None
+
+    def sizes(self, B: int):
+        n = ctypes.c_int64()
+        w = ctypes.c_int64()
+        _check(_lib.bbc_mlp_sizes(self.n_in, self.hidden, self.n_out, B, ctypes.byref(n), ctypes.byref(w)))
+        return n.value, w.value
+
+    def _workspace(self, B):
+        import torch
+        _, w = self.sizes(B)
+        if self._ws is None or self._ws.numel() < w:
+            self._ws = torch.empty(max(w, 1), dtype=torch.float32, device="cuda")
+        return self._ws
+
+    def forward(self, X, stream=None):
+        import torch
+        X = X.contiguous()
+        B = X.shape[0]
+        out = torch.empty((B, self.n_out), dtype=torch.float32, device="cuda")
+        _check(_lib.bbc_mlp_forward(self.params.data_ptr(), self.n_in, self.hidden, self.n_out, X.data_ptr(), B,
+                                    out.data_ptr(), self._workspace(B).data_ptr(), _stream(stream)))
+        return out
+
+    def grad(self, X, y, stream=None):
+        import torch
+        X = X.contiguous()
+        y = y.to(torch.int32).contiguous()
+        B = X.shape[0]
+        g = torch.empty_like(self.params)
+        loss = torch.empty(B, dtype=torch.float32, device="cuda")
+        _check(_lib.bbc_mlp_grad(self.params.data_ptr(), self.n_in, self.hidden, self.n_out, X.data_ptr(),
+                                 y.data_ptr(), B, g.data_ptr(), loss.data_ptr(), self._workspace(B).data_ptr(),
+                                 _stream(stream)))
+        return g, loss
+
+    def train_step(self, X, y, lr=1e-3, stream=None):
+        g, loss = self.grad(X, y, stream)
+        self.step += 1
+        _check(_lib.bbc_mlp_adam(self.params.data_ptr(), g.data_ptr(), self.m.data_ptr(), self.v.data_ptr(),
+                                 self.params.numel(), lr, 0.9, 0.999, 1e-8, self.step, _stream(stream)))
+        return loss
 
 
 def _host_ptr(x):

@@ -604,6 +604,39 @@ int bbc_expm_host(bbc_handle h, const double* hA, int64_t N, double* hOut, doubl
   return BBC_OK;
 }
 
+int bbc_mlp_sizes(int in, int hid, int out, int64_t B, int64_t* n_params, int64_t* ws_floats) {
+  if (in < 1 || hid < 1 || out < 1 || B < 0 || !n_params || !ws_floats) return fail(BBC_INVALID_ARG, "bad MLP sizes");
+  *n_params = mlp_param_count(in, hid, out);
+  *ws_floats = mlp_workspace_floats(hid, out, B);
+  return BBC_OK;
+}
+
+int bbc_mlp_forward(const float* dParams, int in, int hid, int out, const float* dX, int64_t B, float* dLogits,
+                    float* dWs, void* stream) {
+  g_err.clear();
+  if (!dParams || !dX || !dLogits || !dWs || in < 1 || hid < 1 || out < 1 || B < 1)
+    return fail(BBC_INVALID_ARG, "bad MLP forward arguments");
+  const cudaError_t e = mlp_forward(dParams, in, hid, out, dX, B, dLogits, dWs, (cudaStream_t)stream);
+  return e == cudaSuccess ? BBC_OK : cuda_fail(e, "mlp forward");
+}
+
+int bbc_mlp_grad(const float* dParams, int in, int hid, int out, const float* dX, const int* dLabels, int64_t B,
+                 float* dGrad, float* dLoss, float* dWs, void* stream) {
+  g_err.clear();
+  if (!dParams || !dX || !dLabels || !dGrad || !dLoss || !dWs || in < 1 || hid < 1 || out < 1 || B < 1)
+    return fail(BBC_INVALID_ARG, "bad MLP gradient arguments");
+  const cudaError_t e = mlp_grad(dParams, in, hid, out, dX, dLabels, B, dGrad, dLoss, dWs, (cudaStream_t)stream);
+  return e == cudaSuccess ? BBC_OK : cuda_fail(e, "mlp grad");
+}
+
+int bbc_mlp_adam(float* dParams, const float* dGrad, float* dM, float* dV, int64_t n, float lr, float beta1,
+                 float beta2, float eps, int step, void* stream) {
+  g_err.clear();
+  if (!dParams || !dGrad || !dM || !dV || n < 1 || step < 1) return fail(BBC_INVALID_ARG, "bad Adam arguments");
+  const cudaError_t e = mlp_adam(dParams, dGrad, dM, dV, n, lr, beta1, beta2, eps, step, (cudaStream_t)stream);
+  return e == cudaSuccess ? BBC_OK : cuda_fail(e, "adam");
+}
+
 int bbc_batch_reserve(bbc_handle h, int64_t max_n, int flags) {
   int rc = begin(h);
   if (rc) return rc;

@@ -82,6 +82,16 @@ cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double al
                           int slices, void* work, unsigned int* flag, cudaStream_t st);
 bool ozaki_supported(int64_t N);
 
+// The (m, s)-proposing MLP (mlp.cu).
+int64_t mlp_param_count(int n_in, int hid, int n_out);
+int64_t mlp_workspace_floats(int hid, int n_out, int64_t B);
+cudaError_t mlp_forward(const float* P, int n_in, int hid, int n_out, const float* X, int64_t B, float* logits,
+                        float* ws, cudaStream_t st);
+cudaError_t mlp_grad(const float* P, int n_in, int hid, int n_out, const float* X, const int* y, int64_t B,
+                     float* grad, float* loss, float* ws, cudaStream_t st);
+cudaError_t mlp_adam(float* P, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                     float eps, int step, cudaStream_t st);
+
 // Persistent batched exp(A) (batched.cu).
 size_t batched_workspace_bytes(int64_t nmax, int ctas);
 int batched_ctas(int device);
