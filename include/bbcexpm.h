@@ -51,6 +51,10 @@ typedef enum {
                                   accumulated exactly; bits 8-11 = slice count k (0 -> 7) */
 #define BBC_PREC_MASK 0xF0
 #define BBC_OZAKI_SLICES(k) (((k) & 0xF) << 8)
+/* selection of (m, s) in bbc_expm_batched (bits 12-13; default: the paper's rule) */
+#define BBC_SELECT_LEARNED 0x1000  /* network proposal, certified, else the paper's rule */
+#define BBC_SELECT_ALPHA 0x2000    /* cheapest (m, s) certified by ||A|| or alpha_2 (computes A^2, A^3) */
+#define BBC_SELECT_MASK 0x3000
 
 typedef struct bbc_handle_s* bbc_handle;
 
@@ -137,7 +141,7 @@ int bbc_expm_host(bbc_handle h, const double* hA, int64_t N, double* hOut, doubl
 #define BBC_DTYPE_F32 1
 
 /* Reserve the device workspace bbc_expm_batched needs for matrices up to
- * max_n x max_n (1 <= max_n <= 256) with `flags`. Allocates; call it before
+ * max_n x max_n (1 <= max_n <= 512) with `flags`. Allocates; call it before
  * any stream capture of bbc_expm_batched. */
 int bbc_batch_reserve(bbc_handle h, int64_t max_n, int flags);
 
@@ -184,6 +188,27 @@ int bbc_mlp_grad(const float* dParams, int in, int hid, int out, const float* dX
 /* One Adam step (bias-corrected, step >= 1) on n parameters in place. */
 int bbc_mlp_adam(float* dParams, const float* dGrad, float* dM, float* dV, int64_t n, float lr, float beta1,
                  float beta2, float eps, int step, void* stream);
+
+/* (m, s) certified by the power norms norms3 = {||A||_1, ||A^2||_1, ||A^3||_1}:
+ * the cheapest choice with ||A||/2^s <= theta_m or alpha_2/2^s <= theta_m,
+ * alpha_2 = max(||A^2||^(1/2), ||A^3||^(1/3)) (a sharper sufficient condition
+ * for the same backward-error bound, from the work the paper builds on; the
+ * paper itself uses ||A|| only). Host-only. */
+int bbc_select_certified(const double* norms3, double u, int scheme, int* m, int* s);
+
+/* Install the network that BBC_SELECT_LEARNED uses on this handle: dParams as
+ * for bbc_mlp_forward with in = 5 features [log ||A||_1, three FP32 estimates
+ * of log ||A^k||_1^(1/k) for k = 2, 3, 4, log N], normalised as (f - mu) / sd
+ * (host arrays of 5); out = 6 * S classes, class c meaning degree index c / S
+ * of {1, 2, 4, 8, 12, 18} and s = c % S. The parameters stay caller-owned. */
+int bbc_batch_set_selector(bbc_handle h, const float* dParams, int hid, int out, int S, const float* hMu,
+                           const float* hSd);
+
+/* Training data for the network, in one persistent launch: per matrix the 5
+ * features (dFeat, count x 5 floats) and the exact ||A^k||_1, k = 1..4 from
+ * FP64 products (dNorms, count x 4 doubles). Arguments as bbc_expm_batched. */
+int bbc_selector_data_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, int64_t count, int dtype,
+                              float* dFeat, double* dNorms, void* stream, bbc_info* dInfo);
 
 /* Kernel classes for bbc_profile_read. */
 #define BBC_KERNEL_PRODUCT 0   /* dense products (with fused epilogues) */

@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libbbcexpm.so")
 OK, INVALID_ARG, NONFINITE_INPUT, OVERFLOW, CUDA_ERROR, TIMEOUT, UNSUPPORTED = range(7)
 SCHEME_NEW, SCHEME_PS = 0x0, 0x1
 PREC_FP64, PREC_OZAKI = 0x00, 0x10
+SELECT_LEARNED, SELECT_ALPHA = 0x1000, 0x2000
+DEGREES = (1, 2, 4, 8, 12, 18)
 U_DOUBLE = 2.0 ** -53
 U_SINGLE = 2.0 ** -24
 
@@ -67,6 +69,10 @@ _SIGS = {
     "bbc_mlp_grad": [_vp, _int, _int, _int, _vp, _vp, _i64, _vp, _vp, _vp, _vp],
     "bbc_mlp_adam": [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                      _int, _vp],
+    "bbc_select_certified": [_dp, _dbl, _int, _ip, _ip],
+    "bbc_batch_set_selector": [_vp, _vp, _int, _int, _int, ctypes.POINTER(ctypes.c_float),
+                               ctypes.POINTER(ctypes.c_float)],
+    "bbc_selector_data_batched": [_vp, _vp, _vp, _i64, _int, _vp, _vp, _vp, _vp],
     "bbc_profile_enable": [_vp, _int],
     "bbc_profile_read": [_vp, _int, ctypes.POINTER(ctypes.c_int64), _dp],
 }
@@ -117,6 +123,14 @@ def norm1_noalloc_raw(a_ptr: int, n: int, out_ptr: int, stream: int = 0) -> None
     _check(_lib.bbc_norm1_noalloc(a_ptr, n, out_ptr, stream))
 
 
+def select_certified(norms3, u: float = U_DOUBLE, scheme: int = SCHEME_NEW) -> tuple[int, int]:
+    """Cheapest (m, s) certified by ||A||_1 or alpha_2 from {||A||, ||A^2||, ||A^3||}."""
+    arr = (ctypes.c_double * 3)(*[float(x) for x in list(norms3)[:3]])
+    m, s = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.bbc_select_certified(arr, u, scheme, ctypes.byref(m), ctypes.byref(s)))
+    return m.value, s.value
+
+
 def _stream(stream) -> int:
     if stream is None:
         import torch
@@ -159,6 +173,22 @@ class Handle:
         ms = ctypes.c_double()
         _check(_lib.bbc_profile_read(self._h, kind, ctypes.byref(n), ctypes.byref(ms)))
         return n.value, ms.value
+
+    def batch_set_selector(self, net: "MLP", S: int, mu, sd) -> None:
+        mu_a = (ctypes.c_float * 5)(*[float(x) for x in mu])
+        sd_a = (ctypes.c_float * 5)(*[float(x) for x in sd])
+        self._selector = net  # keep the parameters alive while installed
+        _check(_lib.bbc_batch_set_selector(self._h, net.params.data_ptr(), net.hidden, net.n_out, S, mu_a, sd_a))
+
+    def selector_data(self, batch: "Batch", stream=None):
+        """(features [count, 5] float32, exact norms [count, 4] float64) as CUDA tensors."""
+        import torch
+        feat = torch.empty((batch.count, 5), dtype=torch.float32, device="cuda")
+        norms = torch.empty((batch.count, 4), dtype=torch.float64, device="cuda")
+        _check(_lib.bbc_selector_data_batched(self._h, batch.a_ptrs.data_ptr(), batch.ns.data_ptr(), batch.count,
+                                              batch.dtype, feat.data_ptr(), norms.data_ptr(), _stream(stream),
+                                              batch.info.data_ptr()))
+        return feat, norms
 
     def batch_reserve(self, max_n: int, flags: int = 0) -> None:
         _check(_lib.bbc_batch_reserve(self._h, max_n, flags))
@@ -229,8 +259,10 @@ class Batch:
     """Device-side descriptor arrays for bbc_expm_batched, built from lists of
     CUDA tensors (inputs and outputs stay owned by the caller)."""
 
-    def __init__(self, inputs, outputs):
+    def __init__(self, inputs, outputs=None):
         import torch
+        if outputs is None:  # feature / norm extraction only
+            outputs = inputs
         if len(inputs) != len(outputs):
             raise ValueError("inputs and outputs differ in length")
         dt = inputs[0].dtype if inputs else torch.float32

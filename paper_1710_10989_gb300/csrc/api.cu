@@ -35,6 +35,7 @@ struct bbc_handle_s {
   std::vector<Rec> recs;       // recorded in this profiling window
   std::vector<cudaEvent_t> pool;
   int64_t batch_nmax = 0;         // reservation of the batched workspace
+  BatchSelector selector = {};    // network for BBC_SELECT_LEARNED (mode 0: none installed)
   int batch_ctas = 0;
   void* batch_work = nullptr;
   int64_t io_n = 0;               // N the host-call staging buffers are sized for
@@ -276,7 +277,8 @@ int check_flags(int flags) {
   const int prec = flags & BBC_PREC_MASK;
   if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS) return fail(BBC_INVALID_ARG, "unknown scheme");
   if (prec != BBC_PREC_FP64 && prec != BBC_PREC_OZAKI) return fail(BBC_INVALID_ARG, "unknown precision");
-  if (flags & ~0xFFF) return fail(BBC_INVALID_ARG, "unknown flag bits");
+  if (flags & ~0x3FFF) return fail(BBC_INVALID_ARG, "unknown flag bits");
+  if ((flags & BBC_SELECT_MASK) == BBC_SELECT_MASK) return fail(BBC_INVALID_ARG, "two selectors requested");
   if (prec == BBC_PREC_OZAKI) {
     const int k = (flags >> 8) & 0xF;
     if (k != 0 && (k < 2 || k > 8)) return fail(BBC_INVALID_ARG, "Ozaki slice count must be 2..8");
@@ -640,7 +642,7 @@ int bbc_mlp_adam(float* dParams, const float* dGrad, float* dM, float* dV, int64
 int bbc_batch_reserve(bbc_handle h, int64_t max_n, int flags) {
   int rc = begin(h);
   if (rc) return rc;
-  if (max_n < 1 || max_n > 256) return fail(BBC_INVALID_ARG, "batched max_n must be in 1..256");
+  if (max_n < 1 || max_n > 512) return fail(BBC_INVALID_ARG, "batched max_n must be in 1..512");
   if ((rc = check_flags(flags))) return rc;
   if ((flags & BBC_SCHEME_MASK) != BBC_SCHEME_NEW || (flags & BBC_PREC_MASK) != BBC_PREC_FP64)
     return fail(BBC_UNSUPPORTED, "batched path: scheme NEW with FP64 products only");
@@ -655,6 +657,68 @@ int bbc_batch_reserve(bbc_handle h, int64_t max_n, int flags) {
     h->batch_ctas = ctas;
     h->batch_nmax = max_n;
   }
+  return BBC_OK;
+}
+
+int bbc_select_certified(const double* norms3, double u, int scheme, int* m, int* s) {
+  if (!norms3 || !m || !s || !valid_u(u)) return fail(BBC_INVALID_ARG, "bad certified selection query");
+  if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS) return fail(BBC_INVALID_ARG, "unknown scheme");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(norms3[k]) || norms3[k] < 0) return fail(BBC_NONFINITE_INPUT, "norm not finite");
+  const double alpha2 = std::fmax(std::sqrt(norms3[1]), std::cbrt(norms3[2]));
+  const int *deg, *prod;
+  const int cnt = scheme_degrees(scheme, &deg, &prod);
+  int bm = -1, bs = 0, bc = 1 << 30;
+  for (int i = 0; i < cnt; ++i) {
+    const double th = theta_cached(deg[i], u);
+    const int si = std::min(least_squarings(norms3[0], th), least_squarings(alpha2, th));
+    const int cost = prod[i] + si;
+    if (cost < bc || (cost == bc && si < bs)) { bc = cost; bm = deg[i]; bs = si; }
+  }
+  *m = bm;
+  *s = bs;
+  return BBC_OK;
+}
+
+int bbc_batch_set_selector(bbc_handle h, const float* dParams, int hid, int out, int S, const float* hMu,
+                           const float* hSd) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!dParams || !hMu || !hSd || hid < 1 || hid > 256 || S < 1 || out != 6 * S || out > 256)
+    return fail(BBC_INVALID_ARG, "bad selector network (hid <= 256, out = 6 S <= 256)");
+  std::lock_guard<std::mutex> lk(h->mu);
+  BatchSelector sel = {};
+  sel.mode = 1;
+  sel.params = dParams;
+  sel.hid = hid;
+  sel.out = out;
+  sel.S = S;
+  for (int i = 0; i < 5; ++i) { sel.mu[i] = hMu[i]; sel.sd[i] = hSd[i]; }
+  h->selector = sel;
+  return BBC_OK;
+}
+
+int bbc_selector_data_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, int64_t count, int dtype,
+                              float* dFeat, double* dNorms, void* stream, bbc_info* dInfo) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (count < 0 || (count > 0 && (!dA || !dNs || !dFeat || !dNorms))) return fail(BBC_INVALID_ARG, "bad data arguments");
+  if (dtype != BBC_DTYPE_F32 && dtype != BBC_DTYPE_F64) return fail(BBC_INVALID_ARG, "unknown dtype");
+  if (count == 0) return BBC_OK;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (!h->batch_work) return fail(BBC_INVALID_ARG, "call bbc_batch_reserve first");
+  static const int deg[6] = {1, 2, 4, 8, 12, 18};
+  double theta[6];
+  for (int i = 0; i < 6; ++i) theta[i] = theta_cached(deg[i], std::ldexp(1.0, -53));
+  BatchSelector sel = {};
+  sel.mode = 3;
+  sel.feat_out = dFeat;
+  sel.norms_out = dNorms;
+  cudaStream_t st = (cudaStream_t)stream;
+  LaunchScope scope(h, BBC_KERNEL_BATCHED, st);
+  const cudaError_t e = batched_launch(dA, nullptr, dNs, count, h->batch_nmax, dtype, theta, h->batch_work,
+                                       h->batch_ctas, dInfo, st, &sel);
+  if (e != cudaSuccess) return cuda_fail(e, "selector data launch");
   return BBC_OK;
 }
 
@@ -684,10 +748,20 @@ int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, in
   static const int deg[6] = {1, 2, 4, 8, 12, 18};
   double theta[6];
   for (int i = 0; i < 6; ++i) theta[i] = theta_cached(deg[i], u);
+  BatchSelector sel = {};
+  const BatchSelector* psel = nullptr;
+  if (flags & BBC_SELECT_LEARNED) {
+    if (h->selector.mode != 1) return fail(BBC_INVALID_ARG, "no network installed (bbc_batch_set_selector)");
+    sel = h->selector;
+    psel = &sel;
+  } else if (flags & BBC_SELECT_ALPHA) {
+    sel.mode = 2;
+    psel = &sel;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   LaunchScope scope(h, BBC_KERNEL_BATCHED, st);
   const cudaError_t e = batched_launch(dA, dOut, dNs, count, h->batch_nmax, dtype, theta, h->batch_work,
-                                       h->batch_ctas, dInfo, st);
+                                       h->batch_ctas, dInfo, st, psel);
   if (e != cudaSuccess) return cuda_fail(e, "batched launch");
   return BBC_OK;
 }

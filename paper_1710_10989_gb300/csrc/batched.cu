@@ -18,6 +18,18 @@
 // on the FP64 pipe (4 x 4 register blocks, 16-deep shared-memory K slabs), each
 // element then passing through the same fused linear-combination epilogue as
 // the single-matrix path (internal.h).
+//
+// Selection modes (per launch):
+//  plain    (m, s) from ||A||_1 and theta_m(u) (the paper's rule);
+//  learned  a small MLP proposes (m, s) from cheap features (log ||A||_1, FP32
+//           estimates of log ||A^k||_1^(1/k) for k = 2, 3, 4 from random-sign
+//           mat-vec chains, log N). The proposal is used only if certified: by
+//           ||A||_1 / 2^s <= theta_m, else by alpha_2 / 2^s <= theta_m with
+//           alpha_2 = max(||A^2||^(1/2), ||A^3||^(1/3)) from exact FP64 powers
+//           (which T12 / T18 then reuse); otherwise the plain rule runs;
+//  alpha    always compute A^2, A^3 and take the cheapest (m, s) certified by
+//           either bound (the closed-form rule the network is compared with);
+//  data     no exponential: features and exact ||A^k||_1, k = 1..4, for training.
 #include <math.h>
 #include <stdint.h>
 
@@ -28,6 +40,8 @@
 namespace bbc {
 
 constexpr int BATCH_THREADS = 256;
+constexpr int BATCH_MAX_N = 512;     // largest matrix the batched path serves
+constexpr int MLP_MAX = 256;         // widest hidden / output layer of in-kernel inference
 constexpr int BATCH_SLOTS = 12;      // W0..W9 (W9 = squaring buffer), A64, T
 constexpr int BSL_A = 10, BSL_T = 11;
 constexpr int BATCH_MAX_STEPS = 8;
@@ -52,6 +66,12 @@ struct BProg {
 };
 
 __constant__ BProg c_progs[BATCH_PROGS];
+__constant__ BProg c_progs_pre[2];  // T12, T18 starting from A^2 (W0) and A^3 (W1), unscaled
+
+constexpr int NFEAT = 5;
+enum { MODE_PLAIN = 0, MODE_LEARNED = 1, MODE_ALPHA = 2, MODE_DATA = 3 };
+// bbc_info.selector values
+enum { SEL_PLAIN = 0, SEL_LEARNED_NORM = 2, SEL_LEARNED_ALPHA = 3, SEL_LEARNED_REJECTED = 4, SEL_ALPHA = 5 };
 
 struct BatchArgs {
   const void* const* A;    // device array of device pointers
@@ -65,6 +85,12 @@ struct BatchArgs {
   double* work;            // per-CTA slices of BATCH_SLOTS * nmax^2 doubles
   unsigned int* counter;   // work queue head (zeroed by the launch)
   bbc_info* info;          // may be null
+  int mode;
+  const float* mlp;        // learned mode: parameters W1 b1 W2 b2 W3 b3
+  int mlp_hid, mlp_out, mlp_S;   // classes: m index * mlp_S + s
+  float mu[NFEAT], sd[NFEAT];    // feature normalisation
+  float* feat_out;         // data mode: count x NFEAT
+  double* norms_out;       // data mode: count x 4
 };
 
 namespace {
@@ -135,15 +161,122 @@ __device__ void block_lincomb(int N, const Epilogue& e) {
   for (int idx = threadIdx.x; idx < N * N; idx += BATCH_THREADS) apply_epilogue(e, N, idx / N, idx % N, 0.0);
 }
 
+// max_j sum_i |M_ij| over an N x N binary64 matrix (one column per thread).
+__device__ double block_norm1(const double* M, int N, double* red) {
+  double best = 0.0;
+  for (int j = threadIdx.x; j < N; j += BATCH_THREADS) {
+    double s = 0.0;
+    for (int i = 0; i < N; ++i) s += fabs(M[(int64_t)i * N + j]);
+    best = (s > best || isnan(s)) ? s : best;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double o = __shfl_xor_sync(0xffffffffu, best, off);
+    best = (o > best || isnan(o)) ? o : best;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < BATCH_THREADS / 32; ++w) r = (red[w] > r || isnan(red[w])) ? red[w] : r;
+  __syncthreads();
+  return r;
+}
+
+// Cheap features: est_k = max over 4 random-sign vectors x of ||A^k x||_1 / ||x||_1
+// (a lower bound of ||A^k||_1), from FP32 mat-vec chains, one warp per row.
+// f = [log ||A||_1, log est_2 / 2, log est_3 / 3, log est_4 / 4, log N].
+__device__ void block_features(const double* A, int N, double norm1, float* y0, float* y1, float* est, float* f) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int e = threadIdx.x; e < 4 * N; e += BATCH_THREADS) {
+    const unsigned h = (unsigned)(e >> 2) * 2654435761u ^ (unsigned)(e & 3) * 40503u;
+    y0[e] = ((h >> 15) & 1u) ? 1.f : -1.f;  // x[j][v] at e = 4 j + v
+  }
+  __syncthreads();
+  float* src = y0;
+  float* dst = y1;
+  for (int k = 1; k <= 4; ++k) {
+    for (int i = warp; i < N; i += BATCH_THREADS / 32) {
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      for (int j = lane; j < N; j += 32) {
+        const float a = (float)A[(int64_t)i * N + j];
+        a0 = fmaf(a, src[4 * j + 0], a0);
+        a1 = fmaf(a, src[4 * j + 1], a1);
+        a2 = fmaf(a, src[4 * j + 2], a2);
+        a3 = fmaf(a, src[4 * j + 3], a3);
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+        a3 += __shfl_xor_sync(0xffffffffu, a3, off);
+      }
+      if (lane == 0) { dst[4 * i] = a0; dst[4 * i + 1] = a1; dst[4 * i + 2] = a2; dst[4 * i + 3] = a3; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      float sum = 0.f;
+      for (int i = 0; i < N; ++i) sum += fabsf(dst[4 * i + threadIdx.x]);
+      est[(k - 1) * 4 + threadIdx.x] = sum / (float)N;
+    }
+    __syncthreads();
+    float* t = src; src = dst; dst = t;
+  }
+  if (threadIdx.x == 0) {
+    f[0] = (float)log(fmax(norm1, 1e-300));
+    for (int k = 2; k <= 4; ++k) {
+      const float* e4 = est + (k - 1) * 4;
+      const float e = fmaxf(fmaxf(e4[0], e4[1]), fmaxf(e4[2], e4[3]));
+      f[k - 1] = (float)(log(fmax((double)e, 1e-300)) / k);
+    }
+    f[4] = (float)log((double)N);
+  }
+  __syncthreads();
+}
+
+// argmax of the network's logits on one feature vector (all threads take part)
+__device__ int block_mlp_argmax(const BatchArgs& a, const float* f, float* h1, float* h2, float* lg) {
+  const int hid = a.mlp_hid, out = a.mlp_out;
+  const float *W1 = a.mlp, *b1 = W1 + hid * NFEAT, *W2 = b1 + hid, *b2 = W2 + hid * hid;
+  const float *W3 = b2 + hid, *b3 = W3 + out * hid;
+  for (int t = threadIdx.x; t < hid; t += BATCH_THREADS) {
+    float acc = b1[t];
+    for (int i = 0; i < NFEAT; ++i) acc = fmaf(W1[t * NFEAT + i], (f[i] - a.mu[i]) / a.sd[i], acc);
+    h1[t] = fmaxf(acc, 0.f);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < hid; t += BATCH_THREADS) {
+    float acc = b2[t];
+    for (int j = 0; j < hid; ++j) acc = fmaf(W2[t * hid + j], h1[j], acc);
+    h2[t] = fmaxf(acc, 0.f);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < out; t += BATCH_THREADS) {
+    float acc = b3[t];
+    for (int j = 0; j < hid; ++j) acc = fmaf(W3[t * hid + j], h2[j], acc);
+    lg[t] = acc;
+  }
+  __syncthreads();
+  int best = 0;
+  for (int t = 1; t < out; ++t) best = lg[t] > lg[best] ? t : best;
+  __syncthreads();
+  return best;
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchArgs args) {
+
   __shared__ GemmSmem sm;
   __shared__ Epilogue s_epi;
   __shared__ double s_red[BATCH_THREADS / 32];
-  __shared__ int s_idx, s_m, s_s, s_prog, s_status;
+  __shared__ int s_idx, s_m, s_s, s_prog, s_status, s_sel, s_pre;
   __shared__ double s_norm;
   __shared__ unsigned int s_flag;
+  __shared__ float s_feat[NFEAT];
+  __shared__ float s_h1[MLP_MAX], s_h2[MLP_MAX], s_lg[MLP_MAX];
+  __shared__ float s_y[2][4 * BATCH_MAX_N];
+  __shared__ float s_est[16];
+  __shared__ double s_pnorm[4];
+  __shared__ int s_pow, s_prop_m, s_prop_s;
 
   const int tid = threadIdx.x;
   const size_t nn_max = (size_t)args.nmax * args.nmax;
@@ -192,22 +325,93 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchAr
       for (int w = 0; w < BATCH_THREADS / 32; ++w) nrm = (s_red[w] > nrm || isnan(s_red[w])) ? s_red[w] : nrm;
       s_norm = nrm;
       s_flag = 0u;
-      if (!isfinite(nrm)) {
-        s_status = BBC_NONFINITE_INPUT;
-      } else {
-        s_status = BBC_OK;
-        int bm = 0, bs = 0, bc = 1 << 30;
-        for (int i = 0; i < BATCH_PROGS; ++i) {
-          const int si = least_squarings_dev(nrm, args.theta[i]);
-          const int cost = args.prod[i] + si;
-          if (cost < bc || (cost == bc && si < bs)) { bc = cost; bm = i; bs = si; }
+      s_pre = 0;
+      s_pow = 0;
+      s_sel = SEL_PLAIN;
+      s_status = isfinite(nrm) ? BBC_OK : BBC_NONFINITE_INPUT;
+    }
+    __syncthreads();
+    if (s_status == BBC_OK && (args.mode == MODE_LEARNED || args.mode == MODE_DATA))
+      block_features(A64, N, s_norm, s_y[0], s_y[1], s_est, s_feat);
+    if (s_status == BBC_OK && args.mode == MODE_LEARNED) {
+      const int c = block_mlp_argmax(args, s_feat, s_h1, s_h2, s_lg);
+      if (tid == 0) {
+        s_prop_m = c / args.mlp_S;
+        s_prop_s = c % args.mlp_S;
+        // the paper's own bound already certifies the proposal: no powers needed
+        s_pow = !(s_prop_m < BATCH_PROGS && ldexp(s_norm, -s_prop_s) <= args.theta[s_prop_m]);
+      }
+    }
+    if (tid == 0 && s_status == BBC_OK && (args.mode == MODE_ALPHA || args.mode == MODE_DATA)) s_pow = 1;
+    __syncthreads();
+    // exact powers A^2 -> W0, A^3 -> W1 (and A^4 -> W2 for training data) when a bound needs them
+    if (s_status == BBC_OK && s_pow) {
+      double* W0p = slots;
+      const int npow = args.mode == MODE_DATA ? 3 : 2;
+      for (int k = 0; k < npow; ++k) {
+        if (tid == 0) {
+          s_epi.nout = 1;
+          s_epi.flag = nullptr;
+          s_epi.o[0].out = slots + (size_t)k * nn_max;
+          s_epi.o[0].cv = 1.0;
+          s_epi.o[0].cI = 0.0;
+          s_epi.o[0].nt = 0;
         }
-        s_prog = bm;
-        s_m = args.deg[bm];
-        s_s = bs;
+        __syncthreads();
+        // A^2 = A A, A^3 = A^2 A, A^4 = A^2 A^2
+        block_gemm_f64(k == 0 ? A64 : W0p, k == 2 ? W0p : A64, N, 1.0, s_epi, sm);
+        __syncthreads();
+        const double nk = block_norm1(slots + (size_t)k * nn_max, N, s_red);
+        if (tid == 0) s_pnorm[k + 1] = nk;
       }
     }
     __syncthreads();
+    if (tid == 0 && s_status == BBC_OK && args.mode != MODE_DATA) {
+      const double nrm = s_norm;
+      const double alpha2 = s_pow ? fmax(sqrt(s_pnorm[1]), cbrt(s_pnorm[2])) * (1.0 + 1e-12) : INFINITY;
+      int bm = 0, bs = 0, bc = 1 << 30;
+      bool done = false;
+      if (args.mode == MODE_LEARNED && s_prop_m < BATCH_PROGS) {
+        if (ldexp(nrm, -s_prop_s) <= args.theta[s_prop_m]) {
+          bm = s_prop_m; bs = s_prop_s; done = true; s_sel = SEL_LEARNED_NORM;
+        } else if (ldexp(alpha2, -s_prop_s) <= args.theta[s_prop_m]) {
+          bm = s_prop_m; bs = s_prop_s; done = true; s_sel = SEL_LEARNED_ALPHA;
+        } else {
+          s_sel = SEL_LEARNED_REJECTED;
+        }
+      }
+      if (!done) {
+        for (int i = 0; i < BATCH_PROGS; ++i) {
+          int si = least_squarings_dev(nrm, args.theta[i]);
+          if (args.mode == MODE_ALPHA) si = min(si, least_squarings_dev(alpha2, args.theta[i]));
+          const int cost = args.prod[i] + si;
+          if (cost < bc || (cost == bc && si < bs)) { bc = cost; bm = i; bs = si; }
+        }
+        if (args.mode == MODE_ALPHA) s_sel = SEL_ALPHA;
+      }
+      s_prog = bm;
+      s_m = args.deg[bm];
+      s_s = bs;
+      s_pre = (s_pow && (args.deg[bm] == 12 || args.deg[bm] == 18)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (args.mode == MODE_DATA) {
+      if (tid == 0) {
+        const bool ok = s_status == BBC_OK;
+        args.norms_out[idx * 4 + 0] = ok ? s_norm : NAN;
+        for (int k = 1; k < 4; ++k) args.norms_out[idx * 4 + k] = ok ? s_pnorm[k] : NAN;
+        for (int k = 0; k < NFEAT; ++k) args.feat_out[idx * NFEAT + k] = ok ? s_feat[k] : NAN;
+        if (args.info) {
+          bbc_info inf = {};
+          inf.norm1 = s_norm;
+          inf.products = ok ? 3 : 0;
+          inf.status = s_status;
+          args.info[idx] = inf;
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     if (s_status != BBC_OK) {
       if (tid == 0 && args.info) {
         bbc_info inf = {};
@@ -220,7 +424,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchAr
     }
     const int s = s_s;
     const double sig = ldexp(1.0, -s);
-    const BProg& prog = c_progs[s_prog];
+    const BProg& prog = s_pre ? c_progs_pre[s_m == 18 ? 1 : 0] : c_progs[s_prog];
+    const int extra_products = s_pow ? 2 : 0;
     double* Tslot = slots + (size_t)BSL_T * nn_max;
     double* SQ = slots + (size_t)SL_SQ * nn_max;
 
@@ -298,7 +503,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchAr
       bbc_info inf = {};
       inf.m = s_m;
       inf.s = s;
-      inf.products = prog.products + s;
+      inf.products = prog.products + s + extra_products;
+      inf.selector = s_sel;
       inf.norm1 = s_norm;
       inf.status = s_flag ? BBC_OVERFLOW : BBC_OK;
       args.info[idx] = inf;
@@ -320,42 +526,64 @@ int batched_ctas(int device) {
   return sms;
 }
 
-// Upload the reduced-product programs (s = 0 coefficients with sigma powers).
+namespace {
+// s = 0 coefficients with the powers of 2^-s each coefficient / alpha carries:
+// given explicitly (sp, ap >= 0) or, for the plain programs, one per use of A.
+bool to_device_program(const Program& p, int m, BProg* out) {
+  if ((int)p.steps.size() > BATCH_MAX_STEPS) return false;
+  out->m = m;
+  out->products = p.products;
+  out->nsteps = (int)p.steps.size();
+  for (size_t k = 0; k < p.steps.size(); ++k) {
+    const StepS& st = p.steps[k];
+    BStep& b = out->st[k];
+    b.P = st.P;
+    b.Q = st.Q;
+    b.alpha_pow = st.ap >= 0 ? st.ap : (st.P == SL_A) + (st.Q == SL_A);
+    b.nout = st.nout;
+    for (int o = 0; o < st.nout; ++o) {
+      b.o[o].dst = st.o[o].dst;
+      b.o[o].cv = st.o[o].cv;
+      b.o[o].cI = st.o[o].cI;
+      b.o[o].nt = st.o[o].nt;
+      for (int t = 0; t < st.o[o].nt; ++t) {
+        const TermS& ts = st.o[o].t[t];
+        b.o[o].slot[t] = ts.slot;
+        b.o[o].c[t] = ts.c;
+        b.o[o].sigma_pow[t] = ts.sp >= 0 ? ts.sp : (ts.slot == SL_A ? 1 : 0);
+      }
+    }
+  }
+  return true;
+}
+}  // namespace
+
+// Upload the reduced-product programs: plain ones and T12 / T18 that start from
+// precomputed A^2, A^3.
 cudaError_t batched_upload_programs() {
   static const int deg[BATCH_PROGS] = {1, 2, 4, 8, 12, 18};
   BProg h[BATCH_PROGS] = {};
   for (int i = 0; i < BATCH_PROGS; ++i) {
     Program p;
-    if (!make_program(BBC_SCHEME_NEW, deg[i], 0, &p) || (int)p.steps.size() > BATCH_MAX_STEPS)
+    if (!make_program(BBC_SCHEME_NEW, deg[i], 0, &p) || !to_device_program(p, deg[i], &h[i]))
       return cudaErrorInvalidValue;
-    h[i].m = deg[i];
-    h[i].products = p.products;
-    h[i].nsteps = (int)p.steps.size();
-    for (size_t k = 0; k < p.steps.size(); ++k) {
-      const StepS& st = p.steps[k];
-      BStep& b = h[i].st[k];
-      b.P = st.P;
-      b.Q = st.Q;
-      b.alpha_pow = (st.P == SL_A) + (st.Q == SL_A);
-      b.nout = st.nout;
-      for (int o = 0; o < st.nout; ++o) {
-        b.o[o].dst = st.o[o].dst;
-        b.o[o].cv = st.o[o].cv;
-        b.o[o].cI = st.o[o].cI;
-        b.o[o].nt = st.o[o].nt;
-        for (int t = 0; t < st.o[o].nt; ++t) {
-          b.o[o].slot[t] = st.o[o].t[t].slot;
-          b.o[o].c[t] = st.o[o].t[t].c;
-          b.o[o].sigma_pow[t] = st.o[o].t[t].slot == SL_A ? 1 : 0;
-        }
-      }
-    }
   }
-  return cudaMemcpyToSymbol(c_progs, h, sizeof h);
+  cudaError_t e = cudaMemcpyToSymbol(c_progs, h, sizeof h);
+  if (e != cudaSuccess) return e;
+  BProg pre[2] = {};
+  const int pm[2] = {12, 18};
+  for (int i = 0; i < 2; ++i) {
+    Program p;
+    int a2, a3;
+    if (!make_prefilled_program(pm[i], &p, &a2, &a3) || a2 != 0 || a3 != 1 || !to_device_program(p, pm[i], &pre[i]))
+      return cudaErrorInvalidValue;
+  }
+  return cudaMemcpyToSymbol(c_progs_pre, pre, sizeof pre);
 }
 
 cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t* Ns, int64_t count, int64_t nmax,
-                           int dtype, const double* theta, void* work, int ctas, bbc_info* info, cudaStream_t st) {
+                           int dtype, const double* theta, void* work, int ctas, bbc_info* info, cudaStream_t st,
+                           const BatchSelector* sel) {
   static const int deg[BATCH_PROGS] = {1, 2, 4, 8, 12, 18};
   static const int prod[BATCH_PROGS] = {0, 1, 2, 3, 4, 5};
   BatchArgs a = {};
@@ -369,6 +597,21 @@ cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t
   a.counter = static_cast<unsigned int*>(work);
   a.work = reinterpret_cast<double*>(static_cast<char*>(work) + 256);
   a.info = info;
+  a.mode = MODE_PLAIN;
+  if (sel) {
+    a.mode = sel->mode;
+    a.mlp = sel->params;
+    a.mlp_hid = sel->hid;
+    a.mlp_out = sel->out;
+    a.mlp_S = sel->S > 0 ? sel->S : 1;
+    for (int i = 0; i < NFEAT; ++i) { a.mu[i] = sel->mu[i]; a.sd[i] = sel->sd[i] != 0.f ? sel->sd[i] : 1.f; }
+    a.feat_out = sel->feat_out;
+    a.norms_out = sel->norms_out;
+    if (a.mode == MODE_LEARNED && (!a.mlp || a.mlp_hid < 1 || a.mlp_hid > MLP_MAX || a.mlp_out < 1 ||
+                                   a.mlp_out > MLP_MAX))
+      return cudaErrorInvalidValue;
+    if (a.mode == MODE_DATA && (!a.feat_out || !a.norms_out)) return cudaErrorInvalidValue;
+  }
   cudaError_t err = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
   k_batched_expm<<<ctas, BATCH_THREADS, 0, st>>>(a);

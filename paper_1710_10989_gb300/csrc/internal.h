@@ -96,8 +96,16 @@ cudaError_t mlp_adam(float* P, const float* g, float* m, float* v, int64_t n, fl
 size_t batched_workspace_bytes(int64_t nmax, int ctas);
 int batched_ctas(int device);
 cudaError_t batched_upload_programs();
+struct BatchSelector {
+  int mode;                 // 1 learned, 2 alpha rule, 3 training data
+  const float* params;      // network parameters (learned)
+  int hid, out, S;          // hidden width, classes, s values per degree
+  float mu[5], sd[5];       // feature normalisation
+  float* feat_out;          // training data: count x 5
+  double* norms_out;        // training data: count x 4
+};
 cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t* Ns, int64_t count,
                            int64_t nmax, int dtype, const double* theta, void* work, int ctas,
-                           bbc_info* info, cudaStream_t st);
+                           bbc_info* info, cudaStream_t st, const BatchSelector* sel = nullptr);
 
 }  // namespace bbc

@@ -82,6 +82,64 @@ void ps_tail(Program* p, int q, int r, int ys, int acc, int spare, double sig) {
 
 }  // namespace
 
+bool make_prefilled_program(int m, Program* p, int* a2_slot, int* a3_slot) {
+  p->m = m;
+  p->products = 0;
+  p->steps.clear();
+  auto term = [](Out& o, int slot, double c, int sp) -> Out& {
+    if (c != 0.0) { o.o.t[o.o.nt] = TermS{slot, c}; o.o.t[o.o.nt].sp = sp; o.o.nt++; }
+    return o;
+  };
+  auto zero_powers = [](Step& st) {
+    for (int o = 0; o < st.s.nout; ++o)
+      for (int t = 0; t < st.s.o[o].nt; ++t) st.s.o[o].t[t].sp = 0;
+    st.s.ap = 0;
+  };
+  if (m == 18) {  // A^2 in W0, A^3 in W1
+    *a2_slot = W0;
+    *a3_slot = W1;
+    Step st(W1, W1, 1.0);  // v = (2^-3s A^3)^2 = X6
+    st.s.ap = 6;
+    Out b1(W2, 0.0, T18A1[0]);
+    term(b1, SL_A, T18A1[1], 1); term(b1, W0, T18A1[2], 2); term(b1, W1, T18A1[3], 3);
+    st.out(b1);
+    for (int j = 0; j < 4; ++j) {
+      Out b(W3 + j, T18B[4][j], T18B[0][j]);
+      term(b, SL_A, T18B[1][j], 1); term(b, W0, T18B[2][j], 2); term(b, W1, T18B[3][j], 3);
+      st.out(b);
+    }
+    add(p, st);
+    Step s4 = Step(W2, W6, 1.0).out(Out(W7, 1.0).t(W5, 1.0)).out(Out(W8, 1.0).t(W5, 1.0).t(W4, 1.0));
+    zero_powers(s4);
+    add(p, s4);
+    Step s5 = Step(W8, W7, 1.0).out(Out(SL_T, 1.0).t(W3, 1.0));
+    zero_powers(s5);
+    add(p, s5);
+    return true;
+  }
+  if (m == 12) {  // A^2 in W0, A^3 in W1; B_1..B_4 -> W2..W5
+    *a2_slot = W0;
+    *a3_slot = W1;
+    Step st(-1, -1, 0.0);  // B_j = a0j I + a1j X + a2j X2 + a3j X3, no product
+    st.s.ap = 0;
+    for (int j = 0; j < 4; ++j) {
+      Out b(W2 + j, 0.0, T12A[0][j]);
+      term(b, SL_A, T12A[1][j], 1); term(b, W0, T12A[2][j], 2); term(b, W1, T12A[3][j], 3);
+      st.out(b);
+    }
+    add(p, st);
+    // A6 = B3 + B4^2 -> W6;  B2 + A6 -> W7;  T12 = B1 + (B2 + A6) A6
+    Step s3 = Step(W5, W5, 1.0).out(Out(W6, 1.0).t(W4, 1.0)).out(Out(W7, 1.0).t(W4, 1.0).t(W3, 1.0));
+    zero_powers(s3);
+    add(p, s3);
+    Step s4 = Step(W7, W6, 1.0).out(Out(SL_T, 1.0).t(W2, 1.0));
+    zero_powers(s4);
+    add(p, s4);
+    return true;
+  }
+  return false;
+}
+
 int scheme_degrees(int scheme, const int** deg, const int** products) {
   if (scheme == BBC_SCHEME_PS) { *deg = PS_DEG; *products = PS_PROD; return 7; }
   *deg = NEW_DEG; *products = NEW_PROD; return 6;

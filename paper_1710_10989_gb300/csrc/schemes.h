@@ -18,7 +18,11 @@ constexpr int SL_T = 101;  // the polynomial's result
 constexpr int NUM_WORK_SLOTS = 10;  // W0..W9 (W9 is the squaring ping-pong buffer)
 constexpr int SL_SQ = 9;
 
-struct TermS { int slot; double c; };
+struct TermS {
+  int slot;
+  double c;
+  int sp = -1;   // batched path: power of 2^-s the coefficient carries (-1: derive from the slot)
+};
 struct OutS {
   int dst;
   double cv, cI;
@@ -28,6 +32,7 @@ struct OutS {
 struct StepS {
   int P, Q;        // operand slots; P < 0 means no product (v = 0)
   double alpha;
+  int ap = -1;     // batched path: alpha = (2^-s)^ap (-1: derive from the operands)
   int nout;
   OutS o[MAX_OUT];
 };
@@ -40,6 +45,13 @@ struct Program {
 // scheme: BBC_SCHEME_NEW or BBC_SCHEME_PS; returns false for a degree the
 // scheme does not have.
 bool make_program(int scheme, int m, int s, Program* out);
+
+// T12 / T18 of the reduced-product scheme for a caller that already holds the
+// UNSCALED powers A^2 and A^3 (computed to certify the choice of (m, s)): the
+// programs start after those two products and carry 2^-s powers explicitly
+// (X^2 = 2^-2s A^2, X^3 = 2^-3s A^3). *a2_slot / *a3_slot tell where the
+// powers must be. Returns false for other degrees.
+bool make_prefilled_program(int m, Program* out, int* a2_slot, int* a3_slot);
 
 // Degrees and product counts (Table 3) of a scheme.
 int scheme_degrees(int scheme, const int** deg, const int** products);

@@ -77,3 +77,96 @@ def test_training_learns(api):
     l1 = float(net.grad(Xd, yd)[1].mean())
     acc = float((net.forward(Xd).argmax(1) == yd).float().mean())
     assert l1 < 0.25 * l0 and acc > 0.9
+
+
+# ---- selection inside the batched launch ------------------------------------------------
+
+def _batch(n_list, norms, seed, dtype=np.float64):
+    from paper_1710_10989_gb300 import workloads as W
+    return [W.batch_matrix(i, int(n), float(v), seed=seed).astype(dtype) for i, (n, v) in
+            enumerate(zip(n_list, norms))]
+
+
+@pytest.fixture(scope="module")
+def h(api):
+    hh = api.Handle(0)
+    hh.batch_reserve(512)
+    yield hh
+    hh.close()
+
+
+def test_data_mode_norms_and_features(h, api):
+    import torch
+    from oracle import oracle as O
+    ns = [8, 33, 64, 130, 257, 300]
+    mats = _batch(ns, [0.01, 3.0, 20.0, 70.0, 5.0, 0.5], seed=21)
+    ins = [torch.from_numpy(A).cuda() for A in mats]
+    b = api.Batch(ins)
+    feat, norms = h.selector_data(b)
+    feat, norms = feat.cpu().numpy(), norms.cpu().numpy()
+    for A, f, nr in zip(mats, feat, norms):
+        want = O.power_norms(A)
+        assert np.allclose(nr, want, rtol=1e-13, atol=0)
+        assert f[0] == pytest.approx(np.log(want[0]), abs=1e-5)
+        assert f[4] == pytest.approx(np.log(A.shape[0]), abs=1e-5)
+        for k in (2, 3, 4):  # random-vector estimates bound ||A^k|| from below
+            assert f[k - 1] <= np.log(want[k - 1]) / k + 1e-4
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_alpha_rule_matches_oracle(h, api, dtype):
+    import torch
+    from oracle import oracle as O
+    from paper_1710_10989_gb300 import workloads as W
+    ns, nv = W.batch_spec(count=24, seed=22)
+    mats = _batch(ns, nv, seed=22, dtype=dtype)
+    ins = [torch.from_numpy(A).cuda() for A in mats]
+    outs = [torch.zeros_like(a) for a in ins]
+    b = api.Batch(ins, outs)
+    h.expm_batched(b, flags=api.SELECT_ALPHA)
+    torch.cuda.synchronize()
+    pi = {1: 0, 2: 1, 4: 2, 8: 3, 12: 4, 18: 5}
+    tol = 1e-12 if dtype == np.float64 else 1e-6
+    for A, o, inf in zip(mats, outs, b.infos()):
+        A = A.astype(np.float64)
+        m, s = O.select_certified(O.power_norms(A))
+        assert (inf["m"], inf["s"], inf["selector"]) == (m, s, 5), (inf, m, s)
+        # A^2 and A^3 are computed for the bound; T12 and T18 reuse them, smaller degrees do not
+        assert inf["products"] == pi[m] + s + (0 if m in (12, 18) else 2)
+        E, _ = O.expm(A, m=m, s=s)
+        got = o.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(got - E) / np.linalg.norm(E) < tol
+
+
+def test_learned_mode_is_sound_with_any_network(h, api):
+    """A random (untrained) network: whatever it proposes, a choice is used only when
+    certified, everything else falls back, and every result stays accurate."""
+    import torch
+    from oracle import oracle as O
+    from paper_1710_10989_gb300 import workloads as W
+    net = api.MLP(5, 64, 60, seed=11)
+    h.batch_set_selector(net, 10, [0.0] * 5, [1.0] * 5)
+    ns, nv = W.batch_spec(count=40, seed=23)
+    mats = _batch(ns, nv, seed=23)
+    ins = [torch.from_numpy(A).cuda() for A in mats]
+    outs = [torch.zeros_like(a) for a in ins]
+    b = api.Batch(ins, outs)
+    h.expm_batched(b, flags=api.SELECT_LEARNED)
+    torch.cuda.synchronize()
+    th = O.theta_array("new")
+    seen = set()
+    for A, o, inf in zip(mats, outs, b.infos()):
+        nr = O.power_norms(A)
+        m, s = inf["m"], inf["s"]
+        seen.add(inf["selector"])
+        alpha2 = max(nr[1] ** 0.5, nr[2] ** (1 / 3))
+        if inf["selector"] == 2:
+            assert nr[0] / 2 ** s <= th[m]
+        elif inf["selector"] == 3:
+            assert alpha2 / 2 ** s <= th[m] * (1 + 1e-9)
+        else:
+            assert inf["selector"] == 4 and (m, s) == O.select(nr[0])
+        E, _ = O.expm(A, m=m, s=s)
+        got = o.cpu().numpy()
+        assert np.linalg.norm(got - E) / np.linalg.norm(E) < 1e-12
+    assert seen <= {2, 3, 4}
