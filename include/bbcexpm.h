@@ -205,8 +205,9 @@ int bbc_batch_set_selector(bbc_handle h, const float* dParams, int hid, int out,
                            const float* hSd);
 
 /* Training data for the network, in one persistent launch: per matrix the 5
- * features (dFeat, count x 5 floats) and the exact ||A^k||_1, k = 1..4 from
- * FP64 products (dNorms, count x 4 doubles). Arguments as bbc_expm_batched. */
+ * features (dFeat, count x 5 floats) and the exact ||A^k||_1, k = 1..3 from
+ * FP64 products (dNorms, count x 4 doubles; the fourth entry is NaN).
+ * Arguments as bbc_expm_batched. */
 int bbc_selector_data_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, int64_t count, int dtype,
                               float* dFeat, double* dNorms, void* stream, bbc_info* dInfo);
 

