@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("dense4096", "batch", "small", "large"), default="dense4096")
+    ap.add_argument("--workload", choices=("dense4096", "batch", "small", "large", "learned"), default="dense4096")
     ap.add_argument("--precision", choices=("ozaki", "fp64"), default="ozaki")
     ap.add_argument("--slices", type=int, default=7, help="BF16 slices of the split-precision products")
     ap.add_argument("--n", type=int, default=0, help="override the matrix size of dense workloads")
@@ -147,6 +147,7 @@ METRICS = {
     "large": "expm/s (dense 8192x8192 exp(A), FP64-accurate)",
     "batch": "expm/s (batched exp(A), 20000 matrices N in 8..256, binary32 storage)",
     "small": "expm/s (single 64x64 exp(A), FP64, graph-replayed)",
+    "learned": "expm/s (4096 held-out matrices N in 16..512, learned certified (m,s) selection)",
 }
 WORKLOAD_DESC = {
     "dense4096": "dense{n}: 6 Gaussian N(0,1)/sqrt(N) (seeds 1-6) + 6 non-normal upper-triangular "
@@ -155,6 +156,8 @@ WORKLOAD_DESC = {
     "batch": "batch: N uniform on {{8,...,256}}, 1-norms log-uniform [1e-3, 1e2], half Gaussian, "
              "half V diag(lambda) V^-1 (cond(V)=1e3), seed 7",
     "small": "small64: N(0,1) seed 0, 1-norm 1.0, (m,s) = (18,0)",
+    "learned": "4096 held-out matrices (GPU generator, seed 12): N uniform 16..512, 1-norms log-uniform "
+               "[1e-3, 1e2], half Gaussian, half V diag(lambda) V^-1 (cond(V)=1e3)",
 }
 
 
@@ -471,6 +474,83 @@ def run_small(args, torch, dist, api, rank, world, local):
     }
 
 
+def run_learned(args, torch, dist, api, rank, world, local):
+    """The learned selector against the paper's rule and the closed-form alpha rule
+    on the same held-out matrices (one persistent launch per step each)."""
+    from paper_1710_10989_gb300 import selector as SEL
+    h = api.Handle(local)
+    h.batch_reserve(512)
+    _, meta = SEL.install(h)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(12)
+    rng = np.random.default_rng(12)
+    mats = []
+    while len(mats) < 4096:
+        n = int(rng.integers(16, 513))
+        mats += list(SEL.gpu_matrices(torch, n, min(64, 4096 - len(mats)), gen).unbind(0))
+    order = api.batch_order([A.shape[0] for A in mats])
+    mats = [mats[i].contiguous() for i in order]
+    cur = torch.cuda.current_stream()
+    res = {}
+    for name, flags in (("plain", 0), ("alpha", api.SELECT_ALPHA), ("learned", api.SELECT_LEARNED)):
+        outs = [torch.empty_like(a) for a in mats]
+        b = api.Batch(mats, outs)
+        for _ in range(args.warmup):
+            h.expm_batched(b, flags=flags, stream=cur)
+        clocks = ClockSampler(local)
+        clocks.start()
+        ms = timed(torch, dist, world, cur, lambda: h.expm_batched(b, flags=flags, stream=cur), args.steps)
+        clk = clocks.stop()
+        inf = b.infos()
+        sel = np.array([i["selector"] for i in inf])
+        flops = sum(2.0 * A.shape[0] ** 3 * i["products"] for A, i in zip(mats, inf))
+        res[name] = {"value": len(mats) * args.steps * world / (ms / 1e3), "ms_per_step": ms / args.steps,
+                     "mean_products": float(np.mean([i["products"] for i in inf])),
+                     "statuses_not_ok": int(sum(i["status"] != 0 for i in inf)),
+                     "tflops": flops / (ms / args.steps / 1e3) / 1e12, "clocks": clk,
+                     "fallback_rate": float(np.mean(sel == 4)) if name == "learned" else None,
+                     "accepted_by_norm": float(np.mean(sel == 2)) if name == "learned" else None,
+                     "accepted_by_alpha2": float(np.mean(sel == 3)) if name == "learned" else None}
+        res[name]["outs"] = outs
+    from oracle import oracle as O
+    idx = np.linspace(0, len(mats) - 1, 16).astype(int)
+    for name in res:
+        errs = []
+        for i in idx:
+            A = mats[i].cpu().numpy()
+            ref, _ = O.expm(A)
+            errs.append(float(np.linalg.norm(res[name]["outs"][i].cpu().numpy() - ref) / np.linalg.norm(ref)))
+        res[name]["max_rel_err_vs_oracle_sample16"] = max(errs)
+        del res[name]["outs"]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = [mats[i].cpu().numpy() for i in idx]
+        O.theta_array("new")
+        t0 = time.perf_counter()
+        for A in sample:
+            O.expm(A)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(sample) / dt, "unit": "expm/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"oracle exp(A) of 16 of the held-out matrices spread over sizes, in {dt:.1f} s"}
+    h.close()
+    learned = res["learned"]
+    return {
+        "metric": METRICS["learned"], "value": learned["value"], "unit": "expm/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": learned["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC["learned"], "count": len(mats),
+                   "network": f"5-{meta['hidden']}-{meta['hidden']}-{6 * meta['S']} MLP trained on "
+                              f"{meta['count']} matrices (train accuracy {meta['train_accuracy']:.3f})",
+                   "selector": "MLP proposal, certified by ||A||_1 or alpha_2 bound, else theta rule"},
+        "learned": learned, "plain": res["plain"], "alpha_rule": res["alpha"],
+        "roofline": {"bound": "alu", "achieved": learned["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": learned["tflops"] / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_batched_expm (FP64 products, learned selection)"},
+        "cpu_baseline": cpu, "e2e": None, "gpu_launches": 2 * 3 * (args.steps + args.warmup),
+        "clocks": learned["clocks"],
+    }
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -497,6 +577,8 @@ def main():
         line = run_batch(args, torch, dist, api, rank, world, local, mats)
     elif args.workload == "small":
         line = run_small(args, torch, dist, api, rank, world, local)
+    elif args.workload == "learned":
+        line = run_learned(args, torch, dist, api, rank, world, local)
     else:
         line = run_dense(args, torch, dist, api, rank, world, local)
     if rank == 0:

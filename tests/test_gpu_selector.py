@@ -170,3 +170,42 @@ def test_learned_mode_is_sound_with_any_network(h, api):
         got = o.cpu().numpy()
         assert np.linalg.norm(got - E) / np.linalg.norm(E) < 1e-12
     assert seen <= {2, 3, 4}
+
+
+def test_trained_network_gains_over_the_plain_rule(api):
+    """The committed network (trained on 10^6 generated matrices): on held-out
+    matrices it needs fewer products than the paper's rule, nearly never falls
+    back, and every result stays as accurate."""
+    import torch
+    from oracle import oracle as O
+    from paper_1710_10989_gb300 import selector as SEL
+    hh = api.Handle(0)
+    hh.batch_reserve(512)
+    SEL.install(hh)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(12)
+    rng = np.random.default_rng(12)
+    mats = []
+    while len(mats) < 512:
+        n = int(rng.integers(16, 257))
+        mats += list(SEL.gpu_matrices(torch, n, 32, gen).unbind(0))
+    prods, sels = {}, {}
+    outs = {}
+    for name, flags in (("plain", 0), ("learned", api.SELECT_LEARNED)):
+        o = [torch.empty_like(a) for a in mats]
+        b = api.Batch(mats, o)
+        hh.expm_batched(b, flags=flags)
+        torch.cuda.synchronize()
+        inf = b.infos()
+        prods[name] = np.mean([i["products"] for i in inf])
+        sels[name] = np.array([i["selector"] for i in inf])
+        outs[name] = o
+    assert prods["learned"] < 0.95 * prods["plain"], prods
+    assert np.mean(sels["learned"] == 4) < 0.05
+    for i in range(0, 512, 64):
+        A = mats[i].cpu().numpy()
+        ref, _ = O.expm(A)
+        for name in outs:
+            got = outs[name][i].cpu().numpy()
+            assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+    hh.close()
