@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--selector", choices=("plain", "learned", "alpha"), default="learned",
+                    help="(m, s) selection of the batch workload")
     return ap.parse_args()
 
 
@@ -355,22 +357,34 @@ def run_dense(args, torch, dist, api, rank, world, local):
 
 
 def run_batch(args, torch, dist, api, rank, world, local, mats):
+    """20000 uneven matrices: the chosen form (4-slice split products + learned
+    selection, by default) against plain FP64 products with the paper's rule."""
+    from paper_1710_10989_gb300 import selector as SEL
     h = api.Handle(local)
-    h.batch_reserve(256)
+    split = args.precision == "ozaki"
+    h.batch_reserve(256, api.PREC_OZAKI if split else 0)
+    sel_flag = {"plain": 0, "learned": api.SELECT_LEARNED, "alpha": api.SELECT_ALPHA}[args.selector]
+    if args.selector == "learned":
+        SEL.install(h)
+    flags = (api.PREC_OZAKI if split else 0) | sel_flag
     order = api.batch_order([A.shape[0] for A in mats])
     mats = [mats[i] for i in order]
     ins = [torch.from_numpy(A).cuda() for A in mats]
     outs = [torch.empty_like(a) for a in ins]
     batch = api.Batch(ins, outs)
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        h.expm_batched(batch, stream=stream)  # warm-up outside the capture
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=stream):
-            h.expm_batched(batch, stream=stream)
-    # replays run on the current stream, so the events go there too
-    cur = torch.cuda.current_stream()
+
+    def capture(fl):
+        with torch.cuda.stream(stream):
+            h.expm_batched(batch, flags=fl, stream=stream)  # warm-up outside the capture
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                h.expm_batched(batch, flags=fl, stream=stream)
+        return g
+
+    graph = capture(flags)
+    cur = torch.cuda.current_stream()  # replays run on the current stream, so the events go there too
     for _ in range(args.warmup):
         graph.replay()
     clocks = ClockSampler(local)
@@ -379,13 +393,32 @@ def run_batch(args, torch, dist, api, rank, world, local, mats):
     ms = timed(torch, dist, world, cur, graph.replay, args.steps)
     clk = clocks.stop()
     h.profile_enable(False)
+    torch.cuda.synchronize()
     infos = batch.infos()
     bad = sum(1 for i in infos if i["status"] != 0)
     products = sum(i["products"] for i in infos)
     flops = sum(2.0 * A.shape[0] ** 3 * i["products"] for A, i in zip(mats, infos))
     bytes_io = sum(2 * A.size * 4 for A in mats)
     value = len(mats) * args.steps * world / (ms / 1e3)
-    achieved = flops / (ms / args.steps / 1e3) / 1e12
+    logical = flops / (ms / args.steps / 1e3) / 1e12
+    sel = np.array([i["selector"] for i in infos])
+    chosen_out = [o.cpu().numpy() for o in outs[::200]]
+
+    plain = None
+    if flags != 0 and not args.no_fp64_compare:
+        g64 = capture(0)
+        g64.replay()
+        ms64 = timed(torch, dist, world, cur, g64.replay, 1)
+        inf64 = batch.infos()
+        plain = {"value": len(mats) * world / (ms64 / 1e3), "unit": "expm/s", "steps": 1,
+                 "mean_products": float(np.mean([i["products"] for i in inf64])), "form": "FP64 products, paper's rule"}
+
+    # accuracy of the chosen form against the oracle on every 200th matrix
+    from oracle import oracle as O
+    errs = []
+    for A, E in zip(mats[::200], chosen_out):
+        ref, _ = O.expm(A.astype(np.float64))
+        errs.append(float(np.linalg.norm(E.astype(np.float64) - ref) / np.linalg.norm(ref)))
 
     e2e = None
     if not args.no_e2e:
@@ -395,33 +428,48 @@ def run_batch(args, torch, dist, api, rank, world, local, mats):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            with torch.cuda.stream(stream):
-                for a, d in zip(hin, ins):
-                    d.copy_(a, non_blocking=True)
-                graph.replay()
-                for d, o in zip(outs, hout):
-                    o.copy_(d, non_blocking=True)
-            stream.synchronize()
+            for a, d in zip(hin, ins):
+                d.copy_(a, non_blocking=True)
+            graph.replay()
+            for d, o in zip(outs, hout):
+                o.copy_(d, non_blocking=True)
+            torch.cuda.synchronize()
         te = time.perf_counter() - t0
         e2e = {"value": len(mats) * e2e_steps * world / te, "unit": "expm/s", "h2d_bytes_per_step": bytes_io // 2,
                "d2h_bytes_per_step": bytes_io // 2, "steps": e2e_steps}
     cpu = cpu_batch_sample(mats[::max(1, len(mats) // 200)]) if (rank == 0 and world == 1
                                                                  and not args.no_cpu_baseline) else None
     h.close()
+    pk = peaks()
+    if split:
+        # executed work: 10 BF16 slice products per product on the warp-level MMAs (padding to 32 excluded)
+        executed = 10 * flops / (ms / args.steps / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": executed, "peak": 0.32 * pk.get("bf16_tflops", 1899.1),
+                "unit": "TFLOP/s", "frac": executed / (0.32 * pk.get("bf16_tflops", 1899.1)), "traffic": None,
+                "kernel": "k_batched_expm (4-slice BF16 mma.sync products)",
+                "peak_source": "mma.sync m16n8k16 BF16 measured at 604 TFLOP/s on this GB300 (0.32 of the "
+                               "MEASURED_PEAKS bf16 figure, which is tcgen05/cuBLAS)",
+                "logical_fp64_tflops": logical}
+    else:
+        roof = {"bound": "alu", "achieved": logical, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": logical / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_batched_expm (FP64 products)",
+                "peak_source": "FP64 pipe, 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"}
     return {
         "metric": METRICS["batch"], "value": value,
         "unit": "expm/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 (binary32 storage)", "data": "synthetic",
+        "dtype": ("bf16x4-slices(exact group sums)->f64" if split else "f64") + " (binary32 storage)",
+        "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC["batch"].format(),
                    "count": len(mats), "products_per_step": products, "statuses_not_ok": bad,
+                   "precision": args.precision, "selector": args.selector,
                    "graph": "one persistent kernel per step, replayed from a CUDA graph", "u": "2^-53",
                    "l2": "per-CTA binary64 work slots; inputs+outputs 3.7 GB per step (larger than L2)"},
-        "tflops_logical": achieved,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "k_batched_expm (FP64 products)",
-                     "peak_source": "FP64 pipe, 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"},
+        "tflops_logical": logical,
+        "selector_stats": {"fallback_rate": float(np.mean(sel == 4)), "accepted_by_norm": float(np.mean(sel == 2)),
+                           "accepted_by_alpha2": float(np.mean(sel == 3))} if args.selector == "learned" else None,
+        "max_rel_err_vs_oracle_sample": max(errs), "error_sample": len(errs), "tolerance": 1e-6,
+        "plain_fp64": plain, "roofline": roof,
         "hbm_gbs_io": bytes_io / (ms / args.steps / 1e3) / 1e9,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk,
     }

@@ -162,7 +162,11 @@ int bbc_batch_order(const int64_t* hNs, int64_t count, int64_t* hOrder);
  * Matrices are taken in array order by whichever CTA is free: put expensive
  * ones first (bbc_batch_order). Needs bbc_batch_reserve first; performs no
  * allocation and no host synchronisation (one memset and one kernel on
- * `stream`), so it can be captured in a CUDA graph. Scheme NEW only. */
+ * `stream`), so it can be captured in a CUDA graph. Scheme NEW only.
+ * Products: FP64 (BBC_PREC_FP64), or with BBC_PREC_OZAKI (reserved with the
+ * same flag) 4 BF16 slices on warp-level tensor-core MMAs with exact FP32
+ * slice-group sums (about 32 significant bits per product; N_i <= 256, larger
+ * matrices use FP64 products). */
 int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, int64_t count, void* const* dOut,
                      int dtype, double tol, int flags, void* stream, bbc_info* dInfo);
 

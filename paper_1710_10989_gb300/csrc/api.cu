@@ -37,6 +37,7 @@ struct bbc_handle_s {
   int64_t batch_nmax = 0;         // reservation of the batched workspace
   BatchSelector selector = {};    // network for BBC_SELECT_LEARNED (mode 0: none installed)
   int batch_ctas = 0;
+  bool batch_split = false;       // reservation includes the split-precision scratch
   void* batch_work = nullptr;
   int64_t io_n = 0;               // N the host-call staging buffers are sized for
   double* io = nullptr;           // 2 * N * N doubles: device copies of hA and hOut
@@ -323,6 +324,16 @@ int run_expm(bbc_handle h, const double* A, int64_t N, double* Out, int m, int s
     info->m = m;
     info->s = s;
     info->products = prog.products + s;
+  }
+  return BBC_OK;
+}
+
+// The batched path serves scheme NEW, with FP64 products or 4-slice split products.
+int batch_flags_ok(int flags) {
+  if ((flags & BBC_SCHEME_MASK) != BBC_SCHEME_NEW) return fail(BBC_UNSUPPORTED, "batched path: scheme NEW only");
+  if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
+    const int k = (flags >> 8) & 0xF;
+    if (k != 0 && k != 4) return fail(BBC_UNSUPPORTED, "batched split products use 4 slices");
   }
   return BBC_OK;
 }
@@ -644,18 +655,21 @@ int bbc_batch_reserve(bbc_handle h, int64_t max_n, int flags) {
   if (rc) return rc;
   if (max_n < 1 || max_n > 512) return fail(BBC_INVALID_ARG, "batched max_n must be in 1..512");
   if ((rc = check_flags(flags))) return rc;
-  if ((flags & BBC_SCHEME_MASK) != BBC_SCHEME_NEW || (flags & BBC_PREC_MASK) != BBC_PREC_FP64)
-    return fail(BBC_UNSUPPORTED, "batched path: scheme NEW with FP64 products only");
+  if ((rc = batch_flags_ok(flags))) return rc;
+  const bool split = (flags & BBC_PREC_MASK) == BBC_PREC_OZAKI;
   std::lock_guard<std::mutex> lk(h->mu);
-  if (max_n > h->batch_nmax) {
+  if (max_n > h->batch_nmax || (split && !h->batch_split)) {
     if (h->batch_work) BBC_CUDA(cudaFree(h->batch_work));
     h->batch_work = nullptr;
+    const int64_t nmax = std::max(max_n, h->batch_nmax);
     h->batch_nmax = 0;
+    const bool want_split = split || h->batch_split;
     const int ctas = batched_ctas(h->device);
-    BBC_CUDA(cudaMalloc(&h->batch_work, batched_workspace_bytes(max_n, ctas)));
+    BBC_CUDA(cudaMalloc(&h->batch_work, batched_workspace_bytes(nmax, ctas, want_split)));
     BBC_CUDA(batched_upload_programs());
     h->batch_ctas = ctas;
-    h->batch_nmax = max_n;
+    h->batch_nmax = nmax;
+    h->batch_split = want_split;
   }
   return BBC_OK;
 }
@@ -740,11 +754,12 @@ int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, in
   const double u = tol > 0 ? tol : std::ldexp(1.0, -53);
   if (!valid_u(u)) return fail(BBC_INVALID_ARG, "tol out of range [2^-60, 2^-5]");
   if ((rc = check_flags(flags))) return rc;
-  if ((flags & BBC_SCHEME_MASK) != BBC_SCHEME_NEW || (flags & BBC_PREC_MASK) != BBC_PREC_FP64)
-    return fail(BBC_UNSUPPORTED, "batched path: scheme NEW with FP64 products only");
+  if ((rc = batch_flags_ok(flags))) return rc;
+  const bool split = (flags & BBC_PREC_MASK) == BBC_PREC_OZAKI;
   if (count == 0) return BBC_OK;
   std::lock_guard<std::mutex> lk(h->mu);
   if (!h->batch_work) return fail(BBC_INVALID_ARG, "call bbc_batch_reserve first");
+  if (split && !h->batch_split) return fail(BBC_INVALID_ARG, "reserve with BBC_PREC_OZAKI first");
   static const int deg[6] = {1, 2, 4, 8, 12, 18};
   double theta[6];
   for (int i = 0; i < 6; ++i) theta[i] = theta_cached(deg[i], u);
@@ -761,7 +776,7 @@ int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, in
   cudaStream_t st = (cudaStream_t)stream;
   LaunchScope scope(h, BBC_KERNEL_BATCHED, st);
   const cudaError_t e = batched_launch(dA, dOut, dNs, count, h->batch_nmax, dtype, theta, h->batch_work,
-                                       h->batch_ctas, dInfo, st, psel);
+                                       h->batch_ctas, dInfo, st, psel, split);
   if (e != cudaSuccess) return cuda_fail(e, "batched launch");
   return BBC_OK;
 }

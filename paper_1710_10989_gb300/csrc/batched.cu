@@ -91,6 +91,8 @@ struct BatchArgs {
   float mu[NFEAT], sd[NFEAT];    // feature normalisation
   float* feat_out;         // data mode: count x NFEAT
   double* norms_out;       // data mode: count x 4
+  int prec;                // 0: products on the FP64 pipe; 1: 4-slice BF16 mma.sync products (N <= 256)
+  uint32_t* ozwork;        // per-CTA slice scratch, OZB_WORDS words each (prec 1)
 };
 
 namespace {
@@ -157,8 +159,221 @@ __device__ void block_gemm_f64(const double* __restrict__ P, const double* __res
   }
 }
 
+// ---------------------------------------------------------------------------
+// Split-precision products inside a CTA (N <= 256): 4 BF16 slices per operand
+// and warp-level mma.sync m16n8k16 (BF16 in, FP32 accumulate). With K <= 256
+// and digits of at most 2^7 in magnitude, a slice group g = p + q (at most 4
+// pairs) sums to at most 4 * 256 * 2^14 = 2^24 in magnitude, so FP32 holds every
+// group sum exactly and no chunking is needed; the groups combine exactly in an
+// int64. The diagonals are deflated as in the single-matrix path
+// (P Q = P'Q' + D_P Q + P D_Q - D_P D_Q). Products carry ~32 significant bits.
+// ---------------------------------------------------------------------------
+constexpr int OZB_K = 4;          // slices
+constexpr int OZB_NMAX = 256;     // largest N served by these products
+constexpr size_t OZB_WORDS = 2 * (size_t)OZB_K * OZB_NMAX * (OZB_NMAX / 2);  // per-CTA slice scratch
+
+struct OzbSmem {
+  int rexp[OZB_NMAX], cexp[OZB_NMAX];      // largest biased exponent of each row of P' / column of Q' (>= 1)
+  double pdiag[OZB_NMAX], qdiag[OZB_NMAX];
+  int bad;
+};
+
+__device__ __forceinline__ int ozb_expf(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// round(x * 2^(32 - e)), e = Emax - 1021 (|x| < 2^(e-1)): an integer below 2^31
+__device__ __forceinline__ long long ozb_fixed(double x, int Emax) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  int E = (int)((bits >> 52) & 0x7FF);
+  unsigned long long M = bits & 0xFFFFFFFFFFFFFull;
+  if (E == 0) E = 1; else M |= 1ull << 52;
+  const int sh = 8 * OZB_K - 54 - (Emax - E);
+  long long X;
+  if (sh >= 0) X = (long long)(M << sh);
+  else if (sh > -60) X = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
+  else X = 0;
+  return (bits >> 63) ? -X : X;
+}
+
+__device__ __forceinline__ uint32_t ozb_bf16(int d) {  // exact for |d| <= 256
+  return (uint32_t)__float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
+}
+
+__device__ __forceinline__ void ozb_digits(long long X, uint32_t (&d)[OZB_K]) {
+#pragma unroll
+  for (int p = OZB_K - 1; p >= 1; --p) {
+    const long long low = ((X + 128) & 255) - 128;
+    d[p] = ozb_bf16((int)low);
+    X = (X - low) >> 8;
+  }
+  d[0] = ozb_bf16((int)X);
+}
+
+// P' rows -> Ps[p][Np][Np/2] and Q' columns -> Qt[q][Np][Np/2] (words of two BF16
+// digits, K contiguous). Returns false (CTA-uniformly) if an operand is not finite.
+__device__ bool block_split_oz(const double* __restrict__ P, const double* __restrict__ Q, int N, int Np,
+                               uint32_t* __restrict__ Ps, uint32_t* __restrict__ Qt, OzbSmem& o) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int half = Np / 2;
+  const size_t plane = (size_t)Np * half;
+  if (tid == 0) o.bad = 0;
+  __syncthreads();
+  for (int i = warp; i < Np; i += BATCH_THREADS / 32) {
+    int em = 0;
+    bool bad = false;
+    if (i < N)
+      for (int j = lane; j < N; j += 32) {
+        const int E = ozb_expf(P[(int64_t)i * N + j]);
+        bad |= (E == 0x7FF);
+        if (j != i) em = max(em, E);
+      }
+    for (int off = 16; off > 0; off >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, off));
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+      if (bad) o.bad = 1;
+      o.rexp[i] = max(em, 1);
+      o.pdiag[i] = (i < N) ? P[(int64_t)i * N + i] : 0.0;
+    }
+  }
+  for (int j = tid; j < Np; j += BATCH_THREADS) {
+    int em = 0;
+    bool bad = false;
+    if (j < N)
+      for (int i = 0; i < N; ++i) {
+        const int E = ozb_expf(Q[(int64_t)i * N + j]);
+        bad |= (E == 0x7FF);
+        if (i != j) em = max(em, E);
+      }
+    if (bad) o.bad = 1;
+    o.cexp[j] = max(em, 1);
+    o.qdiag[j] = (j < N) ? Q[(int64_t)j * N + j] : 0.0;
+  }
+  __syncthreads();
+  if (o.bad) return false;
+  for (int idx = tid; idx < Np * half; idx += BATCH_THREADS) {
+    const int i = idx / half, j = 2 * (idx % half);
+    const double x0 = (i < N && j < N && j != i) ? P[(int64_t)i * N + j] : 0.0;
+    const double x1 = (i < N && j + 1 < N && j + 1 != i) ? P[(int64_t)i * N + j + 1] : 0.0;
+    uint32_t d0[OZB_K], d1[OZB_K];
+    ozb_digits(ozb_fixed(x0, o.rexp[i]), d0);
+    ozb_digits(ozb_fixed(x1, o.rexp[i]), d1);
+#pragma unroll
+    for (int p = 0; p < OZB_K; ++p) Ps[p * plane + idx] = d0[p] | (d1[p] << 16);
+  }
+  for (int idx = tid; idx < Np * half; idx += BATCH_THREADS) {
+    const int j = idx / half, i = 2 * (idx % half);
+    const double x0 = (i < N && j < N && i != j) ? Q[(int64_t)i * N + j] : 0.0;
+    const double x1 = (i + 1 < N && j < N && i + 1 != j) ? Q[(int64_t)(i + 1) * N + j] : 0.0;
+    uint32_t d0[OZB_K], d1[OZB_K];
+    ozb_digits(ozb_fixed(x0, o.cexp[j]), d0);
+    ozb_digits(ozb_fixed(x1, o.cexp[j]), d1);
+#pragma unroll
+    for (int q = 0; q < OZB_K; ++q) Qt[q * plane + idx] = d0[q] | (d1[q] << 16);
+  }
+  __syncthreads();
+  return true;
+}
+
+__device__ __forceinline__ void ozb_mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// alpha * (P Q) with the fused epilogue, from the slices of block_split_oz.
+// Warp tasks of 32 x 16 outputs (two m16 x two n8 tiles), 10 slice pairs.
+__device__ void block_gemm_oz(const uint32_t* __restrict__ Ps, const uint32_t* __restrict__ Qt,
+                              const double* __restrict__ P, const double* __restrict__ Q, int N, int Np,
+                              double alpha, const Epilogue& e, const OzbSmem& o) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  const int half = Np / 2;
+  const size_t plane = (size_t)Np * half;
+  const int tn = Np / 16, tasks = (Np / 32) * tn;
+  for (int task = warp; task < tasks; task += BATCH_THREADS / 32) {
+    const int i0 = (task / tn) * 32, j0 = (task % tn) * 16;
+    float acc[OZB_K][2][2][4];
+#pragma unroll
+    for (int g = 0; g < OZB_K; ++g)
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[g][mt][nt][r] = 0.f;
+    for (int k0 = 0; k0 < Np; k0 += 16) {
+      const int kw = (k0 >> 1) + tig;
+      uint32_t a[OZB_K][2][4], b[OZB_K][2][2];
+#pragma unroll
+      for (int p = 0; p < OZB_K; ++p)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          const uint32_t* base = Ps + p * plane + (size_t)(i0 + 16 * mt + gid) * half + kw;
+          a[p][mt][0] = base[0];
+          a[p][mt][1] = base[8 * half];
+          a[p][mt][2] = base[4];
+          a[p][mt][3] = base[8 * half + 4];
+        }
+#pragma unroll
+      for (int q = 0; q < OZB_K; ++q)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const uint32_t* base = Qt + q * plane + (size_t)(j0 + 8 * nt + gid) * half + kw;
+          b[q][nt][0] = base[0];
+          b[q][nt][1] = base[4];
+        }
+#pragma unroll
+      for (int p = 0; p < OZB_K; ++p)
+#pragma unroll
+        for (int q = 0; q + p < OZB_K; ++q)
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) ozb_mma(acc[p + q][mt][nt], a[p][mt], b[q][nt][0], b[q][nt][1]);
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int row = i0 + 16 * mt + gid + 8 * (r >> 1);
+          const int col = j0 + 8 * nt + 2 * tig + (r & 1);
+          if (row >= N || col >= N) continue;
+          long long R = 0;
+#pragma unroll
+          for (int g = 0; g < OZB_K; ++g)
+            R += (long long)__float2int_rn(acc[g][mt][nt][r]) << (8 * (OZB_K - 1 - g));
+          const int ex = (o.rexp[row] - 1021) + (o.cexp[col] - 1021) - 16 - 8 * (OZB_K - 1);
+          const double scl = (ex >= -1022 && ex <= 1023) ? __longlong_as_double((long long)(ex + 1023) << 52)
+                                                        : ldexp(1.0, ex);
+          const double pii = o.pdiag[row], qjj = o.qdiag[col];
+          double v = fma(pii, Q[(int64_t)row * N + col], (double)R * scl);
+          v = fma(P[(int64_t)row * N + col], qjj, v);
+          if (row == col) v = fma(-pii, qjj, v);
+          apply_epilogue(e, N, row, col, alpha * v);
+        }
+  }
+}
+
 __device__ void block_lincomb(int N, const Epilogue& e) {
   for (int idx = threadIdx.x; idx < N * N; idx += BATCH_THREADS) apply_epilogue(e, N, idx / N, idx % N, 0.0);
+}
+
+// One product of the program: split precision when asked and N <= 256 (and the
+// operands are finite), else the FP64 pipe.
+__device__ void block_product(const BatchArgs& a, const double* P, const double* Q, int N, double alpha,
+                              const Epilogue& e, GemmSmem& sm, OzbSmem& oz) {
+  if (a.prec == 1 && N <= OZB_NMAX) {
+    const int Np = (N + 31) / 32 * 32;
+    uint32_t* Ps = a.ozwork + (size_t)blockIdx.x * OZB_WORDS;
+    uint32_t* Qt = Ps + OZB_WORDS / 2;
+    if (block_split_oz(P, Q, N, Np, Ps, Qt, oz)) {
+      block_gemm_oz(Ps, Qt, P, Q, N, Np, alpha, e, oz);
+      return;
+    }
+  }
+  block_gemm_f64(P, Q, N, alpha, e, sm);
 }
 
 // max_j sum_i |M_ij| over an N x N binary64 matrix (one column per thread).
@@ -277,6 +492,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchAr
   __shared__ float s_est[16];
   __shared__ double s_pnorm[4];
   __shared__ int s_pow, s_prop_m, s_prop_s;
+  __shared__ OzbSmem s_oz;
 
   const int tid = threadIdx.x;
   const size_t nn_max = (size_t)args.nmax * args.nmax;
@@ -465,7 +681,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchAr
         for (int p = 0; p < st.alpha_pow; ++p) alpha *= sig;
         const double* P = slots + (size_t)(st.P == SL_A ? BSL_A : st.P) * nn_max;
         const double* Q = slots + (size_t)(st.Q == SL_A ? BSL_A : st.Q) * nn_max;
-        block_gemm_f64(P, Q, N, alpha, s_epi, sm);
+        block_product(args, P, Q, N, alpha, s_epi, sm, s_oz);
       }
       __syncthreads();
     }
@@ -483,7 +699,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchAr
         s_epi.o[0].nt = 0;
       }
       __syncthreads();
-      block_gemm_f64(src, src, N, 1.0, s_epi, sm);
+      block_product(args, src, src, N, 1.0, s_epi, sm, s_oz);
       __syncthreads();
       src = dst;
     }
@@ -517,8 +733,9 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchAr
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t batched_workspace_bytes(int64_t nmax, int ctas) {
-  return (size_t)ctas * BATCH_SLOTS * nmax * nmax * sizeof(double) + 256;
+size_t batched_workspace_bytes(int64_t nmax, int ctas, bool split) {
+  return (size_t)ctas * BATCH_SLOTS * nmax * nmax * sizeof(double) + 256 +
+         (split ? (size_t)ctas * OZB_WORDS * sizeof(uint32_t) : 0);
 }
 
 int batched_ctas(int device) {
@@ -584,7 +801,7 @@ cudaError_t batched_upload_programs() {
 
 cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t* Ns, int64_t count, int64_t nmax,
                            int dtype, const double* theta, void* work, int ctas, bbc_info* info, cudaStream_t st,
-                           const BatchSelector* sel) {
+                           const BatchSelector* sel, bool split) {
   static const int deg[BATCH_PROGS] = {1, 2, 4, 8, 12, 18};
   static const int prod[BATCH_PROGS] = {0, 1, 2, 3, 4, 5};
   BatchArgs a = {};
@@ -598,6 +815,10 @@ cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t
   a.counter = static_cast<unsigned int*>(work);
   a.work = reinterpret_cast<double*>(static_cast<char*>(work) + 256);
   a.info = info;
+  a.prec = split ? 1 : 0;
+  a.ozwork = split ? reinterpret_cast<uint32_t*>(static_cast<char*>(work) + 256 +
+                                                 (size_t)ctas * BATCH_SLOTS * nmax * nmax * sizeof(double))
+                   : nullptr;
   a.mode = MODE_PLAIN;
   if (sel) {
     a.mode = sel->mode;

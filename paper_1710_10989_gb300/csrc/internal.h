@@ -93,7 +93,7 @@ cudaError_t mlp_adam(float* P, const float* g, float* m, float* v, int64_t n, fl
                      float eps, int step, cudaStream_t st);
 
 // Persistent batched exp(A) (batched.cu).
-size_t batched_workspace_bytes(int64_t nmax, int ctas);
+size_t batched_workspace_bytes(int64_t nmax, int ctas, bool split);
 int batched_ctas(int device);
 cudaError_t batched_upload_programs();
 struct BatchSelector {
@@ -106,6 +106,7 @@ struct BatchSelector {
 };
 cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t* Ns, int64_t count,
                            int64_t nmax, int dtype, const double* theta, void* work, int ctas,
-                           bbc_info* info, cudaStream_t st, const BatchSelector* sel = nullptr);
+                           bbc_info* info, cudaStream_t st, const BatchSelector* sel = nullptr,
+                           bool split = false);
 
 }  // namespace bbc

@@ -110,3 +110,52 @@ def test_batch_graph_capture_replay(h, api):
     for A, o in zip(mats, outs):
         want, _ = O.expm(A, "new")
         assert rel_fro(o.cpu().numpy(), want) < 1e-12
+
+
+def test_batch_split_precision_matches_oracle(api):
+    """4-slice BF16 products (warp-level MMAs, exact group sums): the batched
+    workload's tolerance (1e-6 against the oracle on the binary32-rounded input)."""
+    import torch
+    hh = api.Handle(0)
+    hh.batch_reserve(256, api.PREC_OZAKI)
+    ns, norms = W.batch_spec(count=48, seed=5)
+    ns[:6] = [1, 7, 8, 65, 255, 256]
+    mats = [W.batch_matrix(i, int(n), float(v), seed=5) for i, (n, v) in enumerate(zip(ns, norms))]
+    outs, infos = None, None
+    ins = [torch.from_numpy(A.astype(np.float32)).cuda() for A in mats]
+    outs = [torch.full_like(a, float("nan")) for a in ins]
+    b = api.Batch(ins, outs)
+    hh.expm_batched(b, flags=api.PREC_OZAKI)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for A, o, inf in zip(mats, outs, b.infos()):
+        A = A.astype(np.float32).astype(np.float64)
+        want, oi = O.expm(A, "new")
+        assert inf["status"] == 0 and (inf["m"], inf["s"]) == (oi.m, oi.s)
+        worst = max(worst, rel_fro(o.cpu().numpy().astype(np.float64), want))
+    assert worst < 1e-6, worst
+    hh.close()
+
+
+def test_batch_split_learned_all_three(api):
+    """Split-precision products + learned selection in one launch; N > 256 falls
+    back to FP64 products inside the same launch."""
+    import torch
+    from paper_1710_10989_gb300 import selector as SEL
+    hh = api.Handle(0)
+    hh.batch_reserve(512, api.PREC_OZAKI)
+    SEL.install(hh)
+    ns, norms = W.batch_spec(count=24, seed=6)
+    ns[0], ns[1] = 300, 512
+    mats = [W.batch_matrix(i, int(n), float(v), seed=6) for i, (n, v) in enumerate(zip(ns, norms))]
+    ins = [torch.from_numpy(A).cuda() for A in mats]
+    outs = [torch.zeros_like(a) for a in ins]
+    b = api.Batch(ins, outs)
+    hh.expm_batched(b, flags=api.PREC_OZAKI | api.SELECT_LEARNED)
+    torch.cuda.synchronize()
+    for A, o, inf in zip(mats, outs, b.infos()):
+        assert inf["status"] == 0 and inf["selector"] in (2, 3, 4)
+        want, _ = O.expm(A, "new")
+        tol = 1e-12 if A.shape[0] > 256 else 1e-6
+        assert rel_fro(o.cpu().numpy(), want) < tol, (A.shape, inf)
+    hh.close()
