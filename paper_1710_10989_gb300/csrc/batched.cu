@@ -574,8 +574,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchAr
           s_epi.o[0].nt = 0;
         }
         __syncthreads();
-        // A^2 = A A, A^3 = A^2 A
-        block_gemm_f64(k == 0 ? A64 : W0p, A64, N, 1.0, s_epi, sm);
+        // A^2 = A A, A^3 = A^2 A (split products in split mode; FP64 for training data)
+        block_product(args, k == 0 ? A64 : W0p, A64, N, 1.0, s_epi, sm, s_oz);
         __syncthreads();
         const double nk = block_norm1(slots + (size_t)k * nn_max, N, s_red);
         if (tid == 0) s_pnorm[k + 1] = nk;
@@ -584,7 +584,9 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchAr
     __syncthreads();
     if (tid == 0 && s_status == BBC_OK && args.mode != MODE_DATA) {
       const double nrm = s_norm;
-      const double alpha2 = s_pow ? fmax(sqrt(s_pnorm[1]), cbrt(s_pnorm[2])) * (1.0 + 1e-12) : INFINITY;
+      // the margin covers the rounding of the computed powers (~2^-30 relative for split products)
+      const double margin = (args.prec == 1 && N <= OZB_NMAX) ? 1e-6 : 1e-12;
+      const double alpha2 = s_pow ? fmax(sqrt(s_pnorm[1]), cbrt(s_pnorm[2])) * (1.0 + margin) : INFINITY;
       int bm = 0, bs = 0, bc = 1 << 30;
       bool done = false;
       if (args.mode == MODE_LEARNED && s_prop_m < BATCH_PROGS) {
