@@ -461,7 +461,8 @@ def run_batch(args, torch, dist, api, rank, world, local, mats):
         "dtype": ("bf16x4-slices(exact group sums)->f64" if split else "f64") + " (binary32 storage)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC["batch"].format(),
-                   "count": len(mats), "products_per_step": products, "statuses_not_ok": bad,
+                   "count": len(mats) * world, "products_per_step": products, "statuses_not_ok": bad,
+                   "parallelism": f"{world} ranks, LPT shards of the batch, no collective" if world > 1 else "single",
                    "precision": args.precision, "selector": args.selector,
                    "graph": "one persistent kernel per step, replayed from a CUDA graph", "u": "2^-53",
                    "l2": "per-CTA binary64 work slots; inputs+outputs 3.7 GB per step (larger than L2)"},
@@ -607,8 +608,17 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
-    # the batch is generated by spawned workers before CUDA starts in this process
-    mats = W.batch_matrices(args.count) if args.workload == "batch" else None
+    # the batch is generated by spawned workers before CUDA starts in this process; with
+    # several ranks the global batch is world x count matrices and each rank builds its
+    # longest-processing-time shard of it (weak scaling, no data-path collective)
+    mats = None
+    if args.workload == "batch":
+        if world == 1:
+            mats = W.batch_matrices(args.count)
+        else:
+            from paper_1710_10989_gb300 import sharding
+            ns, _ = W.batch_spec(count=args.count * world)
+            mats = W.batch_matrices_subset(sharding.shard_indices(ns, rank, world), count=args.count * world)
 
     import torch
     import torch.distributed as dist

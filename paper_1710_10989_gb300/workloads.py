@@ -125,6 +125,11 @@ def _batch_chunk(args):
             for i in range(lo, hi)]
 
 
+def _batch_pick(args):
+    idx, ns, norms, seed = args
+    return [batch_matrix(int(i), int(n), float(v), seed).astype(np.float32) for i, n, v in zip(idx, ns, norms)]
+
+
 def batch_matrices(count: int = BATCH_COUNT, seed: int = BATCH_SEED, workers: int = 0):
     """All matrices of the batched workload as binary32 arrays (their storage type).
 
@@ -153,3 +158,29 @@ def batch_matrices(count: int = BATCH_COUNT, seed: int = BATCH_SEED, workers: in
             else:
                 os.environ[k] = v
     return [m for part in parts for m in part]
+
+
+def batch_matrices_subset(indices, count: int = BATCH_COUNT, seed: int = BATCH_SEED, workers: int = 0):
+    """Matrices `indices` of the batch of `count` (a rank's shard), generated as
+    canonically as batch_matrices (spawned single-threaded-BLAS workers)."""
+    import multiprocessing as mp
+    import os
+    ns, norms = batch_spec(count, seed)
+    idx = np.asarray(list(indices), dtype=np.int64)
+    workers = workers or min(16, os.cpu_count() or 1)
+    parts = np.array_split(np.arange(len(idx)), max(1, workers * 4))
+    jobs = [(idx[p], ns[idx[p]], norms[idx[p]], seed) for p in parts if len(p)]
+    keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            out = pool.map(_batch_pick, jobs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return [m for part in out for m in part]
