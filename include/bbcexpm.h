@@ -45,6 +45,7 @@ typedef enum {
 /* flags: scheme in bits 0-3, product precision in bits 4-11. */
 #define BBC_SCHEME_NEW 0x0     /* reduced-product Taylor, degrees {1,2,4,8,12,18} (Section 3) */
 #define BBC_SCHEME_PS 0x1      /* Paterson-Stockmeyer Taylor, degrees {1,2,4,6,9,12,16} (eq. poli9) */
+#define BBC_SCHEME_PADE26 0x2  /* diagonal Pade r_26 (eq. pade26), the paper's comparator; N <= 1024 */
 #define BBC_SCHEME_MASK 0xF
 #define BBC_PREC_FP64 0x00     /* every product on the FP64 pipe (DFMA) */
 #define BBC_PREC_OZAKI 0x10    /* products as exact BF16 slice products on tcgen05 tensor cores,
@@ -83,9 +84,14 @@ int bbc_workspace_size(bbc_handle h, int64_t N, int dtype, int flags, size_t* by
  * Host-only; m in 1..30, u in [2^-60, 2^-5]. */
 int bbc_theta(int m, double u, double* theta);
 
+/* theta_2m(u) for the diagonal Pade approximant r_2m (eq. theta with eq. 24,
+ * Table 1), 2m even in 2..30. Host-only. */
+int bbc_theta_pade(int two_m, double u, double* theta);
+
 /* (m, s) selection (Section 4, Table 2, Table 3): minimise products(m) + s
  * subject to norm1 / 2^s <= theta_m(u), ties to the smaller s. Host-only.
- * `scheme` is BBC_SCHEME_NEW or BBC_SCHEME_PS. */
+ * `scheme` is BBC_SCHEME_NEW or BBC_SCHEME_PS; BBC_SCHEME_PADE26 gives m = 26
+ * and the least s with norm1 / 2^s <= theta_26 (the paper's reference rule). */
 int bbc_select(double norm1, double u, int scheme, int* m, int* s);
 
 /* ||A||_1 = max_j sum_i |a_ij| on the device. Writes the result to host

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libbbcexpm.so")
 
 OK, INVALID_ARG, NONFINITE_INPUT, OVERFLOW, CUDA_ERROR, TIMEOUT, UNSUPPORTED = range(7)
-SCHEME_NEW, SCHEME_PS = 0x0, 0x1
+SCHEME_NEW, SCHEME_PS, SCHEME_PADE26 = 0x0, 0x1, 0x2
 PREC_FP64, PREC_OZAKI = 0x00, 0x10
 SELECT_LEARNED, SELECT_ALPHA = 0x1000, 0x2000
 DEGREES = (1, 2, 4, 8, 12, 18)
@@ -53,6 +53,7 @@ _SIGS = {
     "bbc_destroy": [_vp],
     "bbc_workspace_size": [_vp, _i64, _int, _int, ctypes.POINTER(ctypes.c_size_t)],
     "bbc_theta": [_int, _dbl, _dp],
+    "bbc_theta_pade": [_int, _dbl, _dp],
     "bbc_select": [_dbl, _dbl, _int, _ip, _ip],
     "bbc_norm1": [_vp, _vp, _i64, _vp, _dp],
     "bbc_norm1_noalloc": [_vp, _i64, _vp, _vp],
@@ -98,6 +99,12 @@ def _check(rc: int) -> None:
 def theta(m: int, u: float = U_DOUBLE) -> float:
     out = ctypes.c_double()
     _check(_lib.bbc_theta(m, u, ctypes.byref(out)))
+    return out.value
+
+
+def theta_pade(two_m: int, u: float = U_DOUBLE) -> float:
+    out = ctypes.c_double()
+    _check(_lib.bbc_theta_pade(two_m, u, ctypes.byref(out)))
     return out.value
 
 

@@ -110,15 +110,98 @@ double compute_theta(int m, double u) {
   return lo;
 }
 
+// ---------------------------------------------------------------------------
+// theta_2m(u) for the diagonal Pade approximant r_2m (eq. 24, eq. theta). The
+// series rho(x) = log(e^-x r_2m(x)) starts at x^(2m+1), and its coefficients come
+// from a sum whose terms cancel by ~10 orders of magnitude for m = 13, so they
+// are formed in double-double arithmetic (deterministic on every host):
+//   N(x) = e^-x p_m(x) - p_m(-x) (first term at x^(2m+1)), q = N / p_m(-x),
+//   rho = log(1 + q) = q - q^2/2 + ...  (q^3 starts beyond the 150 terms used).
+// ---------------------------------------------------------------------------
+struct DD { double hi, lo; };
+DD dd_two_sum(double a, double b) {
+  const double s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+DD dd_norm(double hi, double lo) {
+  const double s = hi + lo;
+  return {s, lo - (s - hi)};
+}
+DD dd_add(DD a, DD b) {
+  DD s = dd_two_sum(a.hi, b.hi);
+  return dd_norm(s.hi, s.lo + a.lo + b.lo);
+}
+DD dd_mul(DD a, DD b) {
+  const double p = a.hi * b.hi;
+  const double e = std::fma(a.hi, b.hi, -p);
+  return dd_norm(p, e + (a.hi * b.lo + a.lo * b.hi));
+}
+DD dd_div(DD a, double d) {  // a / d for an exact double d
+  const double q1 = a.hi / d;
+  const double r = std::fma(-q1, d, a.hi) + a.lo;
+  return dd_norm(q1, r / d);
+}
+DD dd_neg(DD a) { return {-a.hi, -a.lo}; }
+
+double compute_theta_pade(int two_m, double u) {
+  const int m = two_m / 2;
+  const int K = two_m + 151;
+  std::vector<DD> invf(K + 1), p(m + 1), n(K, DD{0, 0}), q(K, DD{0, 0});
+  invf[0] = {1.0, 0.0};
+  for (int k = 1; k <= K; ++k) invf[k] = dd_div(invf[k - 1], (double)k);
+  for (int j = 0; j <= m; ++j) {  // p_j = prod_{t<j} (m-t)/(2m-t) / j!
+    DD v = invf[j];
+    for (int t = 0; t < j; ++t) v = dd_div(dd_mul(v, DD{(double)(m - t), 0.0}), (double)(2 * m - t));
+    p[j] = v;
+  }
+  for (int k = two_m + 1; k < K; ++k) {
+    DD acc = {0.0, 0.0};
+    for (int j = 0; j <= m; ++j) {
+      const DD t = dd_mul(p[j], invf[k - j]);
+      acc = dd_add(acc, ((k - j) % 2) ? dd_neg(t) : t);
+    }
+    n[k] = acc;
+  }
+  for (int k = 0; k < K; ++k) {  // q = N / p(-x), p(-x)_j = (-1)^j p_j
+    DD acc = n[k];
+    for (int j = 1; j <= m && j <= k; ++j) {
+      const DD t = dd_mul(p[j], q[k - j]);
+      acc = dd_add(acc, (j % 2) ? t : dd_neg(t));
+    }
+    q[k] = acc;
+  }
+  std::vector<double> rho(K, 0.0);
+  for (int i = 0; i < K; ++i) rho[i] = q[i].hi;
+  for (int i = two_m + 1; i < K; ++i)
+    for (int j = two_m + 1; i + j < K; ++j) rho[i + j] -= 0.5 * q[i].hi * q[j].hi;
+  auto f_over_x = [&](double x) {
+    double acc = 0.0, pw = std::pow(x, two_m);  // x^(i-1) at i = 2m+1
+    for (int i = two_m + 1; i < K; ++i) {
+      acc += std::fabs(rho[i]) * pw;
+      pw *= x;
+    }
+    return acc;
+  };
+  double lo = 0.0, hi = 1.0;
+  while (f_over_x(hi) < u) hi *= 2.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid == lo || mid == hi) break;
+    if (f_over_x(mid) < u) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 std::mutex g_theta_mu;
 std::map<std::pair<int, double>, double> g_theta_cache;
 
+// m > 0: Taylor degree m; m < 0: Pade order 2|m|... encoded as -two_m
 double theta_cached(int m, double u) {
   std::lock_guard<std::mutex> lk(g_theta_mu);
   auto key = std::make_pair(m, u);
   auto it = g_theta_cache.find(key);
   if (it != g_theta_cache.end()) return it->second;
-  const double t = compute_theta(m, u);
+  const double t = m > 0 ? compute_theta(m, u) : compute_theta_pade(-m, u);
   g_theta_cache[key] = t;
   return t;
 }
@@ -136,6 +219,11 @@ int least_squarings(double norm, double th) {
 }
 
 int select_ms(double norm, double u, int scheme, int* m, int* s) {
+  if (scheme == BBC_SCHEME_PADE26) {  // the paper's reference method: r_26, s from theta_26
+    *m = 26;
+    *s = least_squarings(norm, theta_cached(-26, u));
+    return BBC_OK;
+  }
   const int *deg, *prod;
   const int cnt = scheme_degrees(scheme, &deg, &prod);
   int bm = -1, bs = 0, bc = 1 << 30;
@@ -276,7 +364,8 @@ int run_step(bbc_handle h, const StepS& st, int64_t N, const double* A, double* 
 int check_flags(int flags) {
   const int scheme = flags & BBC_SCHEME_MASK;
   const int prec = flags & BBC_PREC_MASK;
-  if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS) return fail(BBC_INVALID_ARG, "unknown scheme");
+  if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS && scheme != BBC_SCHEME_PADE26)
+    return fail(BBC_INVALID_ARG, "unknown scheme");
   if (prec != BBC_PREC_FP64 && prec != BBC_PREC_OZAKI) return fail(BBC_INVALID_ARG, "unknown precision");
   if (flags & ~0x3FFF) return fail(BBC_INVALID_ARG, "unknown flag bits");
   if ((flags & BBC_SELECT_MASK) == BBC_SELECT_MASK) return fail(BBC_INVALID_ARG, "two selectors requested");
@@ -302,12 +391,19 @@ int run_expm(bbc_handle h, const double* A, int64_t N, double* Out, int m, int s
   if (!make_program(flags & BBC_SCHEME_MASK, m, s, &prog))
     return fail(BBC_INVALID_ARG, "degree not available in this scheme");
   if (s < 0 || s > 1100) return fail(BBC_INVALID_ARG, "squarings out of range");
+  const bool pade = (flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE26;
+  if (pade && N > 1024) return fail(BBC_UNSUPPORTED, "the Pade comparator serves N <= 1024");
   double* tmp = h->work + (size_t)SL_SQ * N * N;
   double* T = (s % 2 == 0) ? Out : tmp;  // the ping-pong ends in Out
   for (size_t i = 0; i < prog.steps.size(); ++i) {
-    const bool last = (s == 0 && i + 1 == prog.steps.size());
+    const bool last = (s == 0 && i + 1 == prog.steps.size() && !pade);
     const int rc = run_step(h, prog.steps[i], N, A, T, flags, last ? h->dflag : nullptr, stream);
     if (rc) return rc;
+  }
+  if (pade) {  // (-u + v) r_26 = u + v: W8 holds -u + v, T holds u + v
+    LaunchScope scope(h, BBC_KERNEL_LINCOMB, stream);
+    const cudaError_t e = lu_solve_inplace(h->work + (size_t)8 * N * N, T, N, s == 0 ? h->dflag : nullptr, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Pade solve");
   }
   double* src = T;
   for (int k = 0; k < s; ++k) {
@@ -464,9 +560,16 @@ int bbc_theta(int m, double u, double* theta) {
   return BBC_OK;
 }
 
+int bbc_theta_pade(int two_m, double u, double* theta) {
+  if (!theta || two_m < 2 || two_m > 30 || two_m % 2 || !valid_u(u)) return fail(BBC_INVALID_ARG, "bad Pade theta query");
+  *theta = theta_cached(-two_m, u);
+  return BBC_OK;
+}
+
 int bbc_select(double norm1, double u, int scheme, int* m, int* s) {
   if (!m || !s || !valid_u(u)) return fail(BBC_INVALID_ARG, "bad selection query");
-  if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS) return fail(BBC_INVALID_ARG, "unknown scheme");
+  if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS && scheme != BBC_SCHEME_PADE26)
+    return fail(BBC_INVALID_ARG, "unknown scheme");
   if (!std::isfinite(norm1) || norm1 < 0) return fail(BBC_NONFINITE_INPUT, "norm not finite");
   return select_ms(norm1, u, scheme, m, s);
 }

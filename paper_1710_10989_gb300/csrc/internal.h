@@ -82,6 +82,9 @@ cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double al
                           int slices, void* work, unsigned int* flag, cudaStream_t st);
 bool ozaki_supported(int64_t N);
 
+// Solve M X = B in place (X overwrites B, M is destroyed), N <= 1024 (pade.cu).
+cudaError_t lu_solve_inplace(double* M, double* B, int64_t N, unsigned int* flag, cudaStream_t st);
+
 // The (m, s)-proposing MLP (mlp.cu).
 int64_t mlp_param_count(int n_in, int hid, int n_out);
 int64_t mlp_workspace_floats(int hid, int n_out, int64_t B);

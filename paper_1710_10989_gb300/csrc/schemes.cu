@@ -36,6 +36,8 @@ const int NEW_DEG[6] = {1, 2, 4, 8, 12, 18};
 const int NEW_PROD[6] = {0, 1, 2, 3, 4, 5};
 const int PS_DEG[7] = {1, 2, 4, 6, 9, 12, 16};
 const int PS_PROD[7] = {0, 1, 2, 3, 4, 5, 6};
+const int PADE_DEG[1] = {26};
+const int PADE_PROD[1] = {6};
 
 double inv_factorial(int k) {
   double f = 1.0;
@@ -142,6 +144,7 @@ bool make_prefilled_program(int m, Program* p, int* a2_slot, int* a3_slot) {
 
 int scheme_degrees(int scheme, const int** deg, const int** products) {
   if (scheme == BBC_SCHEME_PS) { *deg = PS_DEG; *products = PS_PROD; return 7; }
+  if (scheme == BBC_SCHEME_PADE26) { *deg = PADE_DEG; *products = PADE_PROD; return 1; }
   *deg = NEW_DEG; *products = NEW_PROD; return 6;
 }
 
@@ -151,6 +154,27 @@ bool make_program(int scheme, int m, int s, Program* p) {
   p->steps.clear();
   const double sig = std::ldexp(1.0, -s);     // X = sig * A
   const double sig2 = sig * sig;
+  if (scheme == BBC_SCHEME_PADE26) {           // eq. (pade26): numerator and denominator of r_26
+    if (m != 26) return false;
+    double b[14];                              // p_13(x) = sum b_j x^j, eq. (24), b_0 = 1
+    for (int j = 0; j <= 13; ++j) {
+      double v = inv_factorial(j);
+      for (int t = 0; t < j; ++t) v *= (double)(13 - t) / (double)(26 - t);
+      b[j] = v;
+    }
+    add(p, Step(SL_A, SL_A, sig2).out(Out(W0, 1.0)));                             // A2
+    add(p, Step(W0, W0, 1.0).out(Out(W1, 1.0)));                                  // A4
+    add(p, Step(W0, W1, 1.0)                                                       // A6, and
+               .out(Out(W2, 1.0))
+               .out(Out(W3, b[13]).t(W1, b[11]).t(W0, b[9]))                       // b13 A6 + b11 A4 + b9 A2
+               .out(Out(W4, b[12]).t(W1, b[10]).t(W0, b[8])));                     // b12 A6 + b10 A4 + b8 A2
+    add(p, Step(W2, W3, 1.0).out(Out(W5, 1.0, b[1]).t(W2, b[7]).t(W1, b[5]).t(W0, b[3])));
+    add(p, Step(SL_A, W5, sig).out(Out(W6, 1.0)));                                // u13 = A (...)
+    add(p, Step(W2, W4, 1.0).out(Out(W7, 1.0, b[0]).t(W2, b[6]).t(W1, b[4]).t(W0, b[2])));  // v13
+    add(p, Step(-1, -1, 0.0).out(Out(W8, 0.0).t(W6, -1.0).t(W7, 1.0))             // -u + v
+               .out(Out(SL_T, 0.0).t(W6, 1.0).t(W7, 1.0)));                       // u + v
+    return true;                                                                   // then (-u + v) r = u + v
+  }
   if (m == 1) {                                // T1 = I + X
     add(p, Step(-1, -1, 0.0).out(Out(SL_T, 0.0, 1.0).t(SL_A, sig)));
     return true;

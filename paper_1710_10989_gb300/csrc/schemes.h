@@ -42,8 +42,10 @@ struct Program {
   std::vector<StepS> steps;
 };
 
-// scheme: BBC_SCHEME_NEW or BBC_SCHEME_PS; returns false for a degree the
-// scheme does not have.
+// scheme: BBC_SCHEME_NEW, BBC_SCHEME_PS (Taylor degree m) or BBC_SCHEME_PADE26
+// (m = 26: the numerator / denominator products of eq. pade26, leaving -u + v in
+// W8 and u + v in the result slot for the solve); false for a degree the scheme
+// does not have.
 bool make_program(int scheme, int m, int s, Program* out);
 
 // T12 / T18 of the reduced-product scheme for a caller that already holds the

@@ -67,3 +67,19 @@ def test_host_argument_errors():
     assert e.value.code == api.NONFINITE_INPUT
     with pytest.raises(api.BBCError):
         api.select(1.0, u=0.5)
+
+
+@pytest.mark.parametrize("u", [2.0 ** -53, 2.0 ** -24])
+def test_library_pade_theta_matches_oracle(u):
+    # double-double series in the library, exact rationals in the oracle
+    from paper_1710_10989_gb300 import api
+    for two_m in (2, 6, 10, 14, 18, 26):
+        assert api.theta_pade(two_m, u) == pytest.approx(TH.theta_pade(two_m, u), rel=1e-13)
+
+
+def test_library_pade_selection_matches_oracle():
+    from oracle import oracle as O
+    from paper_1710_10989_gb300 import api
+    import numpy as np
+    for nrm in np.logspace(-3, 3, 200):
+        assert api.select(float(nrm), scheme=api.SCHEME_PADE26) == O.select(float(nrm), "pade26")

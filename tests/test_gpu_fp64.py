@@ -154,3 +154,33 @@ def test_dense_4096_full_size(h, api, idx, nonnormal):
     want, oi = O.expm(A, "new")
     assert (info.m, info.s) == (oi.m, oi.s)
     assert rel_fro(to_host(out), want) < 1e-12
+
+
+# ---- the Pade r_26 comparator on the GPU --------------------------------------------------------
+
+def test_small_workload_pade26(h, api):
+    """64 x 64, ||A||_1 = 1: r_26 with s = 0 (the paper's reference method), GPU vs oracle."""
+    A = W.small_case()
+    out = empty_like_dev(64)
+    info = h.expm(to_dev(A), out, 0.0, api.SCHEME_PADE26)
+    want, oi = O.expm(A, "pade26")
+    assert (info.m, info.s, info.products) == (oi.m, oi.s, oi.products) == (26, 0, 6)
+    assert rel_fro(to_host(out), want) < 1e-13
+
+
+@pytest.mark.parametrize("n,norm,nonnormal", [(96, 20.0, False), (300, 100.0, True), (257, 0.3, False)])
+def test_pade26_matches_oracle(h, api, n, norm, nonnormal):
+    A = W.nonnormal_upper(n, 7, norm) if nonnormal else W.gaussian(n, 8, norm)
+    out = empty_like_dev(n)
+    info = h.expm(to_dev(A), out, 0.0, api.SCHEME_PADE26)
+    want, oi = O.expm(A, "pade26")
+    assert (info.m, info.s) == (oi.m, oi.s)
+    assert rel_fro(to_host(out), want) < 1e-12
+
+
+def test_pade26_split_products(h, api):
+    A = W.gaussian(200, 9, 5.0)
+    out = empty_like_dev(200)
+    h.expm(to_dev(A), out, 0.0, api.SCHEME_PADE26 | api.PREC_OZAKI)
+    want, _ = O.expm(A, "pade26")
+    assert rel_fro(to_host(out), want) < 1e-12
