@@ -33,6 +33,26 @@ sys.path.insert(0, ROOT)
 from paper_1710_10989_gb300 import workloads as W  # noqa: E402
 
 PI = {1: 0, 2: 1, 4: 2, 8: 3, 12: 4, 18: 5}
+# DRAM traffic per launch of the dominant kernels from one ncu capture each (profiles/),
+# valid only while the kernel source is the one that was captured.
+NCU_TRAFFIC = {
+    "gemm_ozaki.cu": ("417c891e64454be19866565803975cf69f3356aafd1b2c909da2896594987471", 4096, 7.753078e9 + 0.168836352e9),
+    "gemm_f64.cu": ("c1965ca226ec4ee76ccab7620c3105f1abf10d5ba9ea3047e862e9126f56b6a5", 4096, 3.733487e9 + 0.133997312e9),
+    "batched.cu": ("3f86258f8371369fa84e7c05b2e817d5299e265d45b46618f23f4add0ce661b4", 512, 3.662761e9 + 1.816421e9),
+}
+
+
+def ncu_traffic(source: str, n: int):
+    import hashlib
+    sha, n_cap, traffic = NCU_TRAFFIC[source]
+    path = os.path.join(ROOT, "paper_1710_10989_gb300", "csrc", source)
+    try:
+        cur = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return traffic if (cur == sha and n == n_cap) else None
+
+
 # FP64 pipe: the GB300's nominal 1.25 TFLOP/s FP64 is 2 DFMA per clock per SM:
 # 152 SMs x 2 DFMA x 2 flop x 2.07 GHz (maximum SM clock).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -318,7 +338,8 @@ def run_dense(args, torch, dist, api, rank, world, local):
     logical = flops_per_product / (avg_ms / 1e3) / 1e12
     if args.precision == "fp64":
         roof = {"bound": "alu", "achieved": logical, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": logical / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_gemm_f64<64,64>",
+                "frac": logical / FP64_PEAK_TFLOPS, "traffic": ncu_traffic("gemm_f64.cu", n),
+                "kernel": "k_gemm_f64<64,64>",
                 "peak_source": "FP64 pipe, 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
                 "flops_per_launch": flops_per_product, "avg_launch_ms": avg_ms, "launches": prod_launches}
     else:
@@ -326,7 +347,8 @@ def run_dense(args, torch, dist, api, rank, world, local):
         executed = pairs * flops_per_product / (avg_ms / 1e3) / 1e12
         peak = pk.get("bf16_tflops", 1899.1)
         roof = {"bound": "tensor", "achieved": executed, "peak": peak, "unit": "TFLOP/s",
-                "frac": executed / peak, "traffic": None,
+                "frac": executed / peak,
+                "traffic": ncu_traffic("gemm_ozaki.cu", n) if args.slices == 7 else None,
                 "kernel": f"k_ozaki_gemm ({args.slices} BF16 slices: {pairs} slice products per FP64 product)",
                 "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS)" if "bf16_tflops" in pk
                                 else "fallback 1.9 PFLOP/s bf16"),

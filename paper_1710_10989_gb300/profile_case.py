@@ -16,7 +16,9 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=("gemm", "expm", "norm"), default="gemm")
+    ap.add_argument("--kernel", choices=("gemm", "expm", "norm", "batched"), default="gemm")
+    ap.add_argument("--count", type=int, default=512, help="matrices of --kernel batched")
+    ap.add_argument("--selector", choices=("plain", "learned"), default="learned")
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--norm", type=float, default=1.0)
     ap.add_argument("--precision", choices=("fp64", "ozaki"), default="fp64")
@@ -30,6 +32,25 @@ def main():
     from paper_1710_10989_gb300 import workloads as W
 
     flags = api.PREC_FP64 if a.precision == "fp64" else api.PREC_OZAKI | api.ozaki_slices(a.slices)
+    if a.kernel == "batched":  # the batched workload's distribution, binary32 storage
+        mats = W.batch_matrices(a.count)
+        h = api.Handle(0)
+        bflags = 0 if a.precision == "fp64" else api.PREC_OZAKI
+        h.batch_reserve(256, bflags)
+        if a.selector == "learned":
+            from paper_1710_10989_gb300 import selector as SEL
+            SEL.install(h)
+            bflags |= api.SELECT_LEARNED
+        order = api.batch_order([m.shape[0] for m in mats])
+        ins = [torch.from_numpy(mats[i]).cuda() for i in order]
+        outs = [torch.empty_like(x) for x in ins]
+        b = api.Batch(ins, outs)
+        for _ in range(a.reps):
+            h.expm_batched(b, flags=bflags)
+        torch.cuda.synchronize()
+        h.close()
+        print("done", a)
+        return
     h = api.Handle(0)
     A = torch.from_numpy(W.gaussian(a.n, 1, a.norm)).cuda()
     B = torch.from_numpy(W.gaussian(a.n, 2, a.norm)).cuda()
