@@ -478,7 +478,7 @@ __device__ int block_mlp_argmax(const BatchArgs& a, const float* f, float* h1, f
 
 }  // namespace
 
-__global__ void __launch_bounds__(BATCH_THREADS, 1) k_batched_expm(const BatchArgs args) {
+__global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchArgs args) {
 
   __shared__ GemmSmem sm;
   __shared__ Epilogue s_epi;
@@ -740,10 +740,12 @@ size_t batched_workspace_bytes(int64_t nmax, int ctas, bool split) {
          (split ? (size_t)ctas * OZB_WORDS * sizeof(uint32_t) : 0);
 }
 
+// Two resident CTAs per SM (128 registers, ~43 KB shared memory each): while one
+// waits on its loads the other computes.
 int batched_ctas(int device) {
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) sms = 152;
-  return sms;
+  return 2 * sms;
 }
 
 namespace {
