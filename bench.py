@@ -359,7 +359,7 @@ def run_dense(args, torch, dist, api, rank, world, local):
                                                                                and args.slices in (6, 7)) else None,
                 "traffic_note": "ncu capture at 7 slices; slice-plane traffic scales with slice pairs" if
                                 args.slices == 6 else None,
-                "kernel": f"k_ozaki_gemm ({args.slices} BF16 slices: {pairs} slice products per FP64 product)",
+                "kernel": f"k_ozaki_pair ({args.slices} BF16 slices: {pairs} slice products per FP64 product)",
                 "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS)" if "bf16_tflops" in pk
                                 else "fallback 1.9 PFLOP/s bf16"),
                 "flops_per_launch": pairs * flops_per_product, "avg_launch_ms": avg_ms,

@@ -28,8 +28,8 @@
 //    integer below 2^24 and FP32 holds it exactly: the K loop of these pairs is
 //    cut into 1024-wide chunks, and after each chunk the FP32 tile is drained from
 //    TMEM, converted to int32 and added, shifted by 2^(8(4-g)), into an integer
-//    accumulator R (two 32-bit TMEM planes; |R| < 2^60 for N <= 16384).
-//  * Low groups g >= 5 weigh at most 2^-40. They accumulate in a second FP32 TMEM
+//    accumulator R (64 bits per element, held in registers; |R| < 2^61 for N <= 16384).
+//  * Low groups g >= 5 weigh at most 2^-40. They accumulate in an FP32 TMEM
 //    tile over the whole K, Horner-style from the smallest weight up, the MMA
 //    scaling the running sum by 2^-8 (scale-input-d) at each change of group.
 //    That FP32 sum of up to ~10^5 terms loses roughly 2^-16 of itself, i.e. about
@@ -37,21 +37,15 @@
 //    the same loss showed up as ~1e-14 relative error per product at N = 4096.)
 //  C_ij = 2^(e_i + f_j - 48) (R + 2^-8 LOW).
 //
-// Kernel shape (one CTA per 128 x 128 output tile, 6 warps):
-//   warp 0: TMA producer (3-D tensor maps over the slice planes, 128B swizzle),
-//           6-stage ring of 128x64 BF16 A and B tiles;
-//   warp 1: tcgen05.mma issuer (M=128, N=128, K=16, BF16 -> FP32 in TMEM). High
-//           and low chunks are interleaved so each drain overlaps low-group MMAs;
-//   warps 2-5: drain (tcgen05.ld / st) and the final FP64 epilogue.
-//           with no low groups (k <= 5) the high accumulator is double-buffered;
-// TMEM: [0,128) high accumulator, [128,256) low accumulator (or the second high
-// buffer), [256,384) low and [384,512) high words of R.
+// The product kernel, k_ozaki_pair, is described at its definition: CTA pairs
+// (tcgen05.mma.cta_group::2) on persistent 256 x 128 output tiles, TMA-fed.
 // Every mbarrier wait is bounded in time; on expiry the kernel records a
 // timeout in the status word, lets its copies and MMAs finish (bounded again),
 // frees TMEM and returns.
 #include <cuda.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -60,13 +54,9 @@
 namespace bbc {
 namespace {
 
-constexpr int TILE = 128;          // M = N tile
+constexpr int TILE = 128;          // rows per CTA and columns of an output tile
 constexpr int KSTEP = 64;          // BF16 elements per 128-byte swizzle row
 constexpr int CHUNK_STEPS = 16;    // 16 x 64 = 1024 K per exact FP32 chunk
-constexpr int STAGES = 6;
-constexpr int STAGE_BYTES = TILE * KSTEP * 2;  // 16 KB per operand tile
-constexpr int NUM_THREADS = 192;
-constexpr int NUM_EPI = 128;
 constexpr int G_EXACT = 5;         // groups 0..4 are summed exactly
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;  // 2 s per wait
 constexpr unsigned int STATUS_NONFINITE = 1u;  // bits of the handle's status word
@@ -83,9 +73,6 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
@@ -116,14 +103,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     }
   }
 }
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
-                                            int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-      "[%2];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -138,61 +117,20 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   d |= (uint64_t)2 << 61;                          // 128-byte swizzle
   return d;
 }
-// Instruction descriptor, kind::f16: BF16 A and B, FP32 D, both K-major.
-constexpr uint32_t IDESC = (1u << 4)                     // D = F32
-                           | (1u << 7)                   // A = BF16
-                           | (1u << 10)                  // B = BF16
-                           | ((uint32_t)(TILE >> 3) << 17)   // N
-                           | ((uint32_t)(TILE >> 4) << 24);  // M
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+// 32 lanes x 16 (8) consecutive 32-bit TMEM columns: thread t gets lane (base + t).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
-      : "memory");
-}
-// D = A B + 2^-8 D (the running low-group sum moves one group down in weight)
-__device__ __forceinline__ void mma_bf16_scaled(uint32_t d_tmem, uint64_t a, uint64_t b) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, 1, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p, 8;\n}\n" ::"r"(
-          d_tmem),
-      "l"(a), "l"(b), "r"(IDESC)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-#define TMEM_REGS32(r)                                                                                      \
-  "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), \
-      "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),   \
-      "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),  \
-      "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-#define TMEM_VALS32(r)                                                                                          \
-  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), \
-      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]),           \
-      "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]),            \
-      "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
-
-// 32 lanes x 32 consecutive 32-bit columns: thread t gets lane (base + t).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : TMEM_REGS32(r)
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
-      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
-      TMEM_VALS32(r)
-      : "memory");
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ------------------------------------------------------------ digit extraction
 // Biased exponent field of x; subnormals and zero report 1 and 0 respectively
@@ -338,251 +276,404 @@ k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, co
 }
 
 // ------------------------------------------------------------ the product kernel
-struct Shared {
-  uint64_t full[STAGES];
-  uint64_t empty[STAGES];
-  uint64_t acc_full[2];
-  uint64_t acc_empty[2];
-  uint64_t low_done;
+// k_ozaki_pair: a cluster of two CTAs computes 256 x 128 output tiles with
+// tcgen05.mma.cta_group::2 (M = 256, N = 128, K = 16): CTA r of the pair stages rows
+// [128 r, 128 r + 128) of the P slice tile and rows [64 r, 64 r + 64) of the Q^T slice
+// tile, and its TMEM receives its 128 x 128 half of the output tile. Per SM that is
+// 24 KB of operands per 64-wide K step (a lone 128 x 128 tile needs 32 KB), so nine
+// steps fit in flight and the L2 serves a quarter fewer bytes per flop.
+//
+// The exact integer accumulator R of the high groups lives in the registers of eight
+// drain warps (64 columns x 64 bits each), which leaves TMEM for two high-group FP32
+// buffers (the MMAs never wait for a drain) and two low-group buffers. The kernel is
+// persistent: every tile runs its low items first, so the MMAs of tile t + 1 proceed
+// while the drain warps compute the epilogue of tile t from R and the other low buffer.
+//
+// Roles (320 threads per CTA): warp 0 TMA producer (both CTAs; their copies signal the
+// even CTA's "full" barriers), warp 1 MMA issuer (even CTA only; commits are multicast
+// to both CTAs), warps 2..9 drains and epilogue (both CTAs; they release buffers by
+// arriving on the even CTA's barriers). 320 threads cap registers at 168 per thread
+// (the register file is split over four sub-partitions and one of them holds three
+// warps), which is why TMEM loads go 16 (drain) and 8 (epilogue) columns at a time.
+// TMEM columns per CTA: [0,128) and [128,256) high buffers, [256,384) and [384,512)
+// low buffers.
+constexpr int P_STAGES = 9;
+constexpr int P_A_BYTES = TILE * KSTEP * 2;          // 128 rows of a P slice plane
+constexpr int P_B_BYTES = (TILE / 2) * KSTEP * 2;    // 64 rows of a Q^T slice plane
+constexpr int P_STAGE_BYTES = P_A_BYTES + P_B_BYTES;
+constexpr int P_THREADS = 320;
+constexpr int P_DRAIN_WARPS = 8;
+constexpr int P_GROUP_M = 8;                         // raster: 8 tile rows per column sweep
+// Instruction descriptor, kind::f16: D = F32 (bit 4), A = B = BF16 (bits 7, 10), both K-major,
+// N = 128 (bits 17-22: N / 8), M = 256 (bits 24-28: M / 16).
+constexpr uint32_t IDESC_PAIR = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TILE >> 3) << 17) |
+                                ((uint32_t)(2 * TILE >> 4) << 24);
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ int cluster_index() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return (int)r;
+}
+__device__ __forceinline__ int cluster_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return (int)r;
+}
+// Address of the same shared variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
+  uint32_t out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(smem_u32(p)), "r"(rank));
+  return out;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait with cluster-scope acquire (the barrier may be completed from the peer CTA).
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t* bar, uint32_t parity, volatile int* cta_err) {
+  if (mbar_try_wait_cl(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait_cl(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*cta_err) return false;
+      if (globaltimer() - t0 > TIMEOUT_NS) {
+        *cta_err = 1;
+        return false;
+      }
+    }
+  }
+}
+// TMA tile load into this CTA's shared memory, completing bytes on a barrier that may
+// belong to the peer CTA (cluster address).
+__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map, uint32_t bar_cluster, int x,
+                                                 int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, "
+      "%5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(bar_cluster), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void mma_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(IDESC_PAIR), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_pair_scaled(uint32_t d_tmem, uint64_t a, uint64_t b) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, 1, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p, 8;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(IDESC_PAIR)
+      : "memory");
+}
+// Arrive on the barrier at this offset in both CTAs once all prior MMAs completed.
+__device__ __forceinline__ void commit_pair(uint64_t* bar) {
+  const uint16_t both = 3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(both)
+      : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+struct PairShared {
+  uint64_t full[P_STAGES];   // even CTA: both CTAs' copies of a stage landed
+  uint64_t empty[P_STAGES];  // each CTA: the MMAs reading its stage completed
+  uint64_t acc_full[2];      // each CTA: a high buffer holds a finished chunk
+  uint64_t acc_empty[2];     // even CTA: all 16 drain warps read that buffer
+  uint64_t low_full[2];      // each CTA: a low buffer holds a tile's low groups
+  uint64_t low_empty[2];     // even CTA: all 16 drain warps read that low buffer
   uint64_t mma_done;
   uint32_t tmem_base;
   int err;
 };
+constexpr size_t PAIR_SMEM_BYTES = (size_t)P_STAGES * P_STAGE_BYTES + sizeof(PairShared) + 1024;
 
-// Work items: 1024-wide K chunks of slice pairs. High items (g <= 3) in order of
-// increasing g; low items (g >= 4) in order of decreasing g (the Horner order).
-struct Sched {
-  int nslices, nch, nH, nL;
-  __device__ Sched(int k, int nch_) : nslices(k), nch(nch_) {
-    const int gh = min(k, G_EXACT);
-    nH = gh * (gh + 1) / 2 * nch;
-    nL = (k * (k + 1) / 2 - gh * (gh + 1) / 2) * nch;
+// Tile t -> (pair row block mp, column block nt); P_GROUP_M row blocks sweep the
+// columns together so that concurrently running tiles share operand rows in L2.
+__device__ __forceinline__ void pair_tile(int t, int tiles_m, int tiles_n, int* mp, int* nt) {
+  const int per_group = P_GROUP_M * tiles_n;
+  const int grp = t / per_group;
+  const int first = grp * P_GROUP_M;
+  const int rows = min(P_GROUP_M, tiles_m - first);
+  const int w = t - grp * per_group;
+  *mp = first + w % rows;
+  *nt = w / rows;
+}
+
+// Work items of one output tile, in the order all three roles walk them: the low
+// groups first (g = k-1 down to G_EXACT: the Horner order), then the high groups
+// (g = 0 up); inside a group the slice pairs p = 0..g (q = g - p), inside a pair the
+// 1024-wide K chunks c. Advancing needs no division (the MMA issuer's time per item
+// matters: it must keep a new MMA ready every ~65 cycles).
+struct ItemCursor {
+  int g, p, c;
+  bool low;
+  int nch;
+  __device__ ItemCursor(int k, int nch_) : p(0), c(0), nch(nch_) {
+    low = k > G_EXACT;
+    g = low ? k - 1 : 0;
   }
-  __device__ void high(int i, int* g, int* p, int* c) const {
-    int gg = 0, base = 0;
-    while (i >= base + (gg + 1) * nch) { base += (gg + 1) * nch; ++gg; }
-    *g = gg;
-    *p = (i - base) / nch;
-    *c = (i - base) % nch;
-  }
-  __device__ void low(int i, int* g, int* p, int* c) const {
-    int gg = nslices - 1, base = 0;
-    while (i >= base + (gg + 1) * nch) { base += (gg + 1) * nch; --gg; }
-    *g = gg;
-    *p = (i - base) / nch;
-    *c = (i - base) % nch;
-  }
-  // idx-th item of the interleaved order H0 L0 H1 L1 ..., then the longer tail.
-  // Returns true for a low item; *i is its index within its own list.
-  __device__ bool item(int idx, int* i) const {
-    const int m = min(nH, nL);
-    if (idx < 2 * m) { *i = idx >> 1; return idx & 1; }
-    *i = idx - m;
-    return nL > nH;
+  __device__ void advance() {
+    if (++c < nch) return;
+    c = 0;
+    if (++p <= g) return;
+    p = 0;
+    if (!low) {
+      ++g;
+    } else if (--g < G_EXACT) {
+      low = false;
+      g = 0;
+    }
   }
 };
 
-__global__ void __launch_bounds__(NUM_THREADS, 1)
-k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+__global__ void __launch_bounds__(P_THREADS, 1)
+k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const int* __restrict__ erow, const int* __restrict__ fcol, const double* __restrict__ P,
              const double* __restrict__ Q, const double* __restrict__ pdiag, const double* __restrict__ qdiag,
-             int64_t N, double alpha, int nslices, int nksteps, const Epilogue e,
+             int64_t N, double alpha, int nslices, int nksteps, int tiles_m, int tiles_n, const Epilogue e,
              unsigned int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   uint8_t* smA = smem;
-  uint8_t* smB = smem + STAGES * STAGE_BYTES;
-  Shared* sh = reinterpret_cast<Shared*>(smem + 2 * STAGES * STAGE_BYTES);
+  uint8_t* smB = smem + P_STAGES * P_A_BYTES;
+  PairShared* sh = reinterpret_cast<PairShared*>(smem + P_STAGES * P_STAGE_BYTES);
   volatile int* cta_err = &sh->err;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.y * TILE, n0 = (int64_t)blockIdx.x * TILE;
+  const uint32_t rank = cluster_rank();
+  const int cid = cluster_index(), ncl = cluster_count();
+  const int ntiles = tiles_m * tiles_n;
   const int nch = (nksteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
-  const Sched sc(nslices, nch);
-  const int nunits = sc.nH + sc.nL;
-  const int nbuf = sc.nL > 0 ? 1 : 2;  // the low accumulator takes the second buffer
+  const int gh = min(nslices, G_EXACT);                        // high groups 0..gh-1
+  const int nH = gh * (gh + 1) / 2 * nch;                        // high items per tile
+  const int nL = nslices * (nslices + 1) / 2 * nch - nH;         // low items per tile
+  const int nunits = nH + nL;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) { mbar_init(&sh->full[s], 1); mbar_init(&sh->empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&sh->acc_full[b], 1); mbar_init(&sh->acc_empty[b], NUM_EPI); }
-    mbar_init(&sh->low_done, 1);
+    for (int s = 0; s < P_STAGES; ++s) { mbar_init(&sh->full[s], 1); mbar_init(&sh->empty[s], 1); }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh->acc_full[b], 1);
+      mbar_init(&sh->acc_empty[b], 2 * P_DRAIN_WARPS);
+      mbar_init(&sh->low_full[b], 1);
+      mbar_init(&sh->low_empty[b], 2 * P_DRAIN_WARPS);
+    }
     mbar_init(&sh->mma_done, 1);
     sh->err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&sh->tmem_base))
+  if (warp == 0) {  // one warp of each CTA of the pair allocates, together
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&sh->tmem_base))
                  : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();  // the peer's barriers are initialised before any remote arrival
   tc_fence_after();
   const uint32_t tmem = sh->tmem_base;
 
   if (warp == 0) {
-    // ---------------- TMA producer
+    // ---------------- TMA producer (both CTAs)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
-      int it = 0;
+      int s = 0;
+      uint32_t ph = 0;
       bool ok = true;
-      for (int idx = 0; idx < nunits && ok; ++idx) {
-        int i, g, p, c;
-        if (sc.item(idx, &i)) sc.low(i, &g, &p, &c); else sc.high(i, &g, &p, &c);
-        const int ks1 = min(nksteps, (c + 1) * CHUNK_STEPS);
-        for (int ks = c * CHUNK_STEPS; ks < ks1; ++ks, ++it) {
-          const int s = it % STAGES;
-          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-          if (!mbar_wait(&sh->empty[s], ph ^ 1u, cta_err)) { ok = false; break; }
-          mbar_arrive_expect_tx(&sh->full[s], 2 * STAGE_BYTES);
-          tma_load_3d(smA + s * STAGE_BYTES, &tmA, &sh->full[s], ks * KSTEP, (int)m0, p);
-          tma_load_3d(smB + s * STAGE_BYTES, &tmB, &sh->full[s], ks * KSTEP, (int)n0, g - p);
+      for (int t = cid; t < ntiles && ok; t += ncl) {
+        int mp, nt;
+        pair_tile(t, tiles_m, tiles_n, &mp, &nt);
+        const int arow = mp * 2 * TILE + (int)rank * TILE;
+        const int brow = nt * TILE + (int)rank * (TILE / 2);
+        ItemCursor cur(nslices, nch);
+        for (int idx = 0; idx < nunits && ok; ++idx, cur.advance()) {
+          const int ks1 = min(nksteps, (cur.c + 1) * CHUNK_STEPS);
+          for (int ks = cur.c * CHUNK_STEPS; ks < ks1; ++ks) {
+            if (!mbar_wait(&sh->empty[s], ph ^ 1u, cta_err)) { ok = false; break; }
+            if (rank == 0) mbar_arrive_expect_tx(&sh->full[s], 2 * P_STAGE_BYTES);
+            const uint32_t fb = peer_addr(&sh->full[s], 0);
+            tma_load_3d_pair(smA + s * P_A_BYTES, &tmA, fb, ks * KSTEP, arow, cur.p);
+            tma_load_3d_pair(smB + s * P_B_BYTES, &tmB, fb, ks * KSTEP, brow, cur.g - cur.p);
+            if (++s == P_STAGES) { s = 0; ph ^= 1u; }
+          }
         }
       }
-      if (!ok) {
-        // let the copies already issued land before the CTA goes away (one
-        // overall deadline; a stage whose phase moved on is simply skipped)
+      if (!ok) {  // give copies already issued time to land (error path only)
         const unsigned long long t0 = globaltimer();
-        for (int back = 1; back <= STAGES && back <= it; ++back) {
-          const int i2 = it - back;
-          while (!mbar_try_wait(&sh->full[i2 % STAGES], (uint32_t)(i2 / STAGES) & 1u) &&
-                 globaltimer() - t0 < TIMEOUT_NS / 16) {
-          }
+        while (globaltimer() - t0 < 1000000ull) {
         }
       }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer
-    if (lane == 0) {
-      int it = 0;
+    // ---------------- MMA issuer (even CTA). The first K step of each item is
+    // peeled off: it alone carries the accumulate / scale choice, so the steady
+    // loop is four unconditional MMAs and a commit.
+    if (rank == 0 && lane == 0) {
+      const uint64_t dA0 = smem_desc(smem_u32(smA)), dB0 = smem_desc(smem_u32(smB));
+      int s = 0;
+      uint32_t ph = 0;
+      int hc = 0, tl = 0;
       bool ok = true;
-      for (int idx = 0; idx < nunits && ok; ++idx) {
-        int i, g, p, c;
-        const bool is_low = sc.item(idx, &i);
-        uint32_t d_tmem;
-        int b = 0;
-        if (is_low) {
-          sc.low(i, &g, &p, &c);
-          d_tmem = tmem + (uint32_t)TILE;  // low-group accumulator
-        } else {
-          sc.high(i, &g, &p, &c);
-          b = i % nbuf;
-          if (!mbar_wait(&sh->acc_empty[b], ((uint32_t)(i / nbuf) & 1u) ^ 1u, cta_err)) { ok = false; break; }
+      for (int t = cid; t < ntiles && ok; t += ncl, ++tl) {
+        const int lb = tl & 1;
+        if (nL > 0) {
+          if (!mbar_wait_cl(&sh->low_empty[lb], ((uint32_t)(tl >> 1) & 1u) ^ 1u, cta_err)) { ok = false; break; }
           tc_fence_after();
-          d_tmem = tmem + (uint32_t)(b * TILE);
         }
-        const int ks0 = c * CHUNK_STEPS, ks1 = min(nksteps, (c + 1) * CHUNK_STEPS);
-        for (int ks = ks0; ks < ks1; ++ks, ++it) {
-          const int s = it % STAGES;
-          if (!mbar_wait(&sh->full[s], (uint32_t)(it / STAGES) & 1u, cta_err)) { ok = false; break; }
-          tc_fence_after();
-          const uint64_t da = smem_desc(smem_u32(smA + s * STAGE_BYTES));
-          const uint64_t db = smem_desc(smem_u32(smB + s * STAGE_BYTES));
-#pragma unroll
-          for (int kk = 0; kk < KSTEP / 16; ++kk) {  // +32 bytes per K=16 step inside the swizzle row
-            const bool first = (ks == ks0 && kk == 0);
-            if (!is_low) {
-              mma_bf16(d_tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), first ? 0u : 1u);
-            } else if (first && i == 0) {                      // start of the low sum
-              mma_bf16(d_tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), 0u);
-            } else if (first && p == 0 && c == 0) {            // next group: weight moves by 2^-8
-              mma_bf16_scaled(d_tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2));
-            } else {
-              mma_bf16(d_tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), 1u);
-            }
+        ItemCursor cur(nslices, nch);
+        for (int idx = 0; idx < nunits && ok; ++idx, cur.advance()) {
+          uint32_t d_tmem;
+          int b = 0, kind0;  // first MMA: 0 fresh, 1 accumulate, 2 accumulate onto 2^-8 x the sum so far
+          if (cur.low) {
+            d_tmem = tmem + 256u + (uint32_t)(lb * TILE);
+            kind0 = (idx == 0) ? 0 : ((cur.p == 0 && cur.c == 0) ? 2 : 1);
+          } else {
+            b = hc & 1;
+            if (!mbar_wait_cl(&sh->acc_empty[b], ((uint32_t)(hc >> 1) & 1u) ^ 1u, cta_err)) { ok = false; break; }
+            tc_fence_after();
+            d_tmem = tmem + (uint32_t)(b * TILE);
+            kind0 = 0;
           }
-          mma_commit(&sh->empty[s]);
+          const int ks1 = min(nksteps, (cur.c + 1) * CHUNK_STEPS);
+          if (!mbar_wait_cl(&sh->full[s], ph, cta_err)) { ok = false; break; }
+          tc_fence_after();
+          {
+            const uint64_t da = dA0 + (uint64_t)(s * (P_A_BYTES >> 4)), db = dB0 + (uint64_t)(s * (P_B_BYTES >> 4));
+            if (kind0 == 2) mma_pair_scaled(d_tmem, da, db);
+            else mma_pair(d_tmem, da, db, (uint32_t)kind0);
+            mma_pair(d_tmem, da + 2, db + 2, 1u);  // +32 bytes per K = 16 inside the swizzle row
+            mma_pair(d_tmem, da + 4, db + 4, 1u);
+            mma_pair(d_tmem, da + 6, db + 6, 1u);
+            commit_pair(&sh->empty[s]);
+            if (++s == P_STAGES) { s = 0; ph ^= 1u; }
+          }
+          for (int ks = cur.c * CHUNK_STEPS + 1; ks < ks1; ++ks) {
+            if (!mbar_wait_cl(&sh->full[s], ph, cta_err)) { ok = false; break; }
+            tc_fence_after();
+            const uint64_t da = dA0 + (uint64_t)(s * (P_A_BYTES >> 4)), db = dB0 + (uint64_t)(s * (P_B_BYTES >> 4));
+            mma_pair(d_tmem, da, db, 1u);
+            mma_pair(d_tmem, da + 2, db + 2, 1u);
+            mma_pair(d_tmem, da + 4, db + 4, 1u);
+            mma_pair(d_tmem, da + 6, db + 6, 1u);
+            commit_pair(&sh->empty[s]);
+            if (++s == P_STAGES) { s = 0; ph ^= 1u; }
+          }
+          if (!ok) break;
+          if (!cur.low) {
+            commit_pair(&sh->acc_full[b]);
+            ++hc;
+          } else if (idx == nL - 1) {
+            commit_pair(&sh->low_full[lb]);
+          }
         }
-        if (!ok) break;
-        if (!is_low) mma_commit(&sh->acc_full[b]);
-        else if (i == sc.nL - 1) mma_commit(&sh->low_done);
       }
-      // no MMA may still be writing TMEM when the CTA frees it
-      mma_commit(&sh->mma_done);
+      commit_pair(&sh->mma_done);
+    }
+    if (lane == 0) {  // no MMA may still write either CTA's TMEM when it is freed
       const unsigned long long t0 = globaltimer();
       while (!mbar_try_wait(&sh->mma_done, 0u) && globaltimer() - t0 < TIMEOUT_NS) {
       }
     }
   } else {
-    // ---------------- drain + epilogue (warps 2..5 cover TMEM lane quarters 2,3,0,1)
-    const int q = warp & 3;
+    // ---------------- drains + epilogue (warps 2..9 of both CTAs)
+    const int q = warp & 3;                // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;      // which 64 of the tile's 128 columns
     const int row_in_tile = q * 32 + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-    uint32_t z[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) z[i] = 0u;
-#pragma unroll
-    for (int c4 = 0; c4 < 4; ++c4) {
-      tmem_st32(lane_base + 256 + 32 * c4, z);
-      tmem_st32(lane_base + 384 + 32 * c4, z);
-    }
-    tmem_wait_st();
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 64);
+    int hc = 0, tl = 0;
     bool ok = true;
-    for (int u = 0; u < sc.nH; ++u) {
-      int g, p, c;
-      sc.high(u, &g, &p, &c);
-      const int b = u % nbuf;
-      // warp-uniform outcome: the TMEM loads below are .sync.aligned
-      ok = __all_sync(0xffffffffu, mbar_wait(&sh->acc_full[b], (uint32_t)(u / nbuf) & 1u, cta_err));
-      if (!ok) break;
-      tc_fence_after();
-      const int shift = 8 * (G_EXACT - 1 - g);
-#pragma unroll 1
-      for (int c4 = 0; c4 < 4; ++c4) {
-        uint32_t acc[32], lo[32], hi[32];
-        tmem_ld32(lane_base + (uint32_t)(b * TILE + 32 * c4), acc);
-        tmem_ld32(lane_base + 256 + 32 * c4, lo);
-        tmem_ld32(lane_base + 384 + 32 * c4, hi);
-        tmem_wait_ld();
-        if (c4 == 3) {  // the accumulator buffer is free once all of it is in registers
-          tc_fence_before();
-          mbar_arrive(&sh->acc_empty[b]);
-        }
+    for (int t = cid; t < ntiles && ok; t += ncl, ++tl) {
+      long long R[64];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const long long a = (long long)__float2int_rn(__uint_as_float(acc[i])) << shift;
-          unsigned long long r = ((unsigned long long)hi[i] << 32) | lo[i];
-          r += (unsigned long long)a;
-          lo[i] = (uint32_t)r;
-          hi[i] = (uint32_t)(r >> 32);
+      for (int i = 0; i < 64; ++i) R[i] = 0;
+      for (int g = 0; g < gh && ok; ++g) {
+        const int shift = 8 * (G_EXACT - 1 - g);
+        for (int n = (g + 1) * nch; n > 0; --n) {  // the items of group g: (g + 1) pairs x nch chunks
+          const int b = hc & 1;
+          ok = __all_sync(0xffffffffu, mbar_wait(&sh->acc_full[b], (uint32_t)(hc >> 1) & 1u, cta_err));
+          if (!ok) break;
+          tc_fence_after();
+#pragma unroll
+          for (int pc = 0; pc < 4; ++pc) {
+            uint32_t a[16];
+            tmem_ld16(lane_base + (uint32_t)(b * TILE + 16 * pc), a);
+            tmem_wait_ld();
+            if (pc == 3) {  // the whole buffer is in registers: hand it back to the MMAs
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive_cluster(peer_addr(&sh->acc_empty[b], 0));
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              R[16 * pc + i] += (long long)__float2int_rn(__uint_as_float(a[i])) << shift;
+          }
+          ++hc;
         }
-        tmem_st32(lane_base + 256 + 32 * c4, lo);
-        tmem_st32(lane_base + 384 + 32 * c4, hi);
       }
-      tmem_wait_st();
-    }
-    if (ok && sc.nL > 0)
-      ok = __all_sync(0xffffffffu, mbar_wait(&sh->low_done, 0u, cta_err));
-    if (ok) tc_fence_after();
-    if (__all_sync(0xffffffffu, ok && !*cta_err)) {
-      const int64_t row = m0 + row_in_tile;
+      if (!ok) break;
+      const int lb = tl & 1;
+      if (nL > 0) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&sh->low_full[lb], (uint32_t)(tl >> 1) & 1u, cta_err));
+        if (!ok) break;
+        tc_fence_after();
+      }
+      int mp, nt;
+      pair_tile(t, tiles_m, tiles_n, &mp, &nt);
+      const int64_t row = (int64_t)mp * 2 * TILE + (int64_t)rank * TILE + row_in_tile;
+      const int64_t col0 = (int64_t)nt * TILE + half * 64;
       const int er = (row < N) ? erow[row] : 0;
       const double pii = (row < N) ? pdiag[row] : 0.0;
-#pragma unroll 1
-      for (int c4 = 0; c4 < 4; ++c4) {
-        uint32_t lo[32], hi[32], lw[32];
-        tmem_ld32(lane_base + 256 + 32 * c4, lo);
-        tmem_ld32(lane_base + 384 + 32 * c4, hi);
-        if (sc.nL > 0) tmem_ld32(lane_base + (uint32_t)TILE + 32 * c4, lw);
-        tmem_wait_ld();
+#pragma unroll
+      for (int pc = 0; pc < 8; ++pc) {
+        uint32_t lw[8];
+        if (nL > 0) {
+          tmem_ld8(lane_base + 256u + (uint32_t)(lb * TILE + 8 * pc), lw);
+          tmem_wait_ld();
+          if (pc == 7) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(peer_addr(&sh->low_empty[lb], 0));
+          }
+        }
         if (row < N) {
-#pragma unroll 4
-          for (int i = 0; i < 32; ++i) {
-            const int64_t col = n0 + 32 * c4 + i;
-            if (col >= N) break;
-            const long long r = (long long)(((unsigned long long)hi[i] << 32) | lo[i]);
-            double v = (double)r;  // rounds to 53 bits when |R| >= 2^53
-            if (sc.nL > 0) v = fma((double)__uint_as_float(lw[i]), 0.00390625, v);
-            const int ex = er + fcol[col] - 16 - 8 * (G_EXACT - 1);
-            const double scl = (ex >= -1022 && ex <= 1023) ? __longlong_as_double((long long)(ex + 1023) << 52)
-                                                          : ldexp(1.0, ex);
-            // the deflated diagonals: + P_ii Q_ij + P_ij Q_jj - [i = j] P_ii Q_jj
-            const double qjj = qdiag[col];
-            double d = fma(pii, __ldg(Q + row * N + col), (v * scl));
-            d = fma(__ldg(P + row * N + col), qjj, d);
-            if (row == col) d = fma(-pii, qjj, d);
-            apply_epilogue(e, N, row, col, alpha * d);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int64_t col = col0 + 8 * pc + i;
+            if (col < N) {
+              double v = (double)R[8 * pc + i];  // rounds to 53 bits when |R| >= 2^53
+              if (nL > 0) v = fma((double)__uint_as_float(lw[i]), 0.00390625, v);
+              const int ex = er + fcol[col] - 16 - 8 * (G_EXACT - 1);
+              const double scl = (ex >= -1022 && ex <= 1023) ? __longlong_as_double((long long)(ex + 1023) << 52)
+                                                            : ldexp(1.0, ex);
+              // the deflated diagonals: + P_ii Q_ij + P_ij Q_jj - [i = j] P_ii Q_jj
+              const double qjj = qdiag[col];
+              double d = fma(pii, __ldg(Q + row * N + col), (v * scl));
+              d = fma(__ldg(P + row * N + col), qjj, d);
+              if (row == col) d = fma(-pii, qjj, d);
+              apply_epilogue(e, N, row, col, alpha * d);
+            }
           }
         }
       }
@@ -591,10 +682,11 @@ k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();  // neither CTA leaves while the other may still reach its memory
   if (threadIdx.x == 0 && sh->err) atomicOr(status, STATUS_TIMEOUT);
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
 }
 
@@ -617,12 +709,12 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, void* base, int64_t Rp, int64_t Kp, int k) {
+bool make_map(CUtensorMap* m, void* base, int64_t Rp, int64_t Kp, int k, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)Rp, (cuuint64_t)k};
   const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)(Rp * Kp * 2)};
-  const cuuint32_t box[3] = {KSTEP, TILE, 1};
+  const cuuint32_t box[3] = {KSTEP, (cuuint32_t)box_rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -630,8 +722,6 @@ bool make_map(CUtensorMap* m, void* base, int64_t Rp, int64_t Kp, int k) {
 }
 
 int64_t padded(int64_t N) { return (N + TILE - 1) / TILE * TILE; }
-
-constexpr size_t SMEM_BYTES = 2 * STAGES * STAGE_BYTES + sizeof(Shared) + 1024;
 
 template <int K>
 cudaError_t split_both(const double* P, const double* Q, int64_t N, int64_t Rp, uint16_t* Ps, uint16_t* Qs,
@@ -708,19 +798,70 @@ cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices,
   }
 }
 
+namespace {
+// Clusters of two k_ozaki_pair CTAs that fit on the device at once (cached per device).
+int pair_clusters() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (cached[dev] > 0) return cached[dev];
+  if (cudaFuncSetAttribute(k_ozaki_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PAIR_SMEM_BYTES) !=
+      cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2 * 1024, 1, 1);
+  cfg.blockDim = dim3(P_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = PAIR_SMEM_BYTES;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_ozaki_pair, &cfg) != cudaSuccess || n <= 0) {
+    // clusters are independent: any count is correct, the SM count / 2 is the natural one
+    cudaGetLastError();
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) n = sms / 2;
+  }
+  cached[dev] = n;
+  return n;
+}
+
+cudaError_t launch_pair(const OzLayout& L, const double* P, const double* Q, int64_t N, double alpha,
+                        const Epilogue& e, int slices, unsigned int* flag, cudaStream_t st) {
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, L.Ps, L.Rp, L.Rp, slices, TILE) || !make_map(&tb, L.Qs, L.Rp, L.Rp, slices, TILE / 2))
+    return cudaErrorNotSupported;
+  const int ncl_max = pair_clusters();
+  if (ncl_max <= 0) return cudaErrorNotSupported;
+  const int tiles_m = (int)((L.Rp + 2 * TILE - 1) / (2 * TILE));
+  const int tiles_n = (int)(L.Rp / TILE);
+  const int ncl = std::min(ncl_max, tiles_m * tiles_n);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
+  cfg.blockDim = dim3(P_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = PAIR_SMEM_BYTES;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_ozaki_pair, ta, tb, (const int*)L.erow, (const int*)L.fcol, P, Q,
+                            (const double*)L.pdiag, (const double*)L.qdiag, N, alpha, slices, (int)(L.Rp / KSTEP),
+                            tiles_m, tiles_n, e, flag);
+}
+}  // namespace
+
 cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e, int slices,
                           void* work, unsigned int* flag, cudaStream_t st) {
   if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
-  const OzLayout L = layout(work, N, slices);
-  CUtensorMap ta, tb;
-  if (!make_map(&ta, L.Ps, L.Rp, L.Rp, slices) || !make_map(&tb, L.Qs, L.Rp, L.Rp, slices))
-    return cudaErrorNotSupported;
-  cudaError_t err = cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-  if (err != cudaSuccess) return err;
-  const dim3 grid((unsigned)(L.Rp / TILE), (unsigned)(L.Rp / TILE));
-  k_ozaki_gemm<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ta, tb, L.erow, L.fcol, P, Q, L.pdiag, L.qdiag, N, alpha,
-                                                      slices, (int)(L.Rp / KSTEP), e, flag);
-  return cudaGetLastError();
+  return launch_pair(layout(work, N, slices), P, Q, N, alpha, e, slices, flag, st);
 }
 
 }  // namespace bbc
