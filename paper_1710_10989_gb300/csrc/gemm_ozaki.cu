@@ -87,22 +87,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait. Returns false when the CTA already failed or the wait expired
-// (then the CTA-wide flag is raised so that every other role stops too).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* cta_err) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63) == 0) {
-      if (*cta_err) return false;
-      if (globaltimer() - t0 > TIMEOUT_NS) {
-        *cta_err = 1;
-        return false;
-      }
-    }
-  }
-}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -343,20 +327,43 @@ __device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* bar, uint32_t parity)
       : "memory");
   return ok != 0;
 }
-// Bounded wait with cluster-scope acquire (the barrier may be completed from the peer CTA).
-__device__ __forceinline__ bool mbar_wait_cl(uint64_t* bar, uint32_t parity, volatile int* cta_err) {
-  if (mbar_try_wait_cl(bar, parity)) return true;
+// Bounded wait by a whole warp: all 32 lanes call it together and get the same
+// answer. The roles that issue TMA copies and MMAs run as whole warps with one
+// elected lane issuing: measured on GB300, a loop run by a single lane (its 31
+// siblings parked) pays ~250 cycles per mbarrier wait, enough to idle the tensor
+// pipe between 4-MMA stages; the converged warp pays almost nothing.
+__device__ __noinline__ bool mbar_wait_warp_slow(uint64_t* bar, uint32_t parity, volatile int* cta_err,
+                                                 bool cluster_scope) {
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait_cl(bar, parity)) return true;
+    const bool done = cluster_scope ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity);
+    if (__any_sync(0xffffffffu, done)) return true;  // a completed phase stays completed
     if ((it & 63) == 0) {
-      if (*cta_err) return false;
-      if (globaltimer() - t0 > TIMEOUT_NS) {
-        *cta_err = 1;
+      int stop = 0;
+      if (*cta_err) stop = 1;
+      else if (globaltimer() - t0 > TIMEOUT_NS) stop = 2;
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      if (stop) {
+        if (stop == 2 && (threadIdx.x & 31) == 0) *cta_err = 1;
         return false;
       }
     }
   }
+}
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* cta_err) {
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+  return mbar_wait_warp_slow(bar, parity, cta_err, false);
+}
+__device__ __forceinline__ bool mbar_wait_warp_cl(uint64_t* bar, uint32_t parity, volatile int* cta_err) {
+  if (__all_sync(0xffffffffu, mbar_try_wait_cl(bar, parity))) return true;
+  return mbar_wait_warp_slow(bar, parity, cta_err, true);
+}
+// One lane of the (converged) warp, chosen by the hardware.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred;
+  asm volatile("{\n .reg .pred P;\n .reg .b32 R;\n elect.sync R|P, 0xffffffff;\n selp.u32 %0, 1, 0, P;\n}\n"
+               : "=r"(pred));
+  return pred != 0;
 }
 // TMA tile load into this CTA's shared memory, completing bytes on a barrier that may
 // belong to the peer CTA (cluster address).
@@ -495,42 +502,48 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   const uint32_t tmem = sh->tmem_base;
 
   if (warp == 0) {
-    // ---------------- TMA producer (both CTAs)
-    if (lane == 0) {
+    // ---------------- TMA producer (both CTAs; the whole warp walks the schedule)
+    const bool leader_lane = elect_one();
+    if (leader_lane) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
-      int s = 0;
-      uint32_t ph = 0;
-      bool ok = true;
-      for (int t = cid; t < ntiles && ok; t += ncl) {
-        int mp, nt;
-        pair_tile(t, tiles_m, tiles_n, &mp, &nt);
-        const int arow = mp * 2 * TILE + (int)rank * TILE;
-        const int brow = nt * TILE + (int)rank * (TILE / 2);
-        ItemCursor cur(nslices, nch);
-        for (int idx = 0; idx < nunits && ok; ++idx, cur.advance()) {
-          const int ks1 = min(nksteps, (cur.c + 1) * CHUNK_STEPS);
-          for (int ks = cur.c * CHUNK_STEPS; ks < ks1; ++ks) {
-            if (!mbar_wait(&sh->empty[s], ph ^ 1u, cta_err)) { ok = false; break; }
+    }
+    int s = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int t = cid; t < ntiles && ok; t += ncl) {
+      int mp, nt;
+      pair_tile(t, tiles_m, tiles_n, &mp, &nt);
+      const int arow = mp * 2 * TILE + (int)rank * TILE;
+      const int brow = nt * TILE + (int)rank * (TILE / 2);
+      ItemCursor cur(nslices, nch);
+      for (int idx = 0; idx < nunits && ok; ++idx, cur.advance()) {
+        const int ks1 = min(nksteps, (cur.c + 1) * CHUNK_STEPS);
+        for (int ks = cur.c * CHUNK_STEPS; ks < ks1; ++ks) {
+          if (!mbar_wait_warp(&sh->empty[s], ph ^ 1u, cta_err)) { ok = false; break; }
+          if (leader_lane) {
             if (rank == 0) mbar_arrive_expect_tx(&sh->full[s], 2 * P_STAGE_BYTES);
             const uint32_t fb = peer_addr(&sh->full[s], 0);
             tma_load_3d_pair(smA + s * P_A_BYTES, &tmA, fb, ks * KSTEP, arow, cur.p);
             tma_load_3d_pair(smB + s * P_B_BYTES, &tmB, fb, ks * KSTEP, brow, cur.g - cur.p);
-            if (++s == P_STAGES) { s = 0; ph ^= 1u; }
           }
-        }
-      }
-      if (!ok) {  // give copies already issued time to land (error path only)
-        const unsigned long long t0 = globaltimer();
-        while (globaltimer() - t0 < 1000000ull) {
+          __syncwarp();
+          if (++s == P_STAGES) { s = 0; ph ^= 1u; }
         }
       }
     }
+    if (!ok) {  // give copies already issued time to land (error path only)
+      const unsigned long long t0 = globaltimer();
+      while (globaltimer() - t0 < 1000000ull) {
+      }
+    }
   } else if (warp == 1) {
-    // ---------------- MMA issuer (even CTA). The first K step of each item is
-    // peeled off: it alone carries the accumulate / scale choice, so the steady
-    // loop is four unconditional MMAs and a commit.
-    if (rank == 0 && lane == 0) {
+    // ---------------- MMA issuer (the whole warp of the even CTA walks the schedule,
+    // one elected lane issues). The first K step of each item is peeled off: it
+    // alone carries the accumulate / scale choice, so the steady loop is four
+    // unconditional MMAs and a commit.
+    if (rank == 0) {
+      const bool issuer = elect_one();
       const uint64_t dA0 = smem_desc(smem_u32(smA)), dB0 = smem_desc(smem_u32(smB));
       int s = 0;
       uint32_t ph = 0;
@@ -539,7 +552,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       for (int t = cid; t < ntiles && ok; t += ncl, ++tl) {
         const int lb = tl & 1;
         if (nL > 0) {
-          if (!mbar_wait_cl(&sh->low_empty[lb], ((uint32_t)(tl >> 1) & 1u) ^ 1u, cta_err)) { ok = false; break; }
+          if (!mbar_wait_warp_cl(&sh->low_empty[lb], ((uint32_t)(tl >> 1) & 1u) ^ 1u, cta_err)) { ok = false; break; }
           tc_fence_after();
         }
         ItemCursor cur(nslices, nch);
@@ -551,15 +564,14 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             kind0 = (idx == 0) ? 0 : ((cur.p == 0 && cur.c == 0) ? 2 : 1);
           } else {
             b = hc & 1;
-            if (!mbar_wait_cl(&sh->acc_empty[b], ((uint32_t)(hc >> 1) & 1u) ^ 1u, cta_err)) { ok = false; break; }
-            tc_fence_after();
+            if (!mbar_wait_warp_cl(&sh->acc_empty[b], ((uint32_t)(hc >> 1) & 1u) ^ 1u, cta_err)) { ok = false; break; }
+            tc_fence_after();  // the drains' TMEM reads of this buffer come before these MMAs
             d_tmem = tmem + (uint32_t)(b * TILE);
             kind0 = 0;
           }
           const int ks1 = min(nksteps, (cur.c + 1) * CHUNK_STEPS);
-          if (!mbar_wait_cl(&sh->full[s], ph, cta_err)) { ok = false; break; }
-          tc_fence_after();
-          {
+          if (!mbar_wait_warp_cl(&sh->full[s], ph, cta_err)) { ok = false; break; }
+          if (issuer) {
             const uint64_t da = dA0 + (uint64_t)(s * (P_A_BYTES >> 4)), db = dB0 + (uint64_t)(s * (P_B_BYTES >> 4));
             if (kind0 == 2) mma_pair_scaled(d_tmem, da, db);
             else mma_pair(d_tmem, da, db, (uint32_t)kind0);
@@ -567,29 +579,34 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             mma_pair(d_tmem, da + 4, db + 4, 1u);
             mma_pair(d_tmem, da + 6, db + 6, 1u);
             commit_pair(&sh->empty[s]);
-            if (++s == P_STAGES) { s = 0; ph ^= 1u; }
           }
+          __syncwarp();
+          if (++s == P_STAGES) { s = 0; ph ^= 1u; }
           for (int ks = cur.c * CHUNK_STEPS + 1; ks < ks1; ++ks) {
-            if (!mbar_wait_cl(&sh->full[s], ph, cta_err)) { ok = false; break; }
-            tc_fence_after();
-            const uint64_t da = dA0 + (uint64_t)(s * (P_A_BYTES >> 4)), db = dB0 + (uint64_t)(s * (P_B_BYTES >> 4));
-            mma_pair(d_tmem, da, db, 1u);
-            mma_pair(d_tmem, da + 2, db + 2, 1u);
-            mma_pair(d_tmem, da + 4, db + 4, 1u);
-            mma_pair(d_tmem, da + 6, db + 6, 1u);
-            commit_pair(&sh->empty[s]);
+            if (!mbar_wait_warp_cl(&sh->full[s], ph, cta_err)) { ok = false; break; }
+            if (issuer) {
+              const uint64_t da = dA0 + (uint64_t)(s * (P_A_BYTES >> 4)), db = dB0 + (uint64_t)(s * (P_B_BYTES >> 4));
+              mma_pair(d_tmem, da, db, 1u);
+              mma_pair(d_tmem, da + 2, db + 2, 1u);
+              mma_pair(d_tmem, da + 4, db + 4, 1u);
+              mma_pair(d_tmem, da + 6, db + 6, 1u);
+              commit_pair(&sh->empty[s]);
+            }
+            __syncwarp();
             if (++s == P_STAGES) { s = 0; ph ^= 1u; }
           }
           if (!ok) break;
           if (!cur.low) {
-            commit_pair(&sh->acc_full[b]);
+            if (issuer) commit_pair(&sh->acc_full[b]);
             ++hc;
           } else if (idx == nL - 1) {
-            commit_pair(&sh->low_full[lb]);
+            if (issuer) commit_pair(&sh->low_full[lb]);
           }
+          __syncwarp();
         }
       }
-      commit_pair(&sh->mma_done);
+      if (issuer) commit_pair(&sh->mma_done);
+      __syncwarp();
     }
     if (lane == 0) {  // no MMA may still write either CTA's TMEM when it is freed
       const unsigned long long t0 = globaltimer();
@@ -612,7 +629,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         const int shift = 8 * (G_EXACT - 1 - g);
         for (int n = (g + 1) * nch; n > 0; --n) {  // the items of group g: (g + 1) pairs x nch chunks
           const int b = hc & 1;
-          ok = __all_sync(0xffffffffu, mbar_wait(&sh->acc_full[b], (uint32_t)(hc >> 1) & 1u, cta_err));
+          ok = mbar_wait_warp(&sh->acc_full[b], (uint32_t)(hc >> 1) & 1u, cta_err);
           if (!ok) break;
           tc_fence_after();
 #pragma unroll
@@ -635,7 +652,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       if (!ok) break;
       const int lb = tl & 1;
       if (nL > 0) {
-        ok = __all_sync(0xffffffffu, mbar_wait(&sh->low_full[lb], (uint32_t)(tl >> 1) & 1u, cta_err));
+        ok = mbar_wait_warp(&sh->low_full[lb], (uint32_t)(tl >> 1) & 1u, cta_err);
         if (!ok) break;
         tc_fence_after();
       }
