@@ -39,7 +39,7 @@ PI = {1: 0, 2: 1, 4: 2, 8: 3, 12: 4, 18: 5}
 # DRAM traffic per launch of the dominant kernels from one ncu capture each (profiles/),
 # valid only while the kernel source is the one that was captured.
 NCU_TRAFFIC = {
-    "gemm_ozaki.cu": ("417c891e64454be19866565803975cf69f3356aafd1b2c909da2896594987471", 4096, 7.753078e9 + 0.168836352e9),
+    "gemm_ozaki.cu": ("2ba53ed868d103c31deaee82924d1eaf310fcd1c975b60e3987881e56a4fcefa", 4096, 4.628172e9 + 0.152834e9),
     "gemm_f64.cu": ("c1965ca226ec4ee76ccab7620c3105f1abf10d5ba9ea3047e862e9126f56b6a5", 4096, 3.733487e9 + 0.133997312e9),
     "batched.cu": ("3f86258f8371369fa84e7c05b2e817d5299e265d45b46618f23f4add0ce661b4", 512, 3.662761e9 + 1.816421e9),
 }
@@ -355,10 +355,8 @@ def run_dense(args, torch, dist, api, rank, world, local):
         peak = pk.get("bf16_tflops", 1899.1)
         roof = {"bound": "tensor", "achieved": executed, "peak": peak, "unit": "TFLOP/s",
                 "frac": executed / peak,
-                "traffic": (ncu_traffic("gemm_ozaki.cu", n) * pairs / 28) if (ncu_traffic("gemm_ozaki.cu", n)
-                                                                               and args.slices in (6, 7)) else None,
-                "traffic_note": "ncu capture at 7 slices; slice-plane traffic scales with slice pairs" if
-                                args.slices == 6 else None,
+                "traffic": ncu_traffic("gemm_ozaki.cu", n) if args.slices == 6 else None,
+                "traffic_note": "ncu capture of one product at 6 slices (profiles/k_ozaki_pair_dense4096.md)",
                 "kernel": f"k_ozaki_pair ({args.slices} BF16 slices: {pairs} slice products per FP64 product)",
                 "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS)" if "bf16_tflops" in pk
                                 else "fallback 1.9 PFLOP/s bf16"),
