@@ -324,20 +324,19 @@ def run_dense(args, torch, dist, api, rank, world, local):
         hA = [torch.from_numpy(A).pin_memory() for A in mats]
         hO = [torch.empty_like(a).pin_memory() for a in hA]
         e2e_steps = max(1, min(args.steps, 2))
-        for a, o in zip(hA, hO):
-            h.expm_host(a, o, 0.0, flags, stream)
+        # the public host-buffer call: copies of neighbouring matrices overlap the computation
+        h.expm_host_many(hA, hO, 0.0, flags, stream)
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            for a, o in zip(hA, hO):
-                h.expm_host(a, o, 0.0, flags, stream)
+            h.expm_host_many(hA, hO, 0.0, flags, stream)
         te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e = {"value": len(mats) * e2e_steps * world / float(te.item()), "unit": "expm/s",
                "h2d_bytes_per_step": len(mats) * n * n * 8, "d2h_bytes_per_step": len(mats) * n * n * 8,
-               "steps": e2e_steps}
+               "steps": e2e_steps, "api": "bbc_expm_host_many (pinned host buffers, pipelined copies)"}
 
     pk = peaks()
     flops_per_product = 2.0 * n ** 3

@@ -142,6 +142,20 @@ int bbc_expm_fixed(bbc_handle h, const double* dA, int64_t N, double* dOut, int 
 int bbc_expm_host(bbc_handle h, const double* hA, int64_t N, double* hOut, double tol, int flags,
                   void* stream, bbc_info* info);
 
+/* exp(A_i) for `count` matrices in HOST memory (pinned memory recommended),
+ * pipelined: while matrix i is evaluated on `stream` (as by bbc_expm), matrix
+ * i + 1 is copied to the device and matrix i - 1 back to the host on two copy
+ * streams the handle owns, so the copies hide behind the computation.
+ *  hA, hOut  host arrays of `count` host pointers; A_i and Out_i are N_i x N_i
+ *            row-major binary64 and must not overlap.
+ *  Ns        host array of the `count` sizes (N_i >= 1; they may differ).
+ *  info      host array of `count` bbc_info, or NULL.
+ * The device staging (four max N_i x max N_i buffers) lives in the handle and
+ * grows on demand. Stops at the first matrix that fails and returns its status
+ * (earlier results are in hOut); returns after every started copy has finished. */
+int bbc_expm_host_many(bbc_handle h, const double* const* hA, const int64_t* Ns, int64_t count,
+                       double* const* hOut, double tol, int flags, void* stream, bbc_info* info);
+
 /* Element types of bbc_expm_batched. */
 #define BBC_DTYPE_F64 0
 #define BBC_DTYPE_F32 1

@@ -62,6 +62,7 @@ _SIGS = {
     "bbc_expm": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_fixed": [_vp, _vp, _i64, _vp, _int, _int, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_host": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
+    "bbc_expm_host_many": [_vp, _vp, _vp, _i64, _vp, _dbl, _int, _vp, _vp],
     "bbc_batch_reserve": [_vp, _i64, _int],
     "bbc_batch_order": [ctypes.POINTER(ctypes.c_int64), _i64, ctypes.POINTER(ctypes.c_int64)],
     "bbc_expm_batched": [_vp, _vp, _vp, _i64, _vp, _int, _dbl, _int, _vp, _vp],
@@ -250,6 +251,25 @@ class Handle:
         info = Info()
         _check(_lib.bbc_expm_host(self._h, pa, n, po, tol, flags, _stream(stream), ctypes.byref(info)))
         return info
+
+
+    def expm_host_many(self, As, outs, tol: float = 0.0, flags: int = 0, stream=None) -> list:
+        """exp of each host matrix in `As` into `outs` (host tensors/arrays, float64,
+        C-contiguous, square), with the copies pipelined behind the computation."""
+        k = len(As)
+        if len(outs) != k:
+            raise ValueError("As and outs differ in length")
+        pa = (ctypes.c_void_p * max(k, 1))()
+        po = (ctypes.c_void_p * max(k, 1))()
+        ns = (ctypes.c_int64 * max(k, 1))()
+        for i, (a, o) in enumerate(zip(As, outs)):
+            pa[i], ns[i] = _host_ptr(a)
+            po[i], n2 = _host_ptr(o)
+            if n2 != ns[i]:
+                raise ValueError("output size differs from input size")
+        infos = (Info * max(k, 1))()
+        _check(_lib.bbc_expm_host_many(self._h, pa, ns, k, po, tol, flags, _stream(stream), infos))
+        return [infos[i] for i in range(k)]
 
 
 def batch_order(ns) -> list[int]:

@@ -40,7 +40,11 @@ struct bbc_handle_s {
   bool batch_split = false;       // reservation includes the split-precision scratch
   void* batch_work = nullptr;
   int64_t io_n = 0;               // N the host-call staging buffers are sized for
-  double* io = nullptr;           // 2 * N * N doubles: device copies of hA and hOut
+  double* io = nullptr;           // 4 * N * N doubles: device copies of two inputs and two outputs
+  cudaStream_t copy_in = nullptr;   // host-call pipeline: host -> device copies
+  cudaStream_t copy_out = nullptr;  // host-call pipeline: device -> host copies
+  cudaEvent_t ev_in[2] = {nullptr, nullptr};
+  cudaEvent_t ev_out[2] = {nullptr, nullptr};
   std::mutex mu;
 };
 
@@ -499,6 +503,12 @@ int bbc_destroy(bbc_handle h) {
   cudaFree(h->ozaki);
   cudaFree(h->io);
   cudaFree(h->batch_work);
+  if (h->copy_in) cudaStreamDestroy(h->copy_in);
+  if (h->copy_out) cudaStreamDestroy(h->copy_out);
+  for (int k = 0; k < 2; ++k) {
+    if (h->ev_in[k]) cudaEventDestroy(h->ev_in[k]);
+    if (h->ev_out[k]) cudaEventDestroy(h->ev_out[k]);
+  }
   for (auto& r : h->recs) { h->pool.push_back(r.a); h->pool.push_back(r.b); }
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   if (h->hstage) cudaFreeHost(h->hstage);
@@ -692,31 +702,93 @@ int bbc_expm(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol
   return BBC_OK;
 }
 
+namespace {
+// Device staging for the host-buffer calls: four N x N slots (two inputs, two
+// outputs), grown on demand. Caller holds no lock.
+int ensure_io(bbc_handle h, int64_t N) {
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (N <= h->io_n) return BBC_OK;
+  if (h->io) BBC_CUDA(cudaFree(h->io));
+  h->io = nullptr;
+  h->io_n = 0;
+  BBC_CUDA(cudaMalloc(&h->io, (size_t)4 * N * N * sizeof(double)));
+  h->io_n = N;
+  return BBC_OK;
+}
+}  // namespace
+
 int bbc_expm_host(bbc_handle h, const double* hA, int64_t N, double* hOut, double tol, int flags,
                   void* stream, bbc_info* info) {
   int rc = begin(h);
   if (rc) return rc;
   if (!hA || !hOut || N <= 0) return fail(BBC_INVALID_ARG, "bad expm arguments");
   if (overlaps(hA, hOut, N)) return fail(BBC_INVALID_ARG, "output aliases the input");
-  {
-    std::lock_guard<std::mutex> lk(h->mu);
-    if (N > h->io_n) {
-      if (h->io) BBC_CUDA(cudaFree(h->io));
-      h->io = nullptr;
-      h->io_n = 0;
-      BBC_CUDA(cudaMalloc(&h->io, (size_t)2 * N * N * sizeof(double)));
-      h->io_n = N;
-    }
-  }
+  if ((rc = ensure_io(h, N))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)N * N * sizeof(double);
   double* dA = h->io;
-  double* dOut = h->io + (size_t)N * N;
+  double* dOut = h->io + (size_t)2 * h->io_n * h->io_n;
   BBC_CUDA(cudaMemcpyAsync(dA, hA, bytes, cudaMemcpyHostToDevice, st));
   rc = bbc_expm(h, dA, N, dOut, tol, flags, stream, info);
   if (rc) return rc;
   BBC_CUDA(cudaMemcpyAsync(hOut, dOut, bytes, cudaMemcpyDeviceToHost, st));
   BBC_CUDA(cudaStreamSynchronize(st));
+  return BBC_OK;
+}
+
+int bbc_expm_host_many(bbc_handle h, const double* const* hA, const int64_t* Ns, int64_t count,
+                       double* const* hOut, double tol, int flags, void* stream, bbc_info* info) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!hA || !Ns || !hOut || count < 0) return fail(BBC_INVALID_ARG, "bad expm_host_many arguments");
+  int64_t nmax = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    if (!hA[i] || !hOut[i] || Ns[i] <= 0) return fail(BBC_INVALID_ARG, "bad matrix in expm_host_many");
+    if (overlaps(hA[i], hOut[i], Ns[i])) return fail(BBC_INVALID_ARG, "an output aliases its input");
+    nmax = std::max(nmax, Ns[i]);
+  }
+  if (count == 0) return BBC_OK;
+  if ((rc = ensure_io(h, nmax))) return rc;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (!h->copy_in) {
+      BBC_CUDA(cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking));
+      BBC_CUDA(cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking));
+      for (int k = 0; k < 2; ++k) {
+        BBC_CUDA(cudaEventCreateWithFlags(&h->ev_in[k], cudaEventDisableTiming));
+        BBC_CUDA(cudaEventCreateWithFlags(&h->ev_out[k], cudaEventDisableTiming));
+      }
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t slot = (size_t)h->io_n * h->io_n;
+  double* din[2] = {h->io, h->io + slot};
+  double* dout[2] = {h->io + 2 * slot, h->io + 3 * slot};
+  // Matrix i computes on `stream` (bbc_expm returns once it is done) while the
+  // copy streams bring in matrix i + 1 and take out matrix i - 1.
+  BBC_CUDA(cudaMemcpyAsync(din[0], hA[0], (size_t)Ns[0] * Ns[0] * sizeof(double), cudaMemcpyHostToDevice,
+                           h->copy_in));
+  BBC_CUDA(cudaEventRecord(h->ev_in[0], h->copy_in));
+  int first_err = BBC_OK;
+  for (int64_t i = 0; i < count && !first_err; ++i) {
+    const int b = (int)(i & 1);
+    if (i + 1 < count) {  // slot (i+1)&1 was last read by matrix i-1, which has finished
+      BBC_CUDA(cudaMemcpyAsync(din[b ^ 1], hA[i + 1], (size_t)Ns[i + 1] * Ns[i + 1] * sizeof(double),
+                               cudaMemcpyHostToDevice, h->copy_in));
+      BBC_CUDA(cudaEventRecord(h->ev_in[b ^ 1], h->copy_in));
+    }
+    BBC_CUDA(cudaStreamWaitEvent(st, h->ev_in[b], 0));
+    if (i >= 2) BBC_CUDA(cudaStreamWaitEvent(st, h->ev_out[b], 0));  // matrix i-2 has left dout[b]
+    first_err = bbc_expm(h, din[b], Ns[i], dout[b], tol, flags, stream, info ? info + i : nullptr);
+    if (first_err) break;
+    BBC_CUDA(cudaMemcpyAsync(hOut[i], dout[b], (size_t)Ns[i] * Ns[i] * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->copy_out));
+    BBC_CUDA(cudaEventRecord(h->ev_out[b], h->copy_out));
+  }
+  const std::string err = g_err;
+  BBC_CUDA(cudaStreamSynchronize(h->copy_in));
+  BBC_CUDA(cudaStreamSynchronize(h->copy_out));
+  if (first_err) return fail(first_err, err);
   return BBC_OK;
 }
 

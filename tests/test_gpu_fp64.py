@@ -120,6 +120,35 @@ def test_expm_host_buffers(h, api):
     assert rel_fro(out, want) < 1e-12
 
 
+def test_expm_host_many_pipelined(h, api):
+    """Uneven sizes and both precisions through the pipelined host call: every
+    result equals the single-matrix host call's bit for bit (same kernels, same
+    order), and the oracle within the dense tolerance."""
+    sizes = [150, 64, 257, 150, 33]
+    As = [W.gaussian(n, 40 + i, 0.5 + i) for i, n in enumerate(sizes)]
+    for flags in (api.PREC_FP64, api.PREC_OZAKI | api.ozaki_slices(7)):
+        outs = [np.empty_like(A) for A in As]
+        infos = h.expm_host_many(As, outs, 0.0, flags)
+        for A, out, info in zip(As, outs, infos):
+            ref = np.empty_like(A)
+            one = h.expm_host(A, ref, 0.0, flags)
+            assert (info.m, info.s, info.products) == (one.m, one.s, one.products)
+            assert np.array_equal(out, ref)
+            want, oi = O.expm(A, "new")
+            assert (info.m, info.s) == (oi.m, oi.s)
+            assert rel_fro(out, want) < 1e-12
+
+
+def test_expm_host_many_reports_failure(h, api):
+    As = [W.gaussian(40, 1, 1.0), np.full((40, 40), np.nan), W.gaussian(40, 2, 1.0)]
+    outs = [np.zeros_like(A) for A in As]
+    with pytest.raises(api.BBCError) as e:
+        h.expm_host_many(As, outs)
+    assert e.value.code == api.NONFINITE_INPUT
+    want, _ = O.expm(As[0], "new")
+    assert rel_fro(outs[0], want) < 1e-12   # the matrix before the failure is complete
+
+
 # ---- status codes -------------------------------------------------------------------------------
 
 def test_status_codes(h, api):
