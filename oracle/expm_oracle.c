@@ -601,3 +601,82 @@ int orc_expm(int64_t n, const double* A, double* out, int scheme, const double* 
     if (!isfinite(out[e])) { info->status = 3; return 3; }
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Upper triangular A (Section 5, after Al-Mohy and Higham): the diagonal     */
+/* and first superdiagonal of exp(2^-q A) are known in closed form, and the   */
+/* computed ones are replaced by them before every squaring and in the        */
+/* result. For the 2 x 2 block [[l1, t], [0, l2]] of 2^-q A,                  */
+/*   exp = [[e^l1, t (e^l2 - e^l1)/(l2 - l1)], [0, e^l2]],                    */
+/* the divided difference written as e^((l1+l2)/2) sinh(d)/d, d = (l2-l1)/2,  */
+/* which has no cancellation (and is e^l1 when l1 = l2).                      */
+/* ------------------------------------------------------------------------ */
+static double exp_superdiag(double l1, double l2, double t) {
+  const double d = 0.5 * (l2 - l1);
+  const double sinhc = (d == 0.0) ? 1.0 : sinh(d) / d;
+  if (g_mutation == 10) return t * exp(l1);                 /* planted: divided difference dropped */
+  return t * exp(0.5 * (l1 + l2)) * sinhc;
+}
+
+/* Overwrite diag and first superdiagonal of T with those of exp(2^-q A). */
+static void replace_exact(int64_t n, const double* A, int q, double* T) {
+  for (int64_t i = 0; i < n; ++i) T[i * n + i] = exp(ldexp(A[i * n + i], -q));
+  for (int64_t i = 0; i + 1 < n; ++i)
+    T[i * n + i + 1] = exp_superdiag(ldexp(A[i * n + i], -q), ldexp(A[(i + 1) * n + i + 1], -q),
+                                     ldexp(A[i * n + i + 1], -q));
+}
+
+/* 1 if every entry strictly below the diagonal is zero. */
+int orc_is_upper(int64_t n, const double* A) {
+  for (int64_t i = 1; i < n; ++i)
+    for (int64_t j = 0; j < i; ++j)
+      if (A[i * n + j] != 0.0) return 0;
+  return 1;
+}
+
+/* As orc_expm for an upper triangular A (status 1 otherwise), with the exact
+ * diagonal and superdiagonal put in after the polynomial and after every
+ * squaring. The products are the plain ones: their lower triangles come out
+ * exactly zero. */
+int orc_expm_upper(int64_t n, const double* A, double* out, int scheme, const double* theta,
+                   int m_force, int s_force, orc_info* info) {
+  orc_info loc;
+  if (info == NULL) info = &loc;
+  memset(info, 0, sizeof *info);
+  if (n <= 0 || A == NULL || out == NULL || !orc_is_upper(n, A)) { info->status = 1; return 1; }
+  const int64_t nn = n * n;
+  for (int64_t e = 0; e < nn; ++e)
+    if (!isfinite(A[e])) { info->status = 2; return 2; }
+  const long long p0 = g_products;
+  info->norm1 = orc_norm1(n, A);
+  int m, s;
+  if (m_force > 0 && s_force >= 0) {
+    m = m_force; s = s_force;
+  } else {
+    if (theta == NULL) { info->status = 1; return 1; }
+    const int rc = orc_select(info->norm1, scheme, theta, &m, &s);
+    if (rc) { info->status = rc; return rc; }
+  }
+  info->m = m;
+  info->s = s;
+  double* X = mat(n);
+  for (int64_t e = 0; e < nn; ++e) X[e] = ldexp(A[e], -s);
+  int rc;
+  if (scheme == ORC_NEW) rc = orc_taylor_new(n, X, m, out);
+  else if (scheme == ORC_PS) rc = orc_taylor_ps(n, X, m, out);
+  else rc = orc_pade(n, X, m, out);
+  free(X);
+  if (rc < 0) { info->status = 1; return 1; }
+  replace_exact(n, A, s, out);                                 /* T = exp(2^-s A) on the two diagonals */
+  double* tmp = mat(n);
+  for (int k = 1; k <= s; ++k) {                               /* T <- T^2, then exact diagonals of exp(2^(k-s) A) */
+    orc_gemm(n, out, out, tmp);
+    memcpy(out, tmp, (size_t)nn * sizeof(double));
+    if (!(g_mutation == 11 && k == s)) replace_exact(n, A, s - k, out);   /* planted (11): last one skipped */
+  }
+  free(tmp);
+  info->products = (int)(g_products - p0);
+  for (int64_t e = 0; e < nn; ++e)
+    if (!isfinite(out[e])) { info->status = 3; return 3; }
+  return 0;
+}

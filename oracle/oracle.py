@@ -49,6 +49,9 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(ctypes.c_int)]
         L.orc_expm.argtypes = [i64, dp, dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(_Info)]
+        L.orc_expm_upper.argtypes = [i64, dp, dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(_Info)]
+        L.orc_is_upper.argtypes = [i64, dp]
         L.orc_coeffs.argtypes = [ctypes.c_int, dp]
         L.orc_set_mutation.argtypes = [ctypes.c_int]
         L.orc_product_count.restype = ctypes.c_longlong
@@ -132,6 +135,24 @@ def expm(A, scheme: str = "new", u: float = 2.0 ** -53, m: int | None = None,
     mf = m if (m is not None and s is not None) else 0
     sf = s if (m is not None and s is not None) else -1
     lib().orc_expm(A.shape[0], _p(A), _p(out), SCHEMES[scheme], _p(th), mf, sf, ctypes.byref(info))
+    return out, Info(info.m, info.s, info.products, info.status, info.norm1)
+
+
+def expm_upper(A, scheme: str = "new", u: float = 2.0 ** -53, m: int | None = None,
+               s: int | None = None) -> tuple[np.ndarray, Info]:
+    """exp(A) for an upper triangular A, with the exact diagonal and first
+    superdiagonal of exp(2^-q A) put in after the polynomial and every squaring
+    (Section 5, concluding remarks). Raises ValueError when A is not upper
+    triangular."""
+    A = _sq(A)
+    if not lib().orc_is_upper(A.shape[0], _p(A)):
+        raise ValueError("matrix is not upper triangular")
+    out = np.empty_like(A)
+    th = theta_array(scheme, u)
+    info = _Info()
+    mf = m if (m is not None and s is not None) else 0
+    sf = s if (m is not None and s is not None) else -1
+    lib().orc_expm_upper(A.shape[0], _p(A), _p(out), SCHEMES[scheme], _p(th), mf, sf, ctypes.byref(info))
     return out, Info(info.m, info.s, info.products, info.status, info.norm1)
 
 

@@ -50,9 +50,24 @@ def _coefficient_pins() -> bool:
     return max(abs(float(p[k] * math.factorial(k)) - 1.0) for k in range(13)) < 1e-14
 
 
+def _triangular_pins() -> bool:
+    """exp([[a, b], [0, c]]) in closed form (divided difference of exp, evaluated
+    as e^a (e^(c-a) - 1)/(c - a) with expm1: no cancellation), and the diagonal
+    of exp of an upper triangular matrix, e^{a_ii}."""
+    for a, b, c in ((1.0, 1e4, 1.0 + 1e-7), (-3.0, 250.0, 2.5)):
+        E, _ = O.expm_upper(np.array([[a, b], [0.0, c]]))
+        sup = b * math.exp(a) * math.expm1(c - a) / (c - a)
+        if abs(E[0, 1] - sup) > 1e-14 * abs(sup) or E[0, 0] != math.exp(a) or E[1, 1] != math.exp(c):
+            return False
+    rng = np.random.default_rng(3)
+    A = np.triu(rng.standard_normal((12, 12))) * 4.0
+    E, _ = O.expm_upper(A)
+    return all(E[i, i] == math.exp(A[i, i]) for i in range(12))
+
+
 def all_pins_pass() -> bool:
     return (_taylor_pins() and _closed_form_pins() and _norm_and_selection_pins()
-            and _coefficient_pins())
+            and _coefficient_pins() and _triangular_pins())
 
 
 MUTATIONS = {
@@ -65,6 +80,8 @@ MUTATIONS = {
     7: "Pade numerator and denominator swapped",
     8: "one squaring too few",
     9: "infinity-norm instead of 1-norm",
+    10: "triangular path: superdiagonal without the divided difference of exp",
+    11: "triangular path: exact diagonals not put back after the last squaring",
 }
 
 
