@@ -56,6 +56,17 @@ typedef enum {
 #define BBC_SELECT_LEARNED 0x1000  /* network proposal, certified, else the paper's rule */
 #define BBC_SELECT_ALPHA 0x2000    /* cheapest (m, s) certified by ||A|| or alpha_2 (computes A^2, A^3) */
 #define BBC_SELECT_MASK 0x3000
+/* structure (bits 14-15). By default bbc_expm, bbc_expm_fixed and the host-buffer
+ * calls find out, in the 1-norm pass, whether A is upper triangular; if it is,
+ * every product runs on the triangles only (entry (i, j) sums k over [i, j]:
+ * about a sixth of the dense flops) and the computed diagonal and first
+ * superdiagonal are replaced by the exact ones of exp(2^-q A), after the
+ * polynomial and after every squaring (Section 5, concluding remarks: the
+ * diagonal of exp(A) is exp(a_ii), the superdiagonal a divided difference of
+ * exp). bbc_info.structure reports which path ran. The Pade comparator stays dense. */
+#define BBC_DENSE 0x4000   /* treat A as dense: no structure detection */
+#define BBC_UPPER 0x8000   /* bbc_gemm only: the caller guarantees P and Q are upper
+                              triangular; the product then sums only k in [i, j] */
 
 typedef struct bbc_handle_s* bbc_handle;
 
@@ -66,6 +77,7 @@ typedef struct {
   int selector;   /* 0 = theta rule, 1 = caller-fixed (m, s) */
   double norm1;   /* ||A||_1 as computed on the device */
   int status;     /* bbc_status of this evaluation */
+  int structure;  /* 0 dense, 1 upper triangular path */
 } bbc_info;
 
 /* Create a handle bound to CUDA device `device`; allocates its device state.
@@ -252,6 +264,11 @@ int bbc_profile_enable(bbc_handle h, int enable);
  * since bbc_profile_enable; waits for the recorded events. total_ms may be
  * NULL. Launches are counted whether or not timing is enabled. */
 int bbc_profile_read(bbc_handle h, int kind, int64_t* launches, double* total_ms);
+
+/* Algorithmic flops of one kernel class since bbc_profile_enable: for products
+ * (BBC_KERNEL_PRODUCT) 2 N^3 per dense product and N (N+1) (N+2) / 3 per
+ * product of upper triangular operands, whatever precision ran them. */
+int bbc_profile_flops(bbc_handle h, int kind, double* flops);
 
 /* Text of the last error on this thread ("" if none). */
 const char* bbc_last_error(void);

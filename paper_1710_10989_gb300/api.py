@@ -17,6 +17,7 @@ OK, INVALID_ARG, NONFINITE_INPUT, OVERFLOW, CUDA_ERROR, TIMEOUT, UNSUPPORTED = r
 SCHEME_NEW, SCHEME_PS, SCHEME_PADE26 = 0x0, 0x1, 0x2
 PREC_FP64, PREC_OZAKI = 0x00, 0x10
 SELECT_LEARNED, SELECT_ALPHA = 0x1000, 0x2000
+DENSE, UPPER = 0x4000, 0x8000
 DEGREES = (1, 2, 4, 8, 12, 18)
 U_DOUBLE = 2.0 ** -53
 U_SINGLE = 2.0 ** -24
@@ -34,7 +35,8 @@ class BBCError(RuntimeError):
 
 class Info(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("s", ctypes.c_int), ("products", ctypes.c_int),
-                ("selector", ctypes.c_int), ("norm1", ctypes.c_double), ("status", ctypes.c_int)]
+                ("selector", ctypes.c_int), ("norm1", ctypes.c_double), ("status", ctypes.c_int),
+                ("structure", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -77,6 +79,7 @@ _SIGS = {
     "bbc_selector_data_batched": [_vp, _vp, _vp, _i64, _int, _vp, _vp, _vp, _vp],
     "bbc_profile_enable": [_vp, _int],
     "bbc_profile_read": [_vp, _int, ctypes.POINTER(ctypes.c_int64), _dp],
+    "bbc_profile_flops": [_vp, _int, _dp],
 }
 KERNEL_PRODUCT, KERNEL_NORM, KERNEL_LINCOMB, KERNEL_SPLIT, KERNEL_BATCHED, KERNEL_ALL = 0, 1, 2, 3, 4, -1
 DTYPE_F64, DTYPE_F32 = 0, 1
@@ -181,6 +184,13 @@ class Handle:
         ms = ctypes.c_double()
         _check(_lib.bbc_profile_read(self._h, kind, ctypes.byref(n), ctypes.byref(ms)))
         return n.value, ms.value
+
+    def profile_flops(self, kind: int = KERNEL_ALL) -> float:
+        """Algorithmic flops of a kernel class since profile_enable (products: 2 N^3
+        dense, N (N+1) (N+2) / 3 triangular)."""
+        f = ctypes.c_double()
+        _check(_lib.bbc_profile_flops(self._h, kind, ctypes.byref(f)))
+        return f.value
 
     def batch_set_selector(self, net: "MLP", S: int, mu, sd) -> None:
         mu_a = (ctypes.c_float * 5)(*[float(x) for x in mu])

@@ -25,11 +25,13 @@ struct bbc_handle_s {
   double* partial = nullptr;      // norm slab sums
   double* dnorm = nullptr;        // device ||A||_1
   unsigned int* dflag = nullptr;  // device non-finite flag
+  unsigned int* dlower = nullptr; // device: A has a nonzero below its diagonal
   void* hstage = nullptr;         // pinned host staging: [0] norm, [1] flag
   void* ozaki = nullptr;          // Ozaki slice workspace
   size_t ozaki_bytes = 0;
   // profiling: launch counters per kernel class and, when enabled, event pairs
   int64_t launches[5] = {0, 0, 0, 0, 0};
+  double flops[5] = {0, 0, 0, 0, 0};   // algorithmic FP64-product flops per class
   bool prof = false;
   struct Rec { int kind; cudaEvent_t a, b; };
   std::vector<Rec> recs;       // recorded in this profiling window
@@ -310,8 +312,11 @@ double* slot_ptr(bbc_handle h, int slot, int64_t N, const double* A, double* T) 
 
 // One dense product alpha * (P Q) with its fused epilogue, at the precision in flags.
 int launch_product(bbc_handle h, const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
-                   int flags, cudaStream_t stream) {
+                   int flags, cudaStream_t stream, bool upper) {
   cudaError_t err;
+  // algorithmic work: 2 N^3, or for upper triangular operands 2 sum_{i<=j} (j - i + 1) = N(N+1)(N+2)/3
+  const double n = (double)N;
+  h->flops[BBC_KERNEL_PRODUCT] += upper ? n * (n + 1) * (n + 2) / 3.0 : 2.0 * n * n * n;
   if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
     const int k = ((flags >> 8) & 0xF) ? ((flags >> 8) & 0xF) : 7;
     {
@@ -320,10 +325,10 @@ int launch_product(bbc_handle h, const double* P, const double* Q, int64_t N, do
     }
     if (err != cudaSuccess) return cuda_fail(err, "split launch");
     LaunchScope scope(h, BBC_KERNEL_PRODUCT, stream);
-    err = ozaki_product(P, Q, N, alpha, e, k, h->ozaki, h->dflag, stream);
+    err = ozaki_product(P, Q, N, alpha, e, k, h->ozaki, h->dflag, stream, upper);
   } else {
     LaunchScope scope(h, BBC_KERNEL_PRODUCT, stream);
-    err = gemm_f64(P, Q, N, alpha, e, stream);
+    err = gemm_f64(P, Q, N, alpha, e, stream, upper);
   }
   if (err != cudaSuccess) return cuda_fail(err, "product launch");
   return BBC_OK;
@@ -331,7 +336,7 @@ int launch_product(bbc_handle h, const double* P, const double* Q, int64_t N, do
 
 // One product (or linear combination) with its fused epilogue.
 int run_step(bbc_handle h, const StepS& st, int64_t N, const double* A, double* T, int flags,
-             unsigned int* flag, cudaStream_t stream) {
+             unsigned int* flag, cudaStream_t stream, bool upper = false) {
   Epilogue e{};
   int ny = 0;
   e.nout = st.nout;
@@ -362,7 +367,7 @@ int run_step(bbc_handle h, const StepS& st, int64_t N, const double* A, double* 
   }
   const double* P = slot_ptr(h, st.P, N, A, T);
   const double* Q = slot_ptr(h, st.Q, N, A, T);
-  return launch_product(h, P, Q, N, st.alpha, e, flags, stream);
+  return launch_product(h, P, Q, N, st.alpha, e, flags, stream, upper);
 }
 
 int check_flags(int flags) {
@@ -371,7 +376,7 @@ int check_flags(int flags) {
   if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS && scheme != BBC_SCHEME_PADE26)
     return fail(BBC_INVALID_ARG, "unknown scheme");
   if (prec != BBC_PREC_FP64 && prec != BBC_PREC_OZAKI) return fail(BBC_INVALID_ARG, "unknown precision");
-  if (flags & ~0x3FFF) return fail(BBC_INVALID_ARG, "unknown flag bits");
+  if (flags & ~0xFFFF) return fail(BBC_INVALID_ARG, "unknown flag bits");
   if ((flags & BBC_SELECT_MASK) == BBC_SELECT_MASK) return fail(BBC_INVALID_ARG, "two selectors requested");
   if (prec == BBC_PREC_OZAKI) {
     const int k = (flags >> 8) & 0xF;
@@ -389,21 +394,33 @@ bool overlaps(const double* a, const double* b, int64_t N) {
 
 // T_m(2^-s A) into T, then s squarings ending in Out. The final write sets
 // the non-finite flag if any entry of the result is not finite.
+// upper: A is upper triangular. Every product then runs on the triangles only,
+// and the exact diagonal and first superdiagonal of exp(2^-q A) replace the
+// computed ones after the polynomial (q = s) and after every squaring (Section
+// 5, concluding remarks). Not used for the Pade comparator (dense solve).
 int run_expm(bbc_handle h, const double* A, int64_t N, double* Out, int m, int s, int flags,
-             cudaStream_t stream, bbc_info* info) {
+             cudaStream_t stream, bbc_info* info, bool upper = false) {
   Program prog;
   if (!make_program(flags & BBC_SCHEME_MASK, m, s, &prog))
     return fail(BBC_INVALID_ARG, "degree not available in this scheme");
   if (s < 0 || s > 1100) return fail(BBC_INVALID_ARG, "squarings out of range");
   const bool pade = (flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE26;
   if (pade && N > 1024) return fail(BBC_UNSUPPORTED, "the Pade comparator serves N <= 1024");
+  if (pade) upper = false;
+  auto exact = [&](double* T, int q) -> int {
+    if (!upper) return BBC_OK;
+    LaunchScope scope(h, BBC_KERNEL_LINCOMB, stream);
+    const cudaError_t e = exact_diagonals(A, N, q, T, stream);
+    return e == cudaSuccess ? BBC_OK : cuda_fail(e, "exact diagonals");
+  };
   double* tmp = h->work + (size_t)SL_SQ * N * N;
   double* T = (s % 2 == 0) ? Out : tmp;  // the ping-pong ends in Out
   for (size_t i = 0; i < prog.steps.size(); ++i) {
     const bool last = (s == 0 && i + 1 == prog.steps.size() && !pade);
-    const int rc = run_step(h, prog.steps[i], N, A, T, flags, last ? h->dflag : nullptr, stream);
+    const int rc = run_step(h, prog.steps[i], N, A, T, flags, last ? h->dflag : nullptr, stream, upper);
     if (rc) return rc;
   }
+  if (int rc = exact(T, s)) return rc;
   if (pade) {  // (-u + v) r_26 = u + v: W8 holds -u + v, T holds u + v
     LaunchScope scope(h, BBC_KERNEL_LINCOMB, stream);
     const cudaError_t e = lu_solve_inplace(h->work + (size_t)8 * N * N, T, N, s == 0 ? h->dflag : nullptr, stream);
@@ -416,14 +433,16 @@ int run_expm(bbc_handle h, const double* A, int64_t N, double* Out, int m, int s
     sq.P = SL_A; sq.Q = SL_A; sq.alpha = 1.0; sq.nout = 1;
     sq.o[0].dst = SL_T; sq.o[0].cv = 1.0; sq.o[0].cI = 0.0; sq.o[0].nt = 0;
     // SL_A -> src and SL_T -> dst for this step
-    const int rc = run_step(h, sq, N, src, dst, flags, (k + 1 == s) ? h->dflag : nullptr, stream);
+    const int rc = run_step(h, sq, N, src, dst, flags, (k + 1 == s) ? h->dflag : nullptr, stream, upper);
     if (rc) return rc;
+    if (int rc2 = exact(dst, s - k - 1)) return rc2;
     src = dst;
   }
   if (info) {
     info->m = m;
     info->s = s;
     info->products = prog.products + s;
+    info->structure = upper ? 1 : 0;
   }
   return BBC_OK;
 }
@@ -445,17 +464,22 @@ int begin(bbc_handle h) {
   return BBC_OK;
 }
 
-int read_norm(bbc_handle h, const double* A, int64_t N, cudaStream_t st, double* norm) {
+// ||A||_1 to the host; with `upper` non-null also whether A is upper triangular
+// (found in the same pass over A).
+int read_norm(bbc_handle h, const double* A, int64_t N, cudaStream_t st, double* norm, bool* upper = nullptr) {
   cudaError_t e;
   {
     LaunchScope scope(h, BBC_KERNEL_NORM, st);
-    e = bbc::norm1(A, N, h->partial, h->dnorm, st);
+    e = bbc::norm1(A, N, h->partial, h->dnorm, st, upper ? h->dlower : nullptr);
   }
   if (e != cudaSuccess) return cuda_fail(e, "norm1");
   double* hs = (double*)h->hstage;
+  unsigned int* hl = (unsigned int*)(hs + 2);
   BBC_CUDA(cudaMemcpyAsync(hs, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (upper) BBC_CUDA(cudaMemcpyAsync(hl, h->dlower, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   BBC_CUDA(cudaStreamSynchronize(st));
   *norm = hs[0];
+  if (upper) *upper = (*hl == 0) && N > 1;
   return BBC_OK;
 }
 
@@ -484,6 +508,7 @@ int bbc_create(bbc_handle* out, int device) {
   h->device = device;
   cudaError_t e = cudaMalloc(&h->dnorm, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->dflag, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->dlower, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMallocHost(&h->hstage, 64);
   if (e != cudaSuccess) {
     bbc_destroy(h);
@@ -500,6 +525,7 @@ int bbc_destroy(bbc_handle h) {
   cudaFree(h->partial);
   cudaFree(h->dnorm);
   cudaFree(h->dflag);
+  cudaFree(h->dlower);
   cudaFree(h->ozaki);
   cudaFree(h->io);
   cudaFree(h->batch_work);
@@ -537,7 +563,20 @@ int bbc_profile_enable(bbc_handle h, int enable) {
   for (auto& r : h->recs) { h->pool.push_back(r.a); h->pool.push_back(r.b); }
   h->recs.clear();
   for (auto& l : h->launches) l = 0;
+  for (auto& f : h->flops) f = 0.0;
   h->prof = enable != 0;
+  return BBC_OK;
+}
+
+int bbc_profile_flops(bbc_handle h, int kind, double* flops) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!flops || kind < -1 || kind > 4) return fail(BBC_INVALID_ARG, "bad profile query");
+  std::lock_guard<std::mutex> lk(h->mu);
+  double f = 0.0;
+  for (int k = 0; k < 5; ++k)
+    if (kind == -1 || kind == k) f += h->flops[k];
+  *flops = f;
   return BBC_OK;
 }
 
@@ -620,7 +659,7 @@ int bbc_gemm(bbc_handle h, const double* dP, const double* dQ, int64_t N, double
   cudaStream_t st = (cudaStream_t)stream;
   const bool ozaki = (flags & BBC_PREC_MASK) == BBC_PREC_OZAKI;
   if (ozaki) BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
-  if ((rc = launch_product(h, dP, dQ, N, 1.0, e, flags, st))) return rc;
+  if ((rc = launch_product(h, dP, dQ, N, 1.0, e, flags, st, (flags & BBC_UPPER) != 0))) return rc;
   if (ozaki) {  // report a non-finite operand or an expired device wait
     int status = BBC_OK;
     if ((rc = finish_status(h, st, &status))) return rc;
@@ -661,13 +700,14 @@ int bbc_expm_fixed(bbc_handle h, const double* dA, int64_t N, double* dOut, int 
   bbc_info* inf = info ? info : &loc;
   memset(inf, 0, sizeof *inf);
   inf->selector = 1;
-  if ((rc = read_norm(h, dA, N, st, &inf->norm1))) return rc;
+  bool upper = false;
+  if ((rc = read_norm(h, dA, N, st, &inf->norm1, (flags & BBC_DENSE) ? nullptr : &upper))) return rc;
   if (!std::isfinite(inf->norm1)) {
     inf->status = BBC_NONFINITE_INPUT;
     return fail(BBC_NONFINITE_INPUT, "input holds a non-finite value");
   }
   BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
-  if ((rc = run_expm(h, dA, N, dOut, m, s, flags, st, inf))) return rc;
+  if ((rc = run_expm(h, dA, N, dOut, m, s, flags, st, inf, upper))) return rc;
   if ((rc = finish_status(h, st, &inf->status))) return rc;
   if (inf->status) return fail(inf->status, "result holds a non-finite value");
   return BBC_OK;
@@ -688,7 +728,8 @@ int bbc_expm(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol
   bbc_info loc{};
   bbc_info* inf = info ? info : &loc;
   memset(inf, 0, sizeof *inf);
-  if ((rc = read_norm(h, dA, N, st, &inf->norm1))) return rc;
+  bool upper = false;
+  if ((rc = read_norm(h, dA, N, st, &inf->norm1, (flags & BBC_DENSE) ? nullptr : &upper))) return rc;
   if (!std::isfinite(inf->norm1)) {
     inf->status = BBC_NONFINITE_INPUT;
     return fail(BBC_NONFINITE_INPUT, "input holds a non-finite value");
@@ -696,7 +737,7 @@ int bbc_expm(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol
   int m, s;
   select_ms(inf->norm1, u, flags & BBC_SCHEME_MASK, &m, &s);
   BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
-  if ((rc = run_expm(h, dA, N, dOut, m, s, flags, st, inf))) return rc;
+  if ((rc = run_expm(h, dA, N, dOut, m, s, flags, st, inf, upper))) return rc;
   if ((rc = finish_status(h, st, &inf->status))) return rc;
   if (inf->status) return fail(inf->status, "result holds a non-finite value");
   return BBC_OK;

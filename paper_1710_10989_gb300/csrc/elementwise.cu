@@ -25,21 +25,34 @@ int64_t slabs_for(int64_t N) {
 }
 
 __global__ void __launch_bounds__(NORM_THREADS)
-k_colsum(const double* __restrict__ A, int64_t N, int64_t rows_per, double* __restrict__ partial) {
+k_colsum(const double* __restrict__ A, int64_t N, int64_t rows_per, double* __restrict__ partial,
+         unsigned int* __restrict__ lower_nz) {
   const int64_t j = (int64_t)blockIdx.x * NORM_THREADS + threadIdx.x;
   if (j >= N) return;
   const int64_t r0 = (int64_t)blockIdx.y * rows_per;
   const int64_t r1 = r0 + rows_per < N ? r0 + rows_per : N;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  bool below = false;  // a nonzero strictly below the diagonal in this column (rows i > j)
   int64_t i = r0;
   for (; i + 4 <= r1; i += 4) {
-    s0 += fabs(__ldg(A + (i + 0) * N + j));
-    s1 += fabs(__ldg(A + (i + 1) * N + j));
-    s2 += fabs(__ldg(A + (i + 2) * N + j));
-    s3 += fabs(__ldg(A + (i + 3) * N + j));
+    const double a0 = __ldg(A + (i + 0) * N + j), a1 = __ldg(A + (i + 1) * N + j);
+    const double a2 = __ldg(A + (i + 2) * N + j), a3 = __ldg(A + (i + 3) * N + j);
+    s0 += fabs(a0);
+    s1 += fabs(a1);
+    s2 += fabs(a2);
+    s3 += fabs(a3);
+    below |= (i + 0 > j && a0 != 0.0) | (i + 1 > j && a1 != 0.0) | (i + 2 > j && a2 != 0.0) |
+             (i + 3 > j && a3 != 0.0);
   }
-  for (; i < r1; ++i) s0 += fabs(__ldg(A + i * N + j));
+  for (; i < r1; ++i) {
+    const double a = __ldg(A + i * N + j);
+    s0 += fabs(a);
+    below |= (i > j && a != 0.0);
+  }
   partial[(int64_t)blockIdx.y * N + j] = (s0 + s1) + (s2 + s3);
+  const unsigned act = __activemask();
+  const unsigned any = __ballot_sync(act, below);  // one atomic per warp that saw one
+  if (lower_nz && any && (int)(threadIdx.x & 31) == __ffs(act) - 1) atomicOr(lower_nz, 1u);
 }
 
 __global__ void __launch_bounds__(NORM_THREADS)
@@ -69,13 +82,15 @@ __global__ void k_lincomb(int64_t N, const Epilogue e) {
 
 int64_t norm1_partial_len(int64_t N) { return slabs_for(N) * N; }
 
-cudaError_t norm1(const double* A, int64_t N, double* partial, double* dNorm, cudaStream_t st) {
+cudaError_t norm1(const double* A, int64_t N, double* partial, double* dNorm, cudaStream_t st,
+                  unsigned int* lower_nz) {
   const int64_t slabs = slabs_for(N);
   const int64_t rows_per = (N + slabs - 1) / slabs;
   const unsigned colblocks = (unsigned)((N + NORM_THREADS - 1) / NORM_THREADS);
   cudaError_t err = cudaMemsetAsync(dNorm, 0, sizeof(double), st);
   if (err != cudaSuccess) return err;
-  k_colsum<<<dim3(colblocks, (unsigned)slabs), NORM_THREADS, 0, st>>>(A, N, rows_per, partial);
+  if (lower_nz && (err = cudaMemsetAsync(lower_nz, 0, sizeof(unsigned int), st)) != cudaSuccess) return err;
+  k_colsum<<<dim3(colblocks, (unsigned)slabs), NORM_THREADS, 0, st>>>(A, N, rows_per, partial, lower_nz);
   k_colmax<<<colblocks, NORM_THREADS, 0, st>>>(partial, N, slabs, (unsigned long long*)dNorm);
   return cudaGetLastError();
 }
@@ -85,6 +100,34 @@ cudaError_t lincomb(int64_t N, const Epilogue& e, cudaStream_t st) {
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   k_lincomb<<<(unsigned)blocks, 256, 0, st>>>(N, e);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// Upper triangular A: the diagonal and first superdiagonal of exp(2^-q A) in
+// closed form (Section 5, concluding remarks): e^{l_i} on the diagonal, and for
+// the block [[l1, t], [0, l2]] the divided difference t (e^l2 - e^l1)/(l2 - l1),
+// evaluated as t e^((l1+l2)/2) sinh(d)/d with d = (l2 - l1)/2 (no cancellation;
+// e^l1 when l1 = l2). Written over T's computed values.
+__global__ void k_exact_diag(const double* __restrict__ A, int64_t N, int q, double* __restrict__ T) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double l1 = ldexp(A[i * N + i], -q);
+  T[i * N + i] = exp(l1);
+  if (i + 1 < N) {
+    const double l2 = ldexp(A[(i + 1) * N + i + 1], -q);
+    const double t = ldexp(A[i * N + i + 1], -q);
+    const double d = 0.5 * (l2 - l1);
+    const double sinhc = (d == 0.0) ? 1.0 : sinh(d) / d;
+    T[i * N + i + 1] = t * exp(0.5 * (l1 + l2)) * sinhc;
+  }
+}
+
+}  // namespace
+
+cudaError_t exact_diagonals(const double* A, int64_t N, int q, double* T, cudaStream_t st) {
+  k_exact_diag<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(A, N, q, T);
   return cudaGetLastError();
 }
 

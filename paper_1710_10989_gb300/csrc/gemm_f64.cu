@@ -19,9 +19,9 @@ constexpr int BK = 16;
 constexpr int THREADS = 256;
 
 template <int BM, int BN>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 3)  // three blocks per SM keep the FP64 pipe fed
 k_gemm_f64(const double* __restrict__ P, const double* __restrict__ Q, int64_t N, double alpha,
-           const Epilogue e) {
+           const Epilogue e, int upper) {
   constexpr int TM = BM / 16, TN = BN / 16;
   constexpr int LP = BM * BK / THREADS;   // P elements per thread per slab
   constexpr int LQ = BK * BN / THREADS;   // Q elements per thread per slab
@@ -59,13 +59,21 @@ k_gemm_f64(const double* __restrict__ P, const double* __restrict__ Q, int64_t N
     for (int q = 0; q < LQ; ++q) Bs[buf][t / BN + QROWS * q][t % BN] = rq[q];
   };
 
-  const int64_t nslab = (N + BK - 1) / BK;
-  load(0);
-  store(0);
+  // K slabs to sum: all of them, or for upper triangular P and Q the slabs that
+  // meet [m0, n0 + BN) (P_ik = 0 for k < i, Q_kj = 0 for k > j); none below the diagonal
+  int64_t s0 = 0, s1 = (N + BK - 1) / BK;
+  if (upper) {
+    s0 = m0 / BK;
+    s1 = min(s1, (n0 + BN + BK - 1) / BK);
+  }
+  if (s0 < s1) {
+    load(s0 * BK);
+    store(0);
+  }
   __syncthreads();
-  for (int64_t s = 0; s < nslab; ++s) {
-    const int buf = s & 1;
-    if (s + 1 < nslab) load((s + 1) * BK);
+  for (int64_t s = s0; s < s1; ++s) {
+    const int buf = (int)((s - s0) & 1);
+    if (s + 1 < s1) load((s + 1) * BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       double a[TM], b[TN];
@@ -78,10 +86,11 @@ k_gemm_f64(const double* __restrict__ P, const double* __restrict__ Q, int64_t N
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
-    if (s + 1 < nslab) store(buf ^ 1);
+    if (s + 1 < s1) store(buf ^ 1);
     __syncthreads();
   }
 
+  const bool zero_block = upper && n0 + BN <= m0;  // strictly below the diagonal: every output is 0
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int64_t row = m0 + ty + 16 * i;
@@ -89,7 +98,9 @@ k_gemm_f64(const double* __restrict__ P, const double* __restrict__ Q, int64_t N
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int64_t col = n0 + tx + 16 * j;
-      if (col < N) apply_epilogue(e, N, row, col, alpha * acc[i][j]);
+      if (col >= N) continue;
+      if (zero_block) zero_epilogue(e, N, row, col);
+      else apply_epilogue(e, N, row, col, alpha * acc[i][j]);
     }
   }
 }
@@ -97,13 +108,13 @@ k_gemm_f64(const double* __restrict__ P, const double* __restrict__ Q, int64_t N
 }  // namespace
 
 cudaError_t gemm_f64(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
-                     cudaStream_t st) {
+                     cudaStream_t st, bool upper) {
   if (N <= 512) {
     dim3 grid((unsigned)((N + 31) / 32), (unsigned)((N + 31) / 32));
-    k_gemm_f64<32, 32><<<grid, THREADS, 0, st>>>(P, Q, N, alpha, e);
+    k_gemm_f64<32, 32><<<grid, THREADS, 0, st>>>(P, Q, N, alpha, e, upper ? 1 : 0);
   } else {
     dim3 grid((unsigned)((N + 63) / 64), (unsigned)((N + 63) / 64));
-    k_gemm_f64<64, 64><<<grid, THREADS, 0, st>>>(P, Q, N, alpha, e);
+    k_gemm_f64<64, 64><<<grid, THREADS, 0, st>>>(P, Q, N, alpha, e, upper ? 1 : 0);
   }
   return cudaGetLastError();
 }

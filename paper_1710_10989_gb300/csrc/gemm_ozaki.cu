@@ -46,6 +46,9 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
 #include <cstring>
 #include <mutex>
 
@@ -428,6 +431,37 @@ __device__ __forceinline__ void pair_tile(int t, int tiles_m, int tiles_n, int* 
   *nt = w / rows;
 }
 
+// The K steps one output tile needs: all of them, or for upper triangular P and
+// Q the steps meeting [first row, last column] (P_ik = 0 for k < i, Q_kj = 0 for
+// k > j); tiles strictly below the diagonal need none (their epilogue writes the
+// zeros). Chunks are the 1024-wide K blocks that meet that range.
+struct TileWork {
+  int mp, nt;          // pair row block, column block
+  int ks_lo, ks_hi;    // K steps [ks_lo, ks_hi)
+  int c_lo, nch;       // first chunk, number of chunks
+};
+__device__ __forceinline__ TileWork tile_work(int t, const uint32_t* __restrict__ list, int tiles_m, int tiles_n,
+                                              int nksteps, int upper) {
+  TileWork w;
+  if (list) {
+    const uint32_t code = __ldg(list + t);
+    w.mp = (int)(code >> 16);
+    w.nt = (int)(code & 0xFFFFu);
+  } else {
+    pair_tile(t, tiles_m, tiles_n, &w.mp, &w.nt);
+  }
+  w.ks_lo = upper ? min(nksteps, w.mp * (2 * TILE / KSTEP)) : 0;
+  w.ks_hi = upper ? min(nksteps, (w.nt + 1) * (TILE / KSTEP)) : nksteps;
+  if (w.ks_hi <= w.ks_lo) {
+    w.c_lo = 0;
+    w.nch = 0;
+  } else {
+    w.c_lo = w.ks_lo / CHUNK_STEPS;
+    w.nch = (w.ks_hi + CHUNK_STEPS - 1) / CHUNK_STEPS - w.c_lo;
+  }
+  return w;
+}
+
 // Work items of one output tile, in the order all three roles walk them: the low
 // groups first (g = k-1 down to G_EXACT: the Horner order), then the high groups
 // (g = 0 up); inside a group the slice pairs p = 0..g (q = g - p), inside a pair the
@@ -460,7 +494,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
              const int* __restrict__ erow, const int* __restrict__ fcol, const double* __restrict__ P,
              const double* __restrict__ Q, const double* __restrict__ pdiag, const double* __restrict__ qdiag,
              int64_t N, double alpha, int nslices, int nksteps, int tiles_m, int tiles_n, const Epilogue e,
-             unsigned int* __restrict__ status) {
+             unsigned int* __restrict__ status, const uint32_t* __restrict__ tile_list, int upper) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   uint8_t* smA = smem;
@@ -472,11 +506,9 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   const uint32_t rank = cluster_rank();
   const int cid = cluster_index(), ncl = cluster_count();
   const int ntiles = tiles_m * tiles_n;
-  const int nch = (nksteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
-  const int gh = min(nslices, G_EXACT);                        // high groups 0..gh-1
-  const int nH = gh * (gh + 1) / 2 * nch;                        // high items per tile
-  const int nL = nslices * (nslices + 1) / 2 * nch - nH;         // low items per tile
-  const int nunits = nH + nL;
+  const int gh = min(nslices, G_EXACT);                           // high groups 0..gh-1
+  const int pairs_h = gh * (gh + 1) / 2;                            // high slice pairs
+  const int pairs_l = nslices * (nslices + 1) / 2 - pairs_h;        // low slice pairs
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < P_STAGES; ++s) { mbar_init(&sh->full[s], 1); mbar_init(&sh->empty[s], 1); }
@@ -512,14 +544,15 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     uint32_t ph = 0;
     bool ok = true;
     for (int t = cid; t < ntiles && ok; t += ncl) {
-      int mp, nt;
-      pair_tile(t, tiles_m, tiles_n, &mp, &nt);
-      const int arow = mp * 2 * TILE + (int)rank * TILE;
-      const int brow = nt * TILE + (int)rank * (TILE / 2);
-      ItemCursor cur(nslices, nch);
+      const TileWork w = tile_work(t, tile_list, tiles_m, tiles_n, nksteps, upper);
+      const int arow = w.mp * 2 * TILE + (int)rank * TILE;
+      const int brow = w.nt * TILE + (int)rank * (TILE / 2);
+      const int nunits = (pairs_h + pairs_l) * w.nch;
+      ItemCursor cur(nslices, w.nch);
       for (int idx = 0; idx < nunits && ok; ++idx, cur.advance()) {
-        const int ks1 = min(nksteps, (cur.c + 1) * CHUNK_STEPS);
-        for (int ks = cur.c * CHUNK_STEPS; ks < ks1; ++ks) {
+        const int ca = w.c_lo + cur.c;
+        const int ks1 = min(w.ks_hi, (ca + 1) * CHUNK_STEPS);
+        for (int ks = max(w.ks_lo, ca * CHUNK_STEPS); ks < ks1; ++ks) {
           if (!mbar_wait_warp(&sh->empty[s], ph ^ 1u, cta_err)) { ok = false; break; }
           if (leader_lane) {
             if (rank == 0) mbar_arrive_expect_tx(&sh->full[s], 2 * P_STAGE_BYTES);
@@ -547,15 +580,17 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       const uint64_t dA0 = smem_desc(smem_u32(smA)), dB0 = smem_desc(smem_u32(smB));
       int s = 0;
       uint32_t ph = 0;
-      int hc = 0, tl = 0;
+      int hc = 0, ln = 0;  // high items and low-buffer uses so far (the drains count alike)
       bool ok = true;
-      for (int t = cid; t < ntiles && ok; t += ncl, ++tl) {
-        const int lb = tl & 1;
+      for (int t = cid; t < ntiles && ok; t += ncl) {
+        const TileWork w = tile_work(t, tile_list, tiles_m, tiles_n, nksteps, upper);
+        const int nL = pairs_l * w.nch, nunits = (pairs_h + pairs_l) * w.nch;
+        const int lb = ln & 1;
         if (nL > 0) {
-          if (!mbar_wait_warp_cl(&sh->low_empty[lb], ((uint32_t)(tl >> 1) & 1u) ^ 1u, cta_err)) { ok = false; break; }
+          if (!mbar_wait_warp_cl(&sh->low_empty[lb], ((uint32_t)(ln >> 1) & 1u) ^ 1u, cta_err)) { ok = false; break; }
           tc_fence_after();
         }
-        ItemCursor cur(nslices, nch);
+        ItemCursor cur(nslices, w.nch);
         for (int idx = 0; idx < nunits && ok; ++idx, cur.advance()) {
           uint32_t d_tmem;
           int b = 0, kind0;  // first MMA: 0 fresh, 1 accumulate, 2 accumulate onto 2^-8 x the sum so far
@@ -569,7 +604,8 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             d_tmem = tmem + (uint32_t)(b * TILE);
             kind0 = 0;
           }
-          const int ks1 = min(nksteps, (cur.c + 1) * CHUNK_STEPS);
+          const int ca = w.c_lo + cur.c;
+          const int ks0 = max(w.ks_lo, ca * CHUNK_STEPS), ks1 = min(w.ks_hi, (ca + 1) * CHUNK_STEPS);
           if (!mbar_wait_warp_cl(&sh->full[s], ph, cta_err)) { ok = false; break; }
           if (issuer) {
             const uint64_t da = dA0 + (uint64_t)(s * (P_A_BYTES >> 4)), db = dB0 + (uint64_t)(s * (P_B_BYTES >> 4));
@@ -582,7 +618,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           }
           __syncwarp();
           if (++s == P_STAGES) { s = 0; ph ^= 1u; }
-          for (int ks = cur.c * CHUNK_STEPS + 1; ks < ks1; ++ks) {
+          for (int ks = ks0 + 1; ks < ks1; ++ks) {
             if (!mbar_wait_warp_cl(&sh->full[s], ph, cta_err)) { ok = false; break; }
             if (issuer) {
               const uint64_t da = dA0 + (uint64_t)(s * (P_A_BYTES >> 4)), db = dB0 + (uint64_t)(s * (P_B_BYTES >> 4));
@@ -604,6 +640,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           }
           __syncwarp();
         }
+        if (nL > 0) ++ln;
       }
       if (issuer) commit_pair(&sh->mma_done);
       __syncwarp();
@@ -619,15 +656,17 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     const int half = (warp - 2) >> 2;      // which 64 of the tile's 128 columns
     const int row_in_tile = q * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 64);
-    int hc = 0, tl = 0;
+    int hc = 0, ln = 0;
     bool ok = true;
-    for (int t = cid; t < ntiles && ok; t += ncl, ++tl) {
+    for (int t = cid; t < ntiles && ok; t += ncl) {
+      const TileWork w = tile_work(t, tile_list, tiles_m, tiles_n, nksteps, upper);
+      const int nL = pairs_l * w.nch;
       long long R[64];
 #pragma unroll
       for (int i = 0; i < 64; ++i) R[i] = 0;
       for (int g = 0; g < gh && ok; ++g) {
         const int shift = 8 * (G_EXACT - 1 - g);
-        for (int n = (g + 1) * nch; n > 0; --n) {  // the items of group g: (g + 1) pairs x nch chunks
+        for (int n = (g + 1) * w.nch; n > 0; --n) {  // the items of group g: (g + 1) pairs x its chunks
           const int b = hc & 1;
           ok = mbar_wait_warp(&sh->acc_full[b], (uint32_t)(hc >> 1) & 1u, cta_err);
           if (!ok) break;
@@ -650,16 +689,19 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         }
       }
       if (!ok) break;
-      const int lb = tl & 1;
+      const int lb = ln & 1;
       if (nL > 0) {
-        ok = mbar_wait_warp(&sh->low_full[lb], (uint32_t)(tl >> 1) & 1u, cta_err);
+        ok = mbar_wait_warp(&sh->low_full[lb], (uint32_t)(ln >> 1) & 1u, cta_err);
         if (!ok) break;
         tc_fence_after();
       }
-      int mp, nt;
-      pair_tile(t, tiles_m, tiles_n, &mp, &nt);
-      const int64_t row = (int64_t)mp * 2 * TILE + (int64_t)rank * TILE + row_in_tile;
-      const int64_t col0 = (int64_t)nt * TILE + half * 64;
+      const int64_t row = (int64_t)w.mp * 2 * TILE + (int64_t)rank * TILE + row_in_tile;
+      const int64_t col0 = (int64_t)w.nt * TILE + half * 64;
+      if (upper && w.nt * TILE + TILE <= w.mp * 2 * TILE) {  // strictly below the diagonal: zeros
+        if (row < N)
+          for (int64_t col = col0; col < min(N, col0 + 64); ++col) zero_epilogue(e, N, row, col);
+        continue;
+      }
       const int er = (row < N) ? erow[row] : 0;
       const double pii = (row < N) ? pdiag[row] : 0.0;
 #pragma unroll
@@ -694,6 +736,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           }
         }
       }
+      if (nL > 0) ++ln;
     }
   }
 
@@ -763,11 +806,15 @@ bool ozaki_supported(int64_t N) { return N >= 1 && N <= 16384; }
 
 // Layout of the workspace: 256 reserved bytes, erow[Rp], fcol[Rp], fexp[Rp], the
 // deflated diagonals pdiag[Rp], qdiag[Rp], then the P planes and the Q^T planes,
-// each k x Rp x Rp BF16.
+// each k x Rp x Rp BF16, then the tile order of the triangular products.
+size_t tile_count(int64_t N) {
+  const int64_t Rp = padded(N);
+  return (size_t)((Rp + 2 * TILE - 1) / (2 * TILE)) * (size_t)(Rp / TILE);
+}
 size_t ozaki_workspace_bytes(int64_t N, int slices) {
   const int64_t Rp = padded(N);
   return 256 + 3 * (size_t)Rp * sizeof(int) + 256 + 2 * (size_t)Rp * sizeof(double) + 256 +
-         2 * (size_t)slices * Rp * Rp * 2;
+         2 * (size_t)slices * Rp * Rp * 2 + 256 + tile_count(N) * sizeof(uint32_t);
 }
 
 namespace {
@@ -780,6 +827,7 @@ struct OzLayout {
   double* qdiag;
   uint16_t* Ps;
   uint16_t* Qs;
+  uint32_t* tiles;
 };
 OzLayout layout(void* work, int64_t N, int slices) {
   OzLayout L;
@@ -796,6 +844,9 @@ OzLayout layout(void* work, int64_t N, int slices) {
   off = (off + 255) / 256 * 256;
   L.Ps = reinterpret_cast<uint16_t*>(w + off);
   L.Qs = L.Ps + (size_t)slices * L.Rp * L.Rp;
+  off += 2 * (size_t)slices * L.Rp * L.Rp * 2;
+  off = (off + 255) / 256 * 256;
+  L.tiles = reinterpret_cast<uint32_t*>(w + off);
   return L;
 }
 }  // namespace
@@ -847,8 +898,36 @@ int pair_clusters() {
   return n;
 }
 
+// Tile order for triangular products, where tiles cost from nothing (below the
+// diagonal) to a full K sweep (top right): sorted by cost and dealt to the
+// clusters in a snake (cluster c takes list entries c, c + ncl, ...), so every
+// cluster gets about the same number of K steps. Kept per (tiles, clusters).
+const std::vector<uint32_t>& upper_tile_order(int tiles_m, int tiles_n, int nksteps, int ncl) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int>, std::vector<uint32_t>> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(tiles_m, tiles_n, nksteps, ncl);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  struct T { int cost; uint32_t code; };
+  std::vector<T> v;
+  for (int mp = 0; mp < tiles_m; ++mp)
+    for (int nt = 0; nt < tiles_n; ++nt) {
+      const int lo = std::min(nksteps, mp * (2 * TILE / KSTEP)), hi = std::min(nksteps, (nt + 1) * (TILE / KSTEP));
+      v.push_back({std::max(0, hi - lo), ((uint32_t)mp << 16) | (uint32_t)nt});
+    }
+  std::stable_sort(v.begin(), v.end(), [](const T& a, const T& b) { return a.cost > b.cost; });
+  std::vector<uint32_t> out(v.size());
+  const size_t n = v.size();
+  for (size_t r0 = 0, round = 0; r0 < n; r0 += (size_t)ncl, ++round) {
+    const size_t m = std::min((size_t)ncl, n - r0);
+    for (size_t c = 0; c < m; ++c) out[r0 + c] = v[r0 + ((round & 1) ? m - 1 - c : c)].code;
+  }
+  return cache.emplace(key, std::move(out)).first->second;
+}
+
 cudaError_t launch_pair(const OzLayout& L, const double* P, const double* Q, int64_t N, double alpha,
-                        const Epilogue& e, int slices, unsigned int* flag, cudaStream_t st) {
+                        const Epilogue& e, int slices, unsigned int* flag, cudaStream_t st, bool upper) {
   CUtensorMap ta, tb;
   if (!make_map(&ta, L.Ps, L.Rp, L.Rp, slices, TILE) || !make_map(&tb, L.Qs, L.Rp, L.Rp, slices, TILE / 2))
     return cudaErrorNotSupported;
@@ -857,6 +936,14 @@ cudaError_t launch_pair(const OzLayout& L, const double* P, const double* Q, int
   const int tiles_m = (int)((L.Rp + 2 * TILE - 1) / (2 * TILE));
   const int tiles_n = (int)(L.Rp / TILE);
   const int ncl = std::min(ncl_max, tiles_m * tiles_n);
+  const uint32_t* list = nullptr;
+  if (upper) {  // host order -> workspace (the vector lives in the cache, so the async copy may outlast this call)
+    const std::vector<uint32_t>& order = upper_tile_order(tiles_m, tiles_n, (int)(L.Rp / KSTEP), ncl);
+    const cudaError_t err = cudaMemcpyAsync(L.tiles, order.data(), order.size() * sizeof(uint32_t),
+                                            cudaMemcpyHostToDevice, st);
+    if (err != cudaSuccess) return err;
+    list = L.tiles;
+  }
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -871,14 +958,14 @@ cudaError_t launch_pair(const OzLayout& L, const double* P, const double* Q, int
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_ozaki_pair, ta, tb, (const int*)L.erow, (const int*)L.fcol, P, Q,
                             (const double*)L.pdiag, (const double*)L.qdiag, N, alpha, slices, (int)(L.Rp / KSTEP),
-                            tiles_m, tiles_n, e, flag);
+                            tiles_m, tiles_n, e, flag, list, upper ? 1 : 0);
 }
 }  // namespace
 
 cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e, int slices,
-                          void* work, unsigned int* flag, cudaStream_t st) {
+                          void* work, unsigned int* flag, cudaStream_t st, bool upper) {
   if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
-  return launch_pair(layout(work, N, slices), P, Q, N, alpha, e, slices, flag, st);
+  return launch_pair(layout(work, N, slices), P, Q, N, alpha, e, slices, flag, st, upper);
 }
 
 }  // namespace bbc

@@ -53,16 +53,34 @@ __device__ __forceinline__ void apply_epilogue(const Epilogue& e, int64_t N, int
   if (bad && e.flag) atomicOr(e.flag, 1u);
 }
 
-// FP64 DFMA product with fused epilogue: v = alpha * (P Q).
+// Element (row, col) of every output when it is known to be zero: below the
+// diagonal of a product of upper triangular matrices, where v, the identity and
+// every matrix term of an epilogue vanish.
+__device__ __forceinline__ void zero_epilogue(const Epilogue& e, int64_t N, int64_t row, int64_t col) {
+  const int64_t idx = row * N + col;
+#pragma unroll 1
+  for (int o = 0; o < e.nout; ++o) e.o[o].out[idx] = 0.0;
+}
+
+// FP64 DFMA product with fused epilogue: v = alpha * (P Q). upper: P and Q are
+// upper triangular, so entry (i, j) sums k over [i, j] only and blocks strictly
+// below the diagonal skip the sum (their outputs come from the epilogue alone).
 cudaError_t gemm_f64(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
-                     cudaStream_t st);
+                     cudaStream_t st, bool upper = false);
 
 // Element-wise linear combination (no product): outputs of `e` with v = 0.
 cudaError_t lincomb(int64_t N, const Epilogue& e, cudaStream_t st);
 
 // ||A||_1 into *dNorm (device). `partial` must hold norm1_partial_len(N) doubles.
+// lower_nz (device word, may be null) is set to 1 if A has a nonzero strictly
+// below the diagonal, 0 otherwise.
 int64_t norm1_partial_len(int64_t N);
-cudaError_t norm1(const double* A, int64_t N, double* partial, double* dNorm, cudaStream_t st);
+cudaError_t norm1(const double* A, int64_t N, double* partial, double* dNorm, cudaStream_t st,
+                  unsigned int* lower_nz = nullptr);
+
+// Upper triangular A: overwrite the diagonal and first superdiagonal of T with
+// those of exp(2^-q A), known in closed form (Section 5, concluding remarks).
+cudaError_t exact_diagonals(const double* A, int64_t N, int q, double* T, cudaStream_t st);
 
 // ||A||_1 with the slab sums in a static device array instead of a workspace
 // (no allocation); false / cudaErrorInvalidValue when N exceeds its capacity.
@@ -79,7 +97,7 @@ size_t ozaki_workspace_bytes(int64_t N, int slices);
 cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices, void* work,
                         unsigned int* flag, cudaStream_t st);
 cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
-                          int slices, void* work, unsigned int* flag, cudaStream_t st);
+                          int slices, void* work, unsigned int* flag, cudaStream_t st, bool upper = false);
 bool ozaki_supported(int64_t N);
 
 // Solve M X = B in place (X overwrites B, M is destroyed), N <= 1024 (pade.cu).

@@ -95,7 +95,10 @@ def test_expm_selected_matches_oracle(h, api, idx, n, nonnormal):
     A = W.dense_case(idx, n=n, nonnormal=nonnormal)
     out = empty_like_dev(n)
     info = h.expm(to_dev(A), out)
-    want, oi = O.expm(A, "new")
+    # the non-normal family is upper triangular: the library finds that and takes
+    # the triangular path, whose oracle is expm_upper
+    want, oi = O.expm_upper(A, "new") if nonnormal else O.expm(A, "new")
+    assert info.structure == (1 if nonnormal else 0)
     assert (info.m, info.s, info.products) == (oi.m, oi.s, oi.products)
     assert info.norm1 == pytest.approx(oi.norm1, rel=1e-14)
     assert rel_fro(to_host(out), want) < 1e-12
@@ -180,9 +183,71 @@ def test_dense_4096_full_size(h, api, idx, nonnormal):
     A = W.dense_case(idx, nonnormal=nonnormal)
     out = empty_like_dev(A.shape[0])
     info = h.expm(to_dev(A), out)
-    want, oi = O.expm(A, "new")
+    want, oi = O.expm_upper(A, "new") if nonnormal else O.expm(A, "new")
+    assert info.structure == (1 if nonnormal else 0)
     assert (info.m, info.s) == (oi.m, oi.s)
     assert rel_fro(to_host(out), want) < 1e-12
+
+
+# ---- upper triangular structure -----------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 5, 64, 130, 300, 1025])
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_upper_products_match_oracle(h, api, n, prec):
+    """Products of upper triangular operands that sum k over [i, j] only (K ranges
+    per tile, tiles below the diagonal skipped) equal the oracle's full products."""
+    rng = np.random.default_rng(n)
+    P = np.triu(rng.standard_normal((n, n)))
+    Q = np.triu(rng.standard_normal((n, n)))
+    C = empty_like_dev(n)
+    flags = api.UPPER | (api.PREC_FP64 if prec == "fp64" else api.PREC_OZAKI | api.ozaki_slices(7))
+    h.gemm(to_dev(P), to_dev(Q), C, flags)
+    got = to_host(C)
+    want = O.gemm(P, Q)
+    assert not np.tril(got, -1).any()
+    assert rel_fro(got, want) < 4e-16 * max(4, np.sqrt(n))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_upper_expm_matches_oracle(h, api, prec):
+    flags = api.PREC_FP64 if prec == "fp64" else api.PREC_OZAKI | api.ozaki_slices(7)
+    for n, norm, seed in ((200, 20.0, 3), (513, 100.0, 4), (64, 0.05, 5)):
+        A = W.nonnormal_upper(n, seed, norm)
+        out = empty_like_dev(n)
+        info = h.expm(to_dev(A), out, 0.0, flags)
+        want, oi = O.expm_upper(A, "new")
+        assert info.structure == 1 and (info.m, info.s, info.products) == (oi.m, oi.s, oi.products)
+        got = to_host(out)
+        assert rel_fro(got, want) < 1e-12
+        assert not np.tril(got, -1).any()
+        # the exact diagonal is put back last: e^{a_ii} to the libraries' exp (CUDA's and
+        # numpy's may differ in the last place)
+        d, e = np.diag(got), np.exp(np.diag(A))
+        assert np.all(np.abs(d - e) <= 2 * np.spacing(e))
+
+
+def test_dense_flag_turns_structure_off(h, api):
+    A = W.nonnormal_upper(150, 6, 5.0)
+    out = empty_like_dev(150)
+    info = h.expm(to_dev(A), out, 0.0, api.DENSE)
+    want, oi = O.expm(A, "new")
+    assert info.structure == 0 and (info.m, info.s) == (oi.m, oi.s)
+    assert rel_fro(to_host(out), want) < 1e-12
+    B = A.copy()
+    B[100, 3] = 1e-30   # one entry below the diagonal: dense path
+    info = h.expm(to_dev(B), out)
+    assert info.structure == 0
+
+
+def test_upper_flop_accounting(h, api):
+    n = 300
+    A = W.nonnormal_upper(n, 8, 1.0)
+    out = empty_like_dev(n)
+    h.profile_enable(True)
+    info = h.expm(to_dev(A), out)
+    f = h.profile_flops(api.KERNEL_PRODUCT)
+    h.profile_enable(False)
+    assert f == pytest.approx(info.products * n * (n + 1) * (n + 2) / 3.0, rel=1e-12)
 
 
 # ---- the Pade r_26 comparator on the GPU --------------------------------------------------------
