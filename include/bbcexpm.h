@@ -50,8 +50,18 @@ typedef enum {
 #define BBC_PREC_FP64 0x00     /* every product on the FP64 pipe (DFMA) */
 #define BBC_PREC_OZAKI 0x10    /* products as exact BF16 slice products on tcgen05 tensor cores,
                                   accumulated exactly; bits 8-11 = slice count k (0 -> 7) */
+#define BBC_PREC_SPLIT 0x20    /* the literal split: each operand (row / column scaled by a power of
+                                  two) written as k BF16 terms, each the rounding of what the
+                                  earlier terms left; the k(k+1)/2 term products with p + q < k
+                                  accumulated in FP32 on the tensor cores (bits 8-11 = k, 0 -> 3).
+                                  About 8k significant bits per product, no better than FP32 sums
+                                  allow (~1e-7 relative); kept to report the plain split beside
+                                  the exact one */
 #define BBC_PREC_MASK 0xF0
 #define BBC_OZAKI_SLICES(k) (((k) & 0xF) << 8)
+/* bits 16-19: the last n squarings run on the FP64 pipe whatever the product precision
+ * (the squarings amplify a product's error 2^s-fold) */
+#define BBC_SQUARE_FP64_LAST(n) (((n) & 0xF) << 16)
 /* selection of (m, s) in bbc_expm_batched (bits 12-13; default: the paper's rule) */
 #define BBC_SELECT_LEARNED 0x1000  /* network proposal, certified, else the paper's rule */
 #define BBC_SELECT_ALPHA 0x2000    /* cheapest (m, s) certified by ||A|| or alpha_2 (computes A^2, A^3) */

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libbbcexpm.so")
 
 OK, INVALID_ARG, NONFINITE_INPUT, OVERFLOW, CUDA_ERROR, TIMEOUT, UNSUPPORTED = range(7)
 SCHEME_NEW, SCHEME_PS, SCHEME_PADE26 = 0x0, 0x1, 0x2
-PREC_FP64, PREC_OZAKI = 0x00, 0x10
+PREC_FP64, PREC_OZAKI, PREC_SPLIT = 0x00, 0x10, 0x20
 SELECT_LEARNED, SELECT_ALPHA = 0x1000, 0x2000
 DENSE, UPPER = 0x4000, 0x8000
 DEGREES = (1, 2, 4, 8, 12, 18)
@@ -25,6 +25,10 @@ U_SINGLE = 2.0 ** -24
 
 def ozaki_slices(k: int) -> int:
     return (k & 0xF) << 8
+
+
+def square_fp64_last(n: int) -> int:
+    return (n & 0xF) << 16
 
 
 class BBCError(RuntimeError):

@@ -54,6 +54,18 @@ namespace {
 
 thread_local std::string g_err;
 
+// Products rebuilt from BF16 slices on the tensor cores: the exact form
+// (BBC_PREC_OZAKI, default 7 slices) or the literal split (BBC_PREC_SPLIT,
+// default 3 terms).
+bool split_prec(int flags) {
+  const int prec = flags & BBC_PREC_MASK;
+  return prec == BBC_PREC_OZAKI || prec == BBC_PREC_SPLIT;
+}
+int split_slices(int flags) {
+  const int k = (flags >> 8) & 0xF;
+  return k ? k : ((flags & BBC_PREC_MASK) == BBC_PREC_SPLIT ? 3 : 7);
+}
+
 int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
@@ -259,9 +271,8 @@ int ensure_workspace(bbc_handle h, int64_t N, int flags) {
     BBC_CUDA(cudaMalloc(&h->partial, (size_t)h->partial_len * sizeof(double)));
     h->slots_n = N;
   }
-  if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
-    const int k = (flags >> 8) & 0xF;
-    const size_t need = ozaki_workspace_bytes(N, k ? k : 7);
+  if (split_prec(flags)) {
+    const size_t need = ozaki_workspace_bytes(N, split_slices(flags));
     if (need > h->ozaki_bytes) {
       if (h->ozaki) BBC_CUDA(cudaFree(h->ozaki));
       h->ozaki = nullptr;
@@ -317,15 +328,16 @@ int launch_product(bbc_handle h, const double* P, const double* Q, int64_t N, do
   // algorithmic work: 2 N^3, or for upper triangular operands 2 sum_{i<=j} (j - i + 1) = N(N+1)(N+2)/3
   const double n = (double)N;
   h->flops[BBC_KERNEL_PRODUCT] += upper ? n * (n + 1) * (n + 2) / 3.0 : 2.0 * n * n * n;
-  if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
-    const int k = ((flags >> 8) & 0xF) ? ((flags >> 8) & 0xF) : 7;
+  if (split_prec(flags)) {
+    const int k = split_slices(flags);
+    const bool literal = (flags & BBC_PREC_MASK) == BBC_PREC_SPLIT;
     {
       LaunchScope scope(h, BBC_KERNEL_SPLIT, stream);
-      err = ozaki_split(P, Q, N, k, h->ozaki, h->dflag, stream);
+      err = ozaki_split(P, Q, N, k, h->ozaki, h->dflag, stream, literal);
     }
     if (err != cudaSuccess) return cuda_fail(err, "split launch");
     LaunchScope scope(h, BBC_KERNEL_PRODUCT, stream);
-    err = ozaki_product(P, Q, N, alpha, e, k, h->ozaki, h->dflag, stream, upper);
+    err = ozaki_product(P, Q, N, alpha, e, k, h->ozaki, h->dflag, stream, upper, literal);
   } else {
     LaunchScope scope(h, BBC_KERNEL_PRODUCT, stream);
     err = gemm_f64(P, Q, N, alpha, e, stream, upper);
@@ -375,12 +387,13 @@ int check_flags(int flags) {
   const int prec = flags & BBC_PREC_MASK;
   if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS && scheme != BBC_SCHEME_PADE26)
     return fail(BBC_INVALID_ARG, "unknown scheme");
-  if (prec != BBC_PREC_FP64 && prec != BBC_PREC_OZAKI) return fail(BBC_INVALID_ARG, "unknown precision");
-  if (flags & ~0xFFFF) return fail(BBC_INVALID_ARG, "unknown flag bits");
+  if (prec != BBC_PREC_FP64 && prec != BBC_PREC_OZAKI && prec != BBC_PREC_SPLIT)
+    return fail(BBC_INVALID_ARG, "unknown precision");
+  if (flags & ~0xFFFFF) return fail(BBC_INVALID_ARG, "unknown flag bits");
   if ((flags & BBC_SELECT_MASK) == BBC_SELECT_MASK) return fail(BBC_INVALID_ARG, "two selectors requested");
-  if (prec == BBC_PREC_OZAKI) {
+  if (prec == BBC_PREC_OZAKI || prec == BBC_PREC_SPLIT) {
     const int k = (flags >> 8) & 0xF;
-    if (k != 0 && (k < 2 || k > 8)) return fail(BBC_INVALID_ARG, "Ozaki slice count must be 2..8");
+    if (k != 0 && (k < 2 || k > 8)) return fail(BBC_INVALID_ARG, "slice count must be 2..8");
   }
   return BBC_OK;
 }
@@ -432,8 +445,10 @@ int run_expm(bbc_handle h, const double* A, int64_t N, double* Out, int m, int s
     StepS sq{};
     sq.P = SL_A; sq.Q = SL_A; sq.alpha = 1.0; sq.nout = 1;
     sq.o[0].dst = SL_T; sq.o[0].cv = 1.0; sq.o[0].cI = 0.0; sq.o[0].nt = 0;
-    // SL_A -> src and SL_T -> dst for this step
-    const int rc = run_step(h, sq, N, src, dst, flags, (k + 1 == s) ? h->dflag : nullptr, stream, upper);
+    // SL_A -> src and SL_T -> dst for this step; the last n_fp64 squarings on the FP64 pipe
+    const int n_fp64 = (flags >> 16) & 0xF;
+    const int fl = (k >= s - n_fp64) ? ((flags & ~BBC_PREC_MASK & ~0xF00) | BBC_PREC_FP64) : flags;
+    const int rc = run_step(h, sq, N, src, dst, fl, (k + 1 == s) ? h->dflag : nullptr, stream, upper);
     if (rc) return rc;
     if (int rc2 = exact(dst, s - k - 1)) return rc2;
     src = dst;
@@ -548,10 +563,7 @@ int bbc_workspace_size(bbc_handle h, int64_t N, int dtype, int flags, size_t* by
   int rc = check_flags(flags);
   if (rc) return rc;
   size_t b = (size_t)NUM_WORK_SLOTS * N * N * sizeof(double) + norm1_partial_len(N) * sizeof(double);
-  if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
-    const int k = (flags >> 8) & 0xF;
-    b += ozaki_workspace_bytes(N, k ? k : 7);
-  }
+  if (split_prec(flags)) b += ozaki_workspace_bytes(N, split_slices(flags));
   *bytes = b;
   return BBC_OK;
 }
@@ -657,7 +669,7 @@ int bbc_gemm(bbc_handle h, const double* dP, const double* dQ, int64_t N, double
   e.o[0].out = dC;
   e.o[0].cv = 1.0;
   cudaStream_t st = (cudaStream_t)stream;
-  const bool ozaki = (flags & BBC_PREC_MASK) == BBC_PREC_OZAKI;
+  const bool ozaki = split_prec(flags);
   if (ozaki) BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
   if ((rc = launch_product(h, dP, dQ, N, 1.0, e, flags, st, (flags & BBC_UPPER) != 0))) return rc;
   if (ozaki) {  // report a non-finite operand or an expired device wait

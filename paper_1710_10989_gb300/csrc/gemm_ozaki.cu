@@ -43,6 +43,7 @@
 // timeout in the status word, lets its copies and MMAs finish (bounded again),
 // frees TMEM and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -159,9 +160,29 @@ __device__ __forceinline__ void digits(long long X, uint32_t (&out)[K]) {
   out[0] = bf16_of_int((int)X);
 }
 
+// The literal split (BBC_PREC_SPLIT): x scaled by the row's (column's) power of
+// two 2^-(Emax - 1021), so |x| < 1/2, then K BF16 terms, each the rounding to
+// nearest of what the earlier terms left (floating-point splitting, no common
+// fixed point: each term keeps its own exponent).
+template <int K>
+__device__ __forceinline__ void float_terms(double x, int Emax, uint32_t (&out)[K]) {
+  double r = ldexp(x, -(Emax - 1021));
+#pragma unroll
+  for (int p = 0; p < K; ++p) {
+    const __nv_bfloat16 b = __double2bfloat16(r);
+    out[p] = (uint32_t)__bfloat16_as_ushort(b);
+    r -= (double)__bfloat162float(b);
+  }
+}
+template <int K, bool FLT>
+__device__ __forceinline__ void terms(double x, int Emax, uint32_t (&out)[K]) {
+  if (FLT) float_terms<K>(x, Emax, out);
+  else digits<K>(fixed_point(x, Emax, K), out);
+}
+
 // P (N x N, row-major FP64) -> K slice planes [K][Rp][Kp] of BF16 digits with
 // row exponents. One warp per row; padding rows/columns are written as zeros.
-template <int K>
+template <int K, bool FLT>
 __global__ void __launch_bounds__(256)
 k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, uint16_t* __restrict__ planes,
              int* __restrict__ erow, double* __restrict__ pdiag, unsigned int* __restrict__ status) {
@@ -196,8 +217,8 @@ k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, ui
     uint32_t d0[K], d1[K];
     const double x0 = (row < N && j < N && j != row && !bad) ? __ldg(P + row * N + j) : 0.0;
     const double x1 = (row < N && j + 1 < N && j + 1 != row && !bad) ? __ldg(P + row * N + j + 1) : 0.0;
-    digits<K>(fixed_point(x0, Emax, K), d0);
-    digits<K>(fixed_point(x1, Emax, K), d1);
+    terms<K, FLT>(x0, Emax, d0);
+    terms<K, FLT>(x1, Emax, d1);
     const size_t idx = ((size_t)row * Kp + j) >> 1;
 #pragma unroll
     for (int p = 0; p < K; ++p) out[p * (plane >> 1) + idx] = d0[p] | (d1[p] << 16);
@@ -221,7 +242,7 @@ k_col_maxexp(const double* __restrict__ Q, int64_t N, int64_t rows_per, int* __r
 
 // Q (N x N) -> K planes of Q^T digits [K][Rp][Kp] (plane row j holds column j of
 // Q) with column exponents fcol. 32 x 32 tiles transposed through shared memory.
-template <int K>
+template <int K, bool FLT>
 __global__ void __launch_bounds__(256)
 k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, const int* __restrict__ fexp,
              uint16_t* __restrict__ planes, int* __restrict__ fcol, double* __restrict__ qdiag,
@@ -245,7 +266,7 @@ k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, co
     const int64_t i = i0 + il;
     const double x = (i < N && j < N && i != j && !bad) ? __ldg(Q + i * N + j) : 0.0;
     uint32_t d[K];
-    digits<K>(fixed_point(x, Emax, K), d);
+    terms<K, FLT>(x, Emax, d);
 #pragma unroll
     for (int p = 0; p < K; ++p) tile[p][tx][il] = (uint16_t)d[p];
   }
@@ -470,9 +491,9 @@ __device__ __forceinline__ TileWork tile_work(int t, const uint32_t* __restrict_
 struct ItemCursor {
   int g, p, c;
   bool low;
-  int nch;
-  __device__ ItemCursor(int k, int nch_) : p(0), c(0), nch(nch_) {
-    low = k > G_EXACT;
+  int nch, glo;  // glo: lowest low group (G_EXACT; 0 for the literal split, which has no exact groups)
+  __device__ ItemCursor(int k, int nch_, int glo_) : p(0), c(0), nch(nch_), glo(glo_) {
+    low = k > glo;
     g = low ? k - 1 : 0;
   }
   __device__ void advance() {
@@ -482,7 +503,7 @@ struct ItemCursor {
     p = 0;
     if (!low) {
       ++g;
-    } else if (--g < G_EXACT) {
+    } else if (--g < glo) {
       low = false;
       g = 0;
     }
@@ -494,7 +515,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
              const int* __restrict__ erow, const int* __restrict__ fcol, const double* __restrict__ P,
              const double* __restrict__ Q, const double* __restrict__ pdiag, const double* __restrict__ qdiag,
              int64_t N, double alpha, int nslices, int nksteps, int tiles_m, int tiles_n, const Epilogue e,
-             unsigned int* __restrict__ status, const uint32_t* __restrict__ tile_list, int upper) {
+             unsigned int* __restrict__ status, const uint32_t* __restrict__ tile_list, int upper, int literal) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   uint8_t* smA = smem;
@@ -506,7 +527,9 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   const uint32_t rank = cluster_rank();
   const int cid = cluster_index(), ncl = cluster_count();
   const int ntiles = tiles_m * tiles_n;
-  const int gh = min(nslices, G_EXACT);                           // high groups 0..gh-1
+  // high groups 0..gh-1; the literal split has none: every pair accumulates in FP32
+  const int glo = literal ? 0 : G_EXACT;
+  const int gh = min(nslices, glo);
   const int pairs_h = gh * (gh + 1) / 2;                            // high slice pairs
   const int pairs_l = nslices * (nslices + 1) / 2 - pairs_h;        // low slice pairs
 
@@ -548,7 +571,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       const int arow = w.mp * 2 * TILE + (int)rank * TILE;
       const int brow = w.nt * TILE + (int)rank * (TILE / 2);
       const int nunits = (pairs_h + pairs_l) * w.nch;
-      ItemCursor cur(nslices, w.nch);
+      ItemCursor cur(nslices, w.nch, glo);
       for (int idx = 0; idx < nunits && ok; ++idx, cur.advance()) {
         const int ca = w.c_lo + cur.c;
         const int ks1 = min(w.ks_hi, (ca + 1) * CHUNK_STEPS);
@@ -590,13 +613,13 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           if (!mbar_wait_warp_cl(&sh->low_empty[lb], ((uint32_t)(ln >> 1) & 1u) ^ 1u, cta_err)) { ok = false; break; }
           tc_fence_after();
         }
-        ItemCursor cur(nslices, w.nch);
+        ItemCursor cur(nslices, w.nch, glo);
         for (int idx = 0; idx < nunits && ok; ++idx, cur.advance()) {
           uint32_t d_tmem;
           int b = 0, kind0;  // first MMA: 0 fresh, 1 accumulate, 2 accumulate onto 2^-8 x the sum so far
           if (cur.low) {
             d_tmem = tmem + 256u + (uint32_t)(lb * TILE);
-            kind0 = (idx == 0) ? 0 : ((cur.p == 0 && cur.c == 0) ? 2 : 1);
+            kind0 = (idx == 0) ? 0 : ((!literal && cur.p == 0 && cur.c == 0) ? 2 : 1);
           } else {
             b = hc & 1;
             if (!mbar_wait_warp_cl(&sh->acc_empty[b], ((uint32_t)(hc >> 1) & 1u) ^ 1u, cta_err)) { ok = false; break; }
@@ -721,9 +744,16 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           for (int i = 0; i < 8; ++i) {
             const int64_t col = col0 + 8 * pc + i;
             if (col < N) {
-              double v = (double)R[8 * pc + i];  // rounds to 53 bits when |R| >= 2^53
-              if (nL > 0) v = fma((double)__uint_as_float(lw[i]), 0.00390625, v);
-              const int ex = er + fcol[col] - 16 - 8 * (G_EXACT - 1);
+              double v;
+              int ex;
+              if (literal) {  // the FP32 sum of all term products, scaled back
+                v = (nL > 0) ? (double)__uint_as_float(lw[i]) : 0.0;
+                ex = er + fcol[col];
+              } else {
+                v = (double)R[8 * pc + i];  // rounds to 53 bits when |R| >= 2^53
+                if (nL > 0) v = fma((double)__uint_as_float(lw[i]), 0.00390625, v);
+                ex = er + fcol[col] - 16 - 8 * (G_EXACT - 1);
+              }
               const double scl = (ex >= -1022 && ex <= 1023) ? __longlong_as_double((long long)(ex + 1023) << 52)
                                                             : ldexp(1.0, ex);
               // the deflated diagonals: + P_ii Q_ij + P_ij Q_jj - [i = j] P_ii Q_jj
@@ -783,11 +813,11 @@ bool make_map(CUtensorMap* m, void* base, int64_t Rp, int64_t Kp, int k, int box
 
 int64_t padded(int64_t N) { return (N + TILE - 1) / TILE * TILE; }
 
-template <int K>
+template <int K, bool FLT>
 cudaError_t split_both(const double* P, const double* Q, int64_t N, int64_t Rp, uint16_t* Ps, uint16_t* Qs,
                        int* erow, int* fcol, int* fexp, double* pdiag, double* qdiag, unsigned int* status,
                        cudaStream_t st) {
-  k_split_rows<K><<<(unsigned)((Rp + 7) / 8), 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
+  k_split_rows<K, FLT><<<(unsigned)((Rp + 7) / 8), 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
   cudaError_t err = cudaMemsetAsync(fexp, 0, (size_t)N * sizeof(int), st);
   if (err != cudaSuccess) return err;
   const int64_t colblocks = (N + 255) / 256;
@@ -795,7 +825,7 @@ cudaError_t split_both(const double* P, const double* Q, int64_t N, int64_t Rp, 
   slabs = std::min<int64_t>(slabs, (N + 63) / 64);
   const int64_t rows_per = (N + slabs - 1) / slabs;
   k_col_maxexp<<<dim3((unsigned)colblocks, (unsigned)slabs), 256, 0, st>>>(Q, N, rows_per, fexp);
-  k_split_cols<K><<<dim3((unsigned)(Rp / 32), (unsigned)(Rp / 32)), 256, 0, st>>>(Q, N, Rp, Rp, fexp, Qs, fcol,
+  k_split_cols<K, FLT><<<dim3((unsigned)(Rp / 32), (unsigned)(Rp / 32)), 256, 0, st>>>(Q, N, Rp, Rp, fexp, Qs, fcol,
                                                                                    qdiag, status);
   return cudaGetLastError();
 }
@@ -851,19 +881,25 @@ OzLayout layout(void* work, int64_t N, int slices) {
 }
 }  // namespace
 
+template <bool FLT>
+cudaError_t split_k(const double* P, const double* Q, int64_t N, int slices, const OzLayout& L, unsigned int* flag,
+                    cudaStream_t st) {
+  switch (slices) {
+    case 2: return split_both<2, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 3: return split_both<3, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 4: return split_both<4, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 5: return split_both<5, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 6: return split_both<6, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 7: return split_both<7, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    default: return split_both<8, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+  }
+}
+
 cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices, void* work, unsigned int* flag,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool literal) {
   if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
   const OzLayout L = layout(work, N, slices);
-  switch (slices) {
-    case 2: return split_both<2>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 3: return split_both<3>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 4: return split_both<4>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 5: return split_both<5>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 6: return split_both<6>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 7: return split_both<7>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    default: return split_both<8>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-  }
+  return literal ? split_k<true>(P, Q, N, slices, L, flag, st) : split_k<false>(P, Q, N, slices, L, flag, st);
 }
 
 namespace {
@@ -927,7 +963,8 @@ const std::vector<uint32_t>& upper_tile_order(int tiles_m, int tiles_n, int nkst
 }
 
 cudaError_t launch_pair(const OzLayout& L, const double* P, const double* Q, int64_t N, double alpha,
-                        const Epilogue& e, int slices, unsigned int* flag, cudaStream_t st, bool upper) {
+                        const Epilogue& e, int slices, unsigned int* flag, cudaStream_t st, bool upper,
+                        bool literal) {
   CUtensorMap ta, tb;
   if (!make_map(&ta, L.Ps, L.Rp, L.Rp, slices, TILE) || !make_map(&tb, L.Qs, L.Rp, L.Rp, slices, TILE / 2))
     return cudaErrorNotSupported;
@@ -958,14 +995,14 @@ cudaError_t launch_pair(const OzLayout& L, const double* P, const double* Q, int
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_ozaki_pair, ta, tb, (const int*)L.erow, (const int*)L.fcol, P, Q,
                             (const double*)L.pdiag, (const double*)L.qdiag, N, alpha, slices, (int)(L.Rp / KSTEP),
-                            tiles_m, tiles_n, e, flag, list, upper ? 1 : 0);
+                            tiles_m, tiles_n, e, flag, list, upper ? 1 : 0, literal ? 1 : 0);
 }
 }  // namespace
 
 cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e, int slices,
-                          void* work, unsigned int* flag, cudaStream_t st, bool upper) {
+                          void* work, unsigned int* flag, cudaStream_t st, bool upper, bool literal) {
   if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
-  return launch_pair(layout(work, N, slices), P, Q, N, alpha, e, slices, flag, st, upper);
+  return launch_pair(layout(work, N, slices), P, Q, N, alpha, e, slices, flag, st, upper, literal);
 }
 
 }  // namespace bbc

@@ -94,10 +94,13 @@ cudaError_t norm1_noalloc(const double* A, int64_t N, double* dNorm, cudaStream_
 // into `work`; ozaki_product then forms alpha * (P Q) from them with the
 // fused epilogue.
 size_t ozaki_workspace_bytes(int64_t N, int slices);
+// literal: the plain floating-point split of BBC_PREC_SPLIT (each term the BF16
+// rounding of the remainder) with every term product accumulated in FP32.
 cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices, void* work,
-                        unsigned int* flag, cudaStream_t st);
+                        unsigned int* flag, cudaStream_t st, bool literal = false);
 cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
-                          int slices, void* work, unsigned int* flag, cudaStream_t st, bool upper = false);
+                          int slices, void* work, unsigned int* flag, cudaStream_t st, bool upper = false,
+                          bool literal = false);
 bool ozaki_supported(int64_t N);
 
 // Solve M X = B in place (X overwrites B, M is destroyed), N <= 1024 (pade.cu).

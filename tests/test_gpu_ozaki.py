@@ -160,3 +160,41 @@ def test_split_product_is_closer_to_exact_than_fp64(h, api):
         ef.append(abs(float(Fraction(float(Cf[i, j])) - exact)) / scale)
     assert max(es) < 1e-16                   # ~ the final rounding only
     assert max(es) < max(ef)
+
+
+# ---- the literal split (BBC_PREC_SPLIT) and FP64 final squarings ----------------------------------
+
+def test_literal_split_products(h, api):
+    """Plain floating-point BF16 splitting with FP32 accumulation: about 8 bits per
+    term until the FP32 sums limit it; far from the exact form at the same k."""
+    n = 512
+    P = W.gaussian(n, 71, None)
+    Q = W.gaussian(n, 72, None)
+    ref = O.gemm(P, Q)
+    err = {}
+    for k in (2, 3, 4):
+        C = empty_like_dev(n)
+        h.gemm(to_dev(P), to_dev(Q), C, api.PREC_SPLIT | api.ozaki_slices(k))
+        err[k] = rel_fro(to_host(C), ref)
+    assert 1e-9 < err[3] < 1e-5, err
+    assert err[2] > err[3], err
+    assert err[4] > 0.5 * err[3], err   # a fourth term buys nothing: the FP32 sums set the floor
+    C = empty_like_dev(n)
+    h.gemm(to_dev(P), to_dev(Q), C, oz(api, 7))
+    assert rel_fro(to_host(C), ref) < 1e-15   # the exact form, for contrast
+
+
+def test_literal_split_expm_and_fp64_last_squarings(h, api):
+    A = W.gaussian(300, 73, 20.0)      # s = 5
+    want, oi = O.expm(A, "new")
+    out = empty_like_dev(300)
+    info = h.expm(to_dev(A), out, 0.0, api.PREC_SPLIT)
+    e_lit = rel_fro(to_host(out), want)
+    info2 = h.expm(to_dev(A), out, 0.0, api.PREC_SPLIT | api.square_fp64_last(oi.s))
+    e_last = rel_fro(to_host(out), want)
+    info3 = h.expm(to_dev(A), out, 0.0, api.PREC_FP64 | api.square_fp64_last(2))
+    e_fp64 = rel_fro(to_host(out), want)
+    assert (info.m, info.s) == (info2.m, info2.s) == (info3.m, info3.s) == (oi.m, oi.s)
+    assert 1e-10 < e_lit < 1e-4
+    assert e_last < e_lit            # FP64 squarings stop the 2^s amplification
+    assert e_fp64 < 1e-12            # an all-FP64 run is unchanged by the flag
