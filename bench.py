@@ -396,6 +396,13 @@ def run_batch(args, torch, dist, api, rank, world, local, mats):
     h = api.Handle(local)
     split = args.precision == "ozaki"
     h.batch_reserve(256, api.PREC_OZAKI if split else 0)
+    tuning = None
+    if split:  # the autotuner's per-size product family and grid (measured here, or restored from its cache)
+        from paper_1710_10989_gb300 import tuner
+        t0 = time.perf_counter()
+        mask, ctas = tuner.tuned(h, 256)
+        tuning = {"split_mask": f"0x{mask:08x}", "ctas": ctas, "seconds": round(time.perf_counter() - t0, 2),
+                  "split_buckets_N": [8 * (b + 1) for b in range(32) if (mask >> b) & 1]}
     sel_flag = {"plain": 0, "learned": api.SELECT_LEARNED, "alpha": api.SELECT_ALPHA}[args.selector]
     if args.selector == "learned":
         SEL.install(h)
@@ -475,8 +482,12 @@ def run_batch(args, torch, dist, api, rank, world, local, mats):
     h.close()
     pk = peaks()
     if split:
-        # executed work: 10 BF16 slice products per product on the warp-level MMAs (padding to 32 excluded)
-        executed = 10 * flops / (ms / args.steps / 1e3) / 1e12
+        # executed work: 10 BF16 slice products per product on the warp-level MMAs (padding to 32 excluded),
+        # counted for the matrices whose size bucket the autotuner gave split products
+        mask_v = int(tuning["split_mask"], 16) if tuning else 0xFFFFFFFF
+        flops_split = sum(2.0 * A.shape[0] ** 3 * i["products"] for A, i in zip(mats, infos)
+                          if A.shape[0] <= 256 and (mask_v >> ((A.shape[0] - 1) // 8)) & 1)
+        executed = 10 * flops_split / (ms / args.steps / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": executed, "peak": 0.32 * pk.get("bf16_tflops", 1899.1),
                 "unit": "TFLOP/s", "frac": executed / (0.32 * pk.get("bf16_tflops", 1899.1)), "traffic": None,
                 "kernel": "k_batched_expm (4-slice BF16 mma.sync products)",
@@ -498,6 +509,7 @@ def run_batch(args, torch, dist, api, rank, world, local, mats):
                    "parallelism": f"{world} ranks, LPT shards of the batch, no collective" if world > 1 else "single",
                    "precision": args.precision, "selector": args.selector,
                    "graph": "one persistent kernel per step, replayed from a CUDA graph", "u": "2^-53",
+                   "autotuner": tuning,
                    "l2": "per-CTA binary64 work slots; inputs+outputs 3.7 GB per step (larger than L2)"},
         "tflops_logical": logical,
         "selector_stats": {"fallback_rate": float(np.mean(sel == 4)), "accepted_by_norm": float(np.mean(sel == 2)),

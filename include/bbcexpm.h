@@ -212,6 +212,23 @@ int bbc_batch_order(const int64_t* hNs, int64_t count, int64_t* hOrder);
 int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, int64_t count, void* const* dOut,
                      int dtype, double tol, int flags, void* stream, bbc_info* dInfo);
 
+/* Autotuner of bbc_expm_batched (needs bbc_batch_reserve with BBC_PREC_OZAKI).
+ * Times, on this GPU, calibration batches the library generates itself (entries
+ * uniform on [-1, 1), 1-norm about 5, two matrices per resident CTA per size):
+ *  1. for every size bucket ((N - 1) / 8 for N <= min(max_n, 256)) whether split
+ *     products or FP64 products are faster, and
+ *  2. the persistent grid, one or two CTAs per SM, on a largest-first mix of all
+ *     buckets (eight matrices per resident CTA) with the choices of 1.
+ * Keeps the result in the handle for later split-precision batched calls and
+ * returns it (split_mask: bit b set = bucket b uses split products; ctas: CTA
+ * count), so that callers can cache it and restore it with bbc_batch_set_tuning.
+ * Allocates and frees temporary device memory (about 1 GB for max_n = 256 on a
+ * 152-SM GPU) and waits for the stream; takes seconds. */
+int bbc_batch_tune(bbc_handle h, int64_t max_n, double tol, void* stream, uint32_t* split_mask, int* ctas);
+
+/* Install a tuning (from bbc_batch_tune, possibly cached): ctas 0 = the reserved count. */
+int bbc_batch_set_tuning(bbc_handle h, uint32_t split_mask, int ctas);
+
 /* ---- the (m, s)-proposing network (SURVEY-level extension: the paper selects
  * (m, s) from ||A||_1 alone; a proposal is only ever used once the backward-error
  * bound certifies it). A 2-hidden-layer ReLU MLP in FP32 with parameters as one

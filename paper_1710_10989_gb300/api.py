@@ -84,6 +84,8 @@ _SIGS = {
     "bbc_profile_enable": [_vp, _int],
     "bbc_profile_read": [_vp, _int, ctypes.POINTER(ctypes.c_int64), _dp],
     "bbc_profile_flops": [_vp, _int, _dp],
+    "bbc_batch_tune": [_vp, _i64, _dbl, _vp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int)],
+    "bbc_batch_set_tuning": [_vp, ctypes.c_uint32, _int],
 }
 KERNEL_PRODUCT, KERNEL_NORM, KERNEL_LINCOMB, KERNEL_SPLIT, KERNEL_BATCHED, KERNEL_ALL = 0, 1, 2, 3, 4, -1
 DTYPE_F64, DTYPE_F32 = 0, 1
@@ -188,6 +190,16 @@ class Handle:
         ms = ctypes.c_double()
         _check(_lib.bbc_profile_read(self._h, kind, ctypes.byref(n), ctypes.byref(ms)))
         return n.value, ms.value
+
+    def batch_tune(self, max_n: int, tol: float = 0.0, stream=None) -> tuple[int, int]:
+        """Time the batched path's choices on this GPU; returns (split_mask, ctas)."""
+        mask = ctypes.c_uint32()
+        ctas = ctypes.c_int()
+        _check(_lib.bbc_batch_tune(self._h, max_n, tol, _stream(stream), ctypes.byref(mask), ctypes.byref(ctas)))
+        return mask.value, ctas.value
+
+    def batch_set_tuning(self, split_mask: int, ctas: int) -> None:
+        _check(_lib.bbc_batch_set_tuning(self._h, split_mask & 0xFFFFFFFF, ctas))
 
     def profile_flops(self, kind: int = KERNEL_ALL) -> float:
         """Algorithmic flops of a kernel class since profile_enable (products: 2 N^3

@@ -40,6 +40,8 @@ struct bbc_handle_s {
   BatchSelector selector = {};    // network for BBC_SELECT_LEARNED (mode 0: none installed)
   int batch_ctas = 0;
   bool batch_split = false;       // reservation includes the split-precision scratch
+  uint32_t batch_split_mask = 0xFFFFFFFFu;  // tuned: size buckets ((N-1)/8) that use split products
+  int batch_grid = 0;                       // tuned persistent CTA count (0: the reserved count)
   void* batch_work = nullptr;
   int64_t io_n = 0;               // N the host-call staging buffers are sized for
   double* io = nullptr;           // 4 * N * N doubles: device copies of two inputs and two outputs
@@ -845,6 +847,153 @@ int bbc_expm_host_many(bbc_handle h, const double* const* hA, const int64_t* Ns,
   return BBC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the batched path: which size buckets run split products and how
+// many persistent CTAs the launch uses, chosen by timing on this GPU.
+// ---------------------------------------------------------------------------
+namespace {
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+
+// Best of `reps` event-timed launches (after one warm-up) of the batched kernel.
+int time_batch(bbc_handle h, const void* const* dA, void* const* dOut, const int64_t* dNs, int64_t count,
+               const double* theta, int ctas, uint32_t mask, cudaStream_t st, int reps, float* best_ms) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  BBC_CUDA(cudaEventCreate(&a));
+  BBC_CUDA(cudaEventCreate(&b));
+  float best = 1e30f;
+  cudaError_t e = cudaSuccess;
+  for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
+    e = cudaEventRecord(a, st);
+    if (e == cudaSuccess)
+      e = batched_launch(dA, dOut, dNs, count, h->batch_nmax, BBC_DTYPE_F64, theta, h->batch_work, ctas, nullptr,
+                         st, nullptr, true, mask);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (r > 0 && ms < best) best = ms;  // r = 0 is the warm-up
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(e, "autotuner launch");
+  *best_ms = best;
+  return BBC_OK;
+}
+}  // namespace
+
+int bbc_batch_tune(bbc_handle h, int64_t max_n, double tol, void* stream, uint32_t* split_mask, int* ctas) {
+  int rc = begin(h);
+  if (rc) return rc;
+  const double u = tol > 0 ? tol : std::ldexp(1.0, -53);
+  if (!valid_u(u)) return fail(BBC_INVALID_ARG, "tol out of range [2^-60, 2^-5]");
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (!h->batch_work || !h->batch_split) return fail(BBC_INVALID_ARG, "reserve with BBC_PREC_OZAKI first");
+  if (max_n < 1 || max_n > h->batch_nmax) return fail(BBC_INVALID_ARG, "max_n beyond the reservation");
+  cudaStream_t st = (cudaStream_t)stream;
+  static const int deg[6] = {1, 2, 4, 8, 12, 18};
+  double theta[6];
+  for (int i = 0; i < 6; ++i) theta[i] = theta_cached(deg[i], u);
+  const int64_t nlim = std::min<int64_t>(max_n, 256);  // split products serve N <= 256
+  const int nb = (int)((nlim + 7) / 8);
+  const int64_t per = 2 * (int64_t)h->batch_ctas;      // matrices per bucket: every CTA gets two
+  // 1. per size bucket: split or FP64 products, whichever is faster here
+  DevBuf buf, ptrs, ns;
+  BBC_CUDA(cudaMalloc(&buf.p, (size_t)2 * per * nlim * nlim * sizeof(double)));
+  BBC_CUDA(cudaMalloc(&ptrs.p, (size_t)2 * per * sizeof(void*)));
+  BBC_CUDA(cudaMalloc(&ns.p, (size_t)per * sizeof(int64_t)));
+  std::vector<void*> hp(2 * per);
+  std::vector<int64_t> hn(per);
+  uint32_t mask = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int64_t N = std::min<int64_t>(8 * (b + 1), nlim);
+    double* in = static_cast<double*>(buf.p);
+    double* out = in + (size_t)per * N * N;
+    BBC_CUDA(calibration_matrices(in, N, per, 0x5eed0000ull + (uint64_t)b, 5.0, st));
+    for (int64_t i = 0; i < per; ++i) {
+      hp[i] = in + (size_t)i * N * N;
+      hp[per + i] = out + (size_t)i * N * N;
+      hn[i] = N;
+    }
+    BBC_CUDA(cudaMemcpyAsync(ptrs.p, hp.data(), hp.size() * sizeof(void*), cudaMemcpyHostToDevice, st));
+    BBC_CUDA(cudaMemcpyAsync(ns.p, hn.data(), hn.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    const void* const* dA = static_cast<const void* const*>(ptrs.p);
+    void* const* dO = static_cast<void* const*>(ptrs.p) + per;
+    float t_split = 0.f, t_fp64 = 0.f;
+    if ((rc = time_batch(h, dA, dO, static_cast<const int64_t*>(ns.p), per, theta, h->batch_ctas, 1u << b, st, 3,
+                         &t_split)))
+      return rc;
+    if ((rc = time_batch(h, dA, dO, static_cast<const int64_t*>(ns.p), per, theta, h->batch_ctas, 0u, st, 3,
+                         &t_fp64)))
+      return rc;
+    if (t_split < t_fp64) mask |= 1u << b;
+  }
+  for (int b = nb; b < 32; ++b) mask |= 1u << b;  // buckets not tuned keep the default
+  // 2. the persistent grid: one or two CTAs per SM, on a mix of every bucket large
+  //    enough (eight matrices per resident CTA) that the queue's tail does not decide
+  const int64_t mix_per = std::max<int64_t>(16, (8 * (int64_t)h->batch_ctas + nb - 1) / nb);
+  const int64_t mcount = mix_per * nb;
+  DevBuf mbuf, mptrs, mns;
+  size_t mdoubles = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int64_t N = std::min<int64_t>(8 * (b + 1), nlim);
+    mdoubles += (size_t)mix_per * N * N;
+  }
+  BBC_CUDA(cudaMalloc(&mbuf.p, 2 * mdoubles * sizeof(double)));
+  BBC_CUDA(cudaMalloc(&mptrs.p, (size_t)2 * mcount * sizeof(void*)));
+  BBC_CUDA(cudaMalloc(&mns.p, (size_t)mcount * sizeof(int64_t)));
+  std::vector<void*> mp(2 * mcount);
+  std::vector<int64_t> mn(mcount);
+  {
+    double* in = static_cast<double*>(mbuf.p);
+    double* out = in + mdoubles;
+    size_t off = 0;
+    int64_t k = 0;
+    for (int b = nb - 1; b >= 0; --b) {  // largest first, as bbc_batch_order would put them
+      const int64_t N = std::min<int64_t>(8 * (b + 1), nlim);
+      BBC_CUDA(calibration_matrices(in + off, N, mix_per, 0x5eed1000ull + (uint64_t)b, 5.0, st));
+      for (int64_t i = 0; i < mix_per; ++i, ++k) {
+        mp[k] = in + off + (size_t)i * N * N;
+        mp[mcount + k] = out + off + (size_t)i * N * N;
+        mn[k] = N;
+      }
+      off += (size_t)mix_per * N * N;
+    }
+  }
+  BBC_CUDA(cudaMemcpyAsync(mptrs.p, mp.data(), mp.size() * sizeof(void*), cudaMemcpyHostToDevice, st));
+  BBC_CUDA(cudaMemcpyAsync(mns.p, mn.data(), mn.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  const int grids[2] = {h->batch_ctas / 2, h->batch_ctas};
+  float best = 1e30f;
+  int best_grid = h->batch_ctas;
+  for (int g : grids) {
+    if (g < 1) continue;
+    float t = 0.f;
+    if ((rc = time_batch(h, static_cast<const void* const*>(mptrs.p), static_cast<void* const*>(mptrs.p) + mcount,
+                         static_cast<const int64_t*>(mns.p), mcount, theta, g, mask, st, 3, &t)))
+      return rc;
+    if (t < best) { best = t; best_grid = g; }
+  }
+  BBC_CUDA(cudaStreamSynchronize(st));
+  h->batch_split_mask = mask;
+  h->batch_grid = best_grid;
+  if (split_mask) *split_mask = mask;
+  if (ctas) *ctas = best_grid;
+  return BBC_OK;
+}
+
+int bbc_batch_set_tuning(bbc_handle h, uint32_t split_mask, int ctas) {
+  int rc = begin(h);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (ctas < 0 || (h->batch_ctas > 0 && ctas > h->batch_ctas))
+    return fail(BBC_INVALID_ARG, "CTA count beyond the reservation");
+  h->batch_split_mask = split_mask;
+  h->batch_grid = ctas;
+  return BBC_OK;
+}
+
 int bbc_mlp_sizes(int in, int hid, int out, int64_t B, int64_t* n_params, int64_t* ws_floats) {
   if (in < 1 || hid < 1 || out < 1 || B < 0 || !n_params || !ws_floats) return fail(BBC_INVALID_ARG, "bad MLP sizes");
   *n_params = mlp_param_count(in, hid, out);
@@ -1003,8 +1152,9 @@ int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, in
   }
   cudaStream_t st = (cudaStream_t)stream;
   LaunchScope scope(h, BBC_KERNEL_BATCHED, st);
+  const int ctas = (h->batch_grid > 0 && h->batch_grid <= h->batch_ctas) ? h->batch_grid : h->batch_ctas;
   const cudaError_t e = batched_launch(dA, dOut, dNs, count, h->batch_nmax, dtype, theta, h->batch_work,
-                                       h->batch_ctas, dInfo, st, psel, split);
+                                       ctas, dInfo, st, psel, split, h->batch_split_mask);
   if (e != cudaSuccess) return cuda_fail(e, "batched launch");
   return BBC_OK;
 }

@@ -92,6 +92,7 @@ struct BatchArgs {
   float* feat_out;         // data mode: count x NFEAT
   double* norms_out;       // data mode: count x 4
   int prec;                // 0: products on the FP64 pipe; 1: 4-slice BF16 mma.sync products (N <= 256)
+  uint32_t split_mask;     // prec 1: bit b set = matrices with (N - 1) / 8 == b use split products
   uint32_t* ozwork;        // per-CTA slice scratch, OZB_WORDS words each (prec 1)
 };
 
@@ -364,7 +365,7 @@ __device__ void block_lincomb(int N, const Epilogue& e) {
 // operands are finite), else the FP64 pipe.
 __device__ void block_product(const BatchArgs& a, const double* P, const double* Q, int N, double alpha,
                               const Epilogue& e, GemmSmem& sm, OzbSmem& oz) {
-  if (a.prec == 1 && N <= OZB_NMAX) {
+  if (a.prec == 1 && N <= OZB_NMAX && ((a.split_mask >> ((N - 1) >> 3)) & 1u)) {
     const int Np = (N + 31) / 32 * 32;
     uint32_t* Ps = a.ozwork + (size_t)blockIdx.x * OZB_WORDS;
     uint32_t* Qt = Ps + OZB_WORDS / 2;
@@ -805,7 +806,7 @@ cudaError_t batched_upload_programs() {
 
 cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t* Ns, int64_t count, int64_t nmax,
                            int dtype, const double* theta, void* work, int ctas, bbc_info* info, cudaStream_t st,
-                           const BatchSelector* sel, bool split) {
+                           const BatchSelector* sel, bool split, uint32_t split_mask) {
   static const int deg[BATCH_PROGS] = {1, 2, 4, 8, 12, 18};
   static const int prod[BATCH_PROGS] = {0, 1, 2, 3, 4, 5};
   BatchArgs a = {};
@@ -820,6 +821,7 @@ cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t
   a.work = reinterpret_cast<double*>(static_cast<char*>(work) + 256);
   a.info = info;
   a.prec = split ? 1 : 0;
+  a.split_mask = split_mask;
   a.ozwork = split ? reinterpret_cast<uint32_t*>(static_cast<char*>(work) + 256 +
                                                  (size_t)ctas * BATCH_SLOTS * nmax * nmax * sizeof(double))
                    : nullptr;
@@ -841,6 +843,27 @@ cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t
   cudaError_t err = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
   k_batched_expm<<<ctas, BATCH_THREADS, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Calibration matrices for the batched autotuner: count matrices of size N with
+// entries uniform on [-1, 1) from a counter-based hash (splitmix64 of seed and
+// index), scaled so that every column sum of |a_ij| is about 2 norm1 / N * N / 2
+// = norm1 (the 1-norm, hence (m, s), sits near the chosen value).
+__global__ void k_calibration(double* out, int64_t N, int64_t count, uint64_t seed, double norm1) {
+  const int64_t total = N * N * count;
+  const double scale = 2.0 * norm1 / (double)N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    out[i] = scale * ((double)(z >> 11) * 0x1.0p-53 * 2.0 - 1.0);
+  }
+}
+
+cudaError_t calibration_matrices(double* out, int64_t N, int64_t count, uint64_t seed, double norm1, cudaStream_t st) {
+  k_calibration<<<1216, 256, 0, st>>>(out, N, count, seed, norm1);
   return cudaGetLastError();
 }
 

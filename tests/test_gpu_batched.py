@@ -159,3 +159,32 @@ def test_batch_split_learned_all_three(api):
         tol = 1e-12 if A.shape[0] > 256 else 1e-6
         assert rel_fro(o.cpu().numpy(), want) < tol, (A.shape, inf)
     hh.close()
+
+
+def test_autotuner_choice_keeps_parity(api):
+    """bbc_batch_tune times split against FP64 products per size bucket and the
+    grid size; whatever it picks, the batch still matches the oracle."""
+    import torch
+    h = api.Handle(0)
+    h.batch_reserve(64, api.PREC_OZAKI)
+    mask, ctas = h.batch_tune(64)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert ctas in (sms, 2 * sms)
+    assert mask >> 8 == (0xFFFFFFFF >> 8)          # buckets above max_n keep the default
+    mats = [W.gaussian(n, 300 + n, 0.5 + n / 16) for n in (64, 8, 33, 17, 50, 64, 1, 40)]
+    ins = [torch.from_numpy(A).cuda() for A in mats]
+    outs = [torch.empty_like(x) for x in ins]
+    b = api.Batch(ins, outs)
+    h.expm_batched(b, flags=api.PREC_OZAKI)
+    torch.cuda.synchronize()
+    for A, out, inf in zip(mats, outs, b.infos()):
+        want, oi = O.expm(A, "new")
+        assert inf["status"] == 0 and (inf["m"], inf["s"]) == (oi.m, oi.s)
+        assert rel_fro(out.cpu().numpy(), want) < 1e-6
+    h.batch_set_tuning(0, 0)                         # FP64 products everywhere, reserved grid
+    h.expm_batched(api.Batch(ins, outs), flags=api.PREC_OZAKI)
+    torch.cuda.synchronize()
+    for A, out in zip(mats, outs):
+        want, _ = O.expm(A, "new")
+        assert rel_fro(out.cpu().numpy(), want) < 1e-12
+    h.close()
