@@ -305,7 +305,7 @@ k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, co
 // warps), which is why TMEM loads go 16 (drain) and 8 (epilogue) columns at a time.
 // TMEM columns per CTA: [0,128) and [128,256) high buffers, [256,384) and [384,512)
 // low buffers.
-constexpr int P_STAGES = 9;
+constexpr int P_STAGES = 8;
 constexpr int P_A_BYTES = TILE * KSTEP * 2;          // 128 rows of a P slice plane
 constexpr int P_B_BYTES = (TILE / 2) * KSTEP * 2;    // 64 rows of a Q^T slice plane
 constexpr int P_STAGE_BYTES = P_A_BYTES + P_B_BYTES;
@@ -437,6 +437,7 @@ struct PairShared {
   uint64_t mma_done;
   uint32_t tmem_base;
   int err;
+  double epi[P_DRAIN_WARPS][32 * 9];  // per drain warp: 32 rows x 8 columns of results (rows padded to 9)
 };
 constexpr size_t PAIR_SMEM_BYTES = (size_t)P_STAGES * P_STAGE_BYTES + sizeof(PairShared) + 1024;
 
@@ -725,8 +726,14 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           for (int64_t col = col0; col < min(N, col0 + 64); ++col) zero_epilogue(e, N, row, col);
         continue;
       }
+      // Each pass takes 8 columns: the warp's 32 threads (one row each) rebuild the
+      // scaled slice sums and stage them in shared memory; then 8 threads per row
+      // (4 rows per access, 64 contiguous bytes each) add the deflation terms and
+      // run the fused epilogue, so its FP64 loads and stores move whole sectors.
       const int er = (row < N) ? erow[row] : 0;
-      const double pii = (row < N) ? pdiag[row] : 0.0;
+      double* stage = sh->epi[warp - 2];
+      const int tr = lane >> 3, tc = lane & 7;
+      const int64_t rbase = row - lane;
 #pragma unroll
       for (int pc = 0; pc < 8; ++pc) {
         uint32_t lw[8];
@@ -739,32 +746,41 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             if (lane == 0) mbar_arrive_cluster(peer_addr(&sh->low_empty[lb], 0));
           }
         }
-        if (row < N) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int64_t col = col0 + 8 * pc + i;
-            if (col < N) {
-              double v;
-              int ex;
-              if (literal) {  // the FP32 sum of all term products, scaled back
-                v = (nL > 0) ? (double)__uint_as_float(lw[i]) : 0.0;
-                ex = er + fcol[col];
-              } else {
-                v = (double)R[8 * pc + i];  // rounds to 53 bits when |R| >= 2^53
-                if (nL > 0) v = fma((double)__uint_as_float(lw[i]), 0.00390625, v);
-                ex = er + fcol[col] - 16 - 8 * (G_EXACT - 1);
-              }
-              const double scl = (ex >= -1022 && ex <= 1023) ? __longlong_as_double((long long)(ex + 1023) << 52)
-                                                            : ldexp(1.0, ex);
-              // the deflated diagonals: + P_ii Q_ij + P_ij Q_jj - [i = j] P_ii Q_jj
-              const double qjj = qdiag[col];
-              double d = fma(pii, __ldg(Q + row * N + col), (v * scl));
-              d = fma(__ldg(P + row * N + col), qjj, d);
-              if (row == col) d = fma(-pii, qjj, d);
-              apply_epilogue(e, N, row, col, alpha * d);
-            }
+        for (int i = 0; i < 8; ++i) {
+          const int64_t col = col0 + 8 * pc + i;
+          const int fc = (col < N) ? fcol[col] : 0;
+          double v;
+          int ex;
+          if (literal) {  // the FP32 sum of all term products, scaled back
+            v = (nL > 0) ? (double)__uint_as_float(lw[i]) : 0.0;
+            ex = er + fc;
+          } else {
+            v = (double)R[8 * pc + i];  // rounds to 53 bits when |R| >= 2^53
+            if (nL > 0) v = fma((double)__uint_as_float(lw[i]), 0.00390625, v);
+            ex = er + fc - 16 - 8 * (G_EXACT - 1);
+          }
+          const double scl = (ex >= -1022 && ex <= 1023) ? __longlong_as_double((long long)(ex + 1023) << 52)
+                                                        : ldexp(1.0, ex);
+          stage[lane * 9 + i] = v * scl;
+        }
+        __syncwarp();
+        const int64_t col = col0 + 8 * pc + tc;
+        const double qjj = (col < N) ? qdiag[col] : 0.0;
+#pragma unroll 2
+        for (int j = 0; j < 8; ++j) {
+          const int rl = tr + 4 * j;
+          const int64_t r = rbase + rl;
+          if (r < N && col < N) {
+            // the deflated diagonals: + P_ii Q_ij + P_ij Q_jj - [i = j] P_ii Q_jj
+            const double pii = pdiag[r];
+            double d = fma(pii, __ldg(Q + r * N + col), stage[rl * 9 + tc]);
+            d = fma(__ldg(P + r * N + col), qjj, d);
+            if (r == col) d = fma(-pii, qjj, d);
+            apply_epilogue(e, N, r, col, alpha * d);
           }
         }
+        __syncwarp();
       }
       if (nL > 0) ++ln;
     }
@@ -836,15 +852,11 @@ bool ozaki_supported(int64_t N) { return N >= 1 && N <= 16384; }
 
 // Layout of the workspace: 256 reserved bytes, erow[Rp], fcol[Rp], fexp[Rp], the
 // deflated diagonals pdiag[Rp], qdiag[Rp], then the P planes and the Q^T planes,
-// each k x Rp x Rp BF16, then the tile order of the triangular products.
-size_t tile_count(int64_t N) {
-  const int64_t Rp = padded(N);
-  return (size_t)((Rp + 2 * TILE - 1) / (2 * TILE)) * (size_t)(Rp / TILE);
-}
+// each k x Rp x Rp BF16.
 size_t ozaki_workspace_bytes(int64_t N, int slices) {
   const int64_t Rp = padded(N);
   return 256 + 3 * (size_t)Rp * sizeof(int) + 256 + 2 * (size_t)Rp * sizeof(double) + 256 +
-         2 * (size_t)slices * Rp * Rp * 2 + 256 + tile_count(N) * sizeof(uint32_t);
+         2 * (size_t)slices * Rp * Rp * 2;
 }
 
 namespace {
@@ -857,7 +869,6 @@ struct OzLayout {
   double* qdiag;
   uint16_t* Ps;
   uint16_t* Qs;
-  uint32_t* tiles;
 };
 OzLayout layout(void* work, int64_t N, int slices) {
   OzLayout L;
@@ -874,9 +885,6 @@ OzLayout layout(void* work, int64_t N, int slices) {
   off = (off + 255) / 256 * 256;
   L.Ps = reinterpret_cast<uint16_t*>(w + off);
   L.Qs = L.Ps + (size_t)slices * L.Rp * L.Rp;
-  off += 2 * (size_t)slices * L.Rp * L.Rp * 2;
-  off = (off + 255) / 256 * 256;
-  L.tiles = reinterpret_cast<uint32_t*>(w + off);
   return L;
 }
 }  // namespace
@@ -937,10 +945,13 @@ int pair_clusters() {
 // Tile order for triangular products, where tiles cost from nothing (below the
 // diagonal) to a full K sweep (top right): sorted by cost and dealt to the
 // clusters in a snake (cluster c takes list entries c, c + ncl, ...), so every
-// cluster gets about the same number of K steps. Kept per (tiles, clusters).
-const std::vector<uint32_t>& upper_tile_order(int tiles_m, int tiles_n, int nksteps, int ncl) {
+// cluster gets about the same number of K steps. Kept per (tiles, clusters) in
+// mapped pinned host memory that the kernel reads directly (each CTA reads a few
+// entries), so no copy is queued before a launch. Null when that memory is
+// unavailable.
+const uint32_t* upper_tile_order(int tiles_m, int tiles_n, int nksteps, int ncl) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int, int>, std::vector<uint32_t>> cache;
+  static std::map<std::tuple<int, int, int, int>, const uint32_t*> cache;
   std::lock_guard<std::mutex> lk(mu);
   auto key = std::make_tuple(tiles_m, tiles_n, nksteps, ncl);
   auto it = cache.find(key);
@@ -953,13 +964,25 @@ const std::vector<uint32_t>& upper_tile_order(int tiles_m, int tiles_n, int nkst
       v.push_back({std::max(0, hi - lo), ((uint32_t)mp << 16) | (uint32_t)nt});
     }
   std::stable_sort(v.begin(), v.end(), [](const T& a, const T& b) { return a.cost > b.cost; });
-  std::vector<uint32_t> out(v.size());
+  uint32_t* host = nullptr;
+  if (cudaHostAlloc((void**)&host, v.size() * sizeof(uint32_t), cudaHostAllocMapped | cudaHostAllocPortable) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
   const size_t n = v.size();
   for (size_t r0 = 0, round = 0; r0 < n; r0 += (size_t)ncl, ++round) {
     const size_t m = std::min((size_t)ncl, n - r0);
-    for (size_t c = 0; c < m; ++c) out[r0 + c] = v[r0 + ((round & 1) ? m - 1 - c : c)].code;
+    for (size_t c = 0; c < m; ++c) host[r0 + c] = v[r0 + ((round & 1) ? m - 1 - c : c)].code;
   }
-  return cache.emplace(key, std::move(out)).first->second;
+  uint32_t* dev = nullptr;
+  if (cudaHostGetDevicePointer((void**)&dev, host, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(host);
+    return nullptr;
+  }
+  cache.emplace(key, dev);
+  return dev;
 }
 
 cudaError_t launch_pair(const OzLayout& L, const double* P, const double* Q, int64_t N, double alpha,
@@ -973,14 +996,8 @@ cudaError_t launch_pair(const OzLayout& L, const double* P, const double* Q, int
   const int tiles_m = (int)((L.Rp + 2 * TILE - 1) / (2 * TILE));
   const int tiles_n = (int)(L.Rp / TILE);
   const int ncl = std::min(ncl_max, tiles_m * tiles_n);
-  const uint32_t* list = nullptr;
-  if (upper) {  // host order -> workspace (the vector lives in the cache, so the async copy may outlast this call)
-    const std::vector<uint32_t>& order = upper_tile_order(tiles_m, tiles_n, (int)(L.Rp / KSTEP), ncl);
-    const cudaError_t err = cudaMemcpyAsync(L.tiles, order.data(), order.size() * sizeof(uint32_t),
-                                            cudaMemcpyHostToDevice, st);
-    if (err != cudaSuccess) return err;
-    list = L.tiles;
-  }
+  // triangular products: the balanced tile order (without it, the plain raster order, equally correct)
+  const uint32_t* list = upper ? upper_tile_order(tiles_m, tiles_n, (int)(L.Rp / KSTEP), ncl) : nullptr;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
