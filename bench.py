@@ -67,7 +67,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("dense4096", "batch", "small", "large", "learned"), default="dense4096")
+    ap.add_argument("--workload", choices=("dense4096", "batch", "small", "large", "learned", "compare4096"),
+                    default="dense4096")
     ap.add_argument("--precision", choices=("ozaki", "fp64"), default="ozaki")
     ap.add_argument("--slices", type=int, default=6,
                     help="BF16 slices of the split-precision products (6: the fastest that keeps every "
@@ -175,6 +176,7 @@ METRICS = {
     "batch": "expm/s (batched exp(A), 20000 matrices N in 8..256, binary32 storage)",
     "small": "expm/s (single 64x64 exp(A), FP64, graph-replayed)",
     "learned": "expm/s (4096 held-out matrices N in 16..512, learned certified (m,s) selection)",
+    "compare4096": "expm/s (dense 4096x4096 exp(A), new Taylor scheme; Paterson-Stockmeyer and Pade r_26 beside it)",
 }
 WORKLOAD_DESC = {
     "dense4096": "dense{n}: 6 Gaussian N(0,1)/sqrt(N) (seeds 1-6) + 6 non-normal upper-triangular "
@@ -183,6 +185,7 @@ WORKLOAD_DESC = {
     "batch": "batch: N uniform on {{8,...,256}}, 1-norms log-uniform [1e-3, 1e2], half Gaussian, "
              "half V diag(lambda) V^-1 (cond(V)=1e3), seed 7",
     "small": "small64: N(0,1) seed 0, 1-norm 1.0, (m,s) = (18,0)",
+    "compare4096": "the six Gaussian matrices of dense4096 (seeds 1-6, 1-norms 0.01,0.1,1,5,20,100)",
     "learned": "4096 held-out matrices (GPU generator, seed 12): N uniform 16..512, 1-norms log-uniform "
                "[1e-3, 1e2], half Gaussian, half V diag(lambda) V^-1 (cond(V)=1e3)",
 }
@@ -521,6 +524,51 @@ def run_batch(args, torch, dist, api, rank, world, local, mats):
     }
 
 
+def run_compare(args, torch, dist, api, rank, world, local):
+    """The paper's comparison (Section 4, Fig. 1: cost of the new Taylor scheme
+    against Paterson-Stockmeyer and Pade r_26 over a range of norms) in wall time on
+    this GPU: each method's exp(A) of the six Gaussian 4096 matrices, with split
+    products (6 slices) and with FP64 products. The Pade solve is an LU with
+    partial pivoting (the paper's 4/3-product step)."""
+    mats = [W.dense_case(i) for i in range(len(W.DENSE_NORMS))]
+    h = api.Handle(local)
+    dA = [torch.from_numpy(A).cuda() for A in mats]
+    out = torch.empty_like(dA[0])
+    ref = torch.empty_like(dA[0])
+    stream = torch.cuda.current_stream()
+    split = api.PREC_OZAKI | api.ozaki_slices(6)
+    methods = [("new", api.SCHEME_NEW, split), ("ps", api.SCHEME_PS, split), ("pade26", api.SCHEME_PADE26, split),
+               ("new_fp64", api.SCHEME_NEW, api.PREC_FP64), ("pade26_fp64", api.SCHEME_PADE26, api.PREC_FP64)]
+    res = {}
+    for name, scheme, prec in methods:
+        rows = []
+        for A, a in zip(mats, dA):
+            h.expm(a, out, 0.0, scheme | prec, stream)       # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = h.expm(a, out, 0.0, scheme | prec, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            h.expm(a, ref, 0.0, api.SCHEME_NEW | split, stream)
+            diff = float(torch.linalg.norm(out - ref) / torch.linalg.norm(ref))
+            rows.append({"norm1": round(info.norm1, 4), "m": info.m, "s": info.s, "products": info.products,
+                         "ms": e0.elapsed_time(e1), "rel_fro_vs_new": diff})
+        res[name] = rows
+    ms_new = sum(r["ms"] for r in res["new"])
+    h.close()
+    return {
+        "metric": METRICS["compare4096"], "value": len(mats) / (ms_new / 1e3), "unit": "expm/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": ms_new, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x6-slices(exact sums)->f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC["compare4096"], "n": 4096, "u": "2^-53",
+                   "pade_solve": "LU with partial pivoting, N right-hand sides (cuSOLVER getrf/getrs above N = 1024)"},
+        "comparison": res,
+        "wall_time_ratio_new_over_pade": {p: sum(r["ms"] for r in res[a]) / sum(r["ms"] for r in res[b])
+                                          for p, a, b in (("split", "new", "pade26"),
+                                                          ("fp64", "new_fp64", "pade26_fp64"))},
+    }
+
+
 def run_small(args, torch, dist, api, rank, world, local):
     """One 64 x 64 matrix: graph-replayed single exp(A) (batched kernel, count 1)
     and the plain bbc_expm call (two host synchronisations)."""
@@ -687,6 +735,8 @@ def main():
         line = run_small(args, torch, dist, api, rank, world, local)
     elif args.workload == "learned":
         line = run_learned(args, torch, dist, api, rank, world, local)
+    elif args.workload == "compare4096":
+        line = run_compare(args, torch, dist, api, rank, world, local)
     else:
         line = run_dense(args, torch, dist, api, rank, world, local)
     if rank == 0:

@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     raise RuntimeError("nvcc failed: " + " ".join(cmd))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
+        subprocess.run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-ldl"], check=True)
         os.replace(tmp, LIB)
     return LIB
 

@@ -420,7 +420,8 @@ int run_expm(bbc_handle h, const double* A, int64_t N, double* Out, int m, int s
     return fail(BBC_INVALID_ARG, "degree not available in this scheme");
   if (s < 0 || s > 1100) return fail(BBC_INVALID_ARG, "squarings out of range");
   const bool pade = (flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE26;
-  if (pade && N > 1024) return fail(BBC_UNSUPPORTED, "the Pade comparator serves N <= 1024");
+  if (pade && N > 1024 && !lu_solve_large_available())
+    return fail(BBC_UNSUPPORTED, "the Pade comparator beyond N = 1024 needs cuSOLVER, which is not available");
   if (pade) upper = false;
   auto exact = [&](double* T, int q) -> int {
     if (!upper) return BBC_OK;
@@ -438,7 +439,9 @@ int run_expm(bbc_handle h, const double* A, int64_t N, double* Out, int m, int s
   if (int rc = exact(T, s)) return rc;
   if (pade) {  // (-u + v) r_26 = u + v: W8 holds -u + v, T holds u + v
     LaunchScope scope(h, BBC_KERNEL_LINCOMB, stream);
-    const cudaError_t e = lu_solve_inplace(h->work + (size_t)8 * N * N, T, N, s == 0 ? h->dflag : nullptr, stream);
+    double* scratch = (T == Out) ? tmp : Out;  // whichever of the two is not holding u + v
+    const cudaError_t e =
+        lu_solve_inplace(h->work + (size_t)8 * N * N, T, N, s == 0 ? h->dflag : nullptr, stream, scratch);
     if (e != cudaSuccess) return cuda_fail(e, "Pade solve");
   }
   double* src = T;

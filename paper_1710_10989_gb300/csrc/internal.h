@@ -103,8 +103,11 @@ cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double al
                           bool literal = false);
 bool ozaki_supported(int64_t N);
 
-// Solve M X = B in place (X overwrites B, M is destroyed), N <= 1024 (pade.cu).
-cudaError_t lu_solve_inplace(double* M, double* B, int64_t N, unsigned int* flag, cudaStream_t st);
+// Solve M X = B in place (X overwrites B, M is destroyed) (pade.cu). N > 1024 goes
+// through cuSOLVER (loaded at run time) and needs an N x N scratch matrix.
+cudaError_t lu_solve_inplace(double* M, double* B, int64_t N, unsigned int* flag, cudaStream_t st,
+                             double* scratch = nullptr);
+bool lu_solve_large_available();
 
 // The (m, s)-proposing MLP (mlp.cu).
 int64_t mlp_param_count(int n_in, int hid, int n_out);

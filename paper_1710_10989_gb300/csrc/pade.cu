@@ -1,9 +1,16 @@
 // pade.cu -- the linear solve of the diagonal Pade comparator: (v - u) R = u + v
-// (eq. pade10 / eq. pade26), by Gaussian elimination with partial pivoting on the
-// N right-hand sides at once. One CTA of 1024 threads: the paper counts this
-// step as 4/3 of a product, but at the sizes the comparator serves (N <= 1024)
-// a single SM suffices; a blocked multi-CTA factorisation is the way to scale.
+// (eq. pade10 / eq. pade26). The paper counts it as 4/3 of a product: an LU
+// factorisation with partial pivoting (1/3) and N forward / back substitutions (1).
+//  N <= 1024: Gaussian elimination with partial pivoting on the N right-hand
+//    sides at once in one CTA of 1024 threads (this file's kernel).
+//  N > 1024: cuSOLVER's getrf / getrs (FP64), loaded at run time; the comparator
+//    then fails with BBC_UNSUPPORTED where the library is absent. Row-major M is
+//    the column-major M^T, so getrf factors M^T and getrs with op = T solves
+//    M Z = B for B given column-major (a transpose on each side of the solve).
+#include <dlfcn.h>
 #include <math.h>
+
+#include <mutex>
 
 #include "internal.h"
 
@@ -81,11 +88,114 @@ k_lu_solve(double* __restrict__ M, double* __restrict__ B, int N, unsigned int* 
   }
 }
 
+
+// dst = src^T (N x N), 32 x 32 tiles through shared memory; flags a non-finite value.
+__global__ void k_transpose(const double* __restrict__ src, double* __restrict__ dst, int64_t N,
+                            unsigned int* __restrict__ flag) {
+  __shared__ double t[32][33];
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  bool bad = false;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t i = i0 + r, j = j0 + threadIdx.x;
+    if (i < N && j < N) t[r][threadIdx.x] = src[i * N + j];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t i = j0 + r, j = i0 + threadIdx.x;
+    if (i < N && j < N) {
+      const double v = t[threadIdx.x][r];
+      dst[i * N + j] = v;
+      bad |= !isfinite(v);
+    }
+  }
+  if (bad && flag) atomicOr(flag, 1u);
+}
+
+// cuSOLVER dense entry points, resolved at run time (no link-time dependency).
+typedef int (*CreateFn)(void**);
+typedef int (*SetStreamFn)(void*, cudaStream_t);
+typedef int (*GetrfBufFn)(void*, int, int, double*, int, int*);
+typedef int (*GetrfFn)(void*, int, int, double*, int, double*, int*, int*);
+typedef int (*GetrsFn)(void*, int, int, int, const double*, int, const int*, double*, int, int*);
+struct Solver {
+  bool tried = false, ok = false;
+  CreateFn create = nullptr;
+  SetStreamFn set_stream = nullptr;
+  GetrfBufFn getrf_buf = nullptr;
+  GetrfFn getrf = nullptr;
+  GetrsFn getrs = nullptr;
+  void* handle[64] = {};          // per device
+  double* work[64] = {};          // per device: getrf workspace, then pivots and info
+  size_t work_bytes[64] = {};
+};
+Solver g_solver;
+std::mutex g_solver_mu;
+
+bool load_solver() {
+  if (g_solver.tried) return g_solver.ok;
+  g_solver.tried = true;
+  const char* names[] = {"libcusolver.so", "libcusolver.so.12", "libcusolver.so.11"};
+  void* lib = nullptr;
+  for (const char* n : names)
+    if ((lib = dlopen(n, RTLD_NOW | RTLD_LOCAL))) break;
+  if (!lib) return false;
+  g_solver.create = (CreateFn)dlsym(lib, "cusolverDnCreate");
+  g_solver.set_stream = (SetStreamFn)dlsym(lib, "cusolverDnSetStream");
+  g_solver.getrf_buf = (GetrfBufFn)dlsym(lib, "cusolverDnDgetrf_bufferSize");
+  g_solver.getrf = (GetrfFn)dlsym(lib, "cusolverDnDgetrf");
+  g_solver.getrs = (GetrsFn)dlsym(lib, "cusolverDnDgetrs");
+  g_solver.ok = g_solver.create && g_solver.set_stream && g_solver.getrf_buf && g_solver.getrf && g_solver.getrs;
+  return g_solver.ok;
+}
+
 }  // namespace
 
-cudaError_t lu_solve_inplace(double* M, double* B, int64_t N, unsigned int* flag, cudaStream_t st) {
-  if (N < 1 || N > 1024) return cudaErrorInvalidValue;
-  k_lu_solve<<<1, SOLVE_THREADS, 0, st>>>(M, B, (int)N, flag);
+bool lu_solve_large_available() {
+  std::lock_guard<std::mutex> lk(g_solver_mu);
+  return load_solver();
+}
+
+cudaError_t lu_solve_inplace(double* M, double* B, int64_t N, unsigned int* flag, cudaStream_t st,
+                             double* scratch) {
+  if (N < 1) return cudaErrorInvalidValue;
+  if (N <= 1024) {
+    k_lu_solve<<<1, SOLVE_THREADS, 0, st>>>(M, B, (int)N, flag);
+    return cudaGetLastError();
+  }
+  if (!scratch || N > 65535) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lk(g_solver_mu);
+  if (!load_solver()) return cudaErrorNotSupported;
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!g_solver.handle[dev] && g_solver.create(&g_solver.handle[dev]) != 0) return cudaErrorNotSupported;
+  void* hs = g_solver.handle[dev];
+  if (g_solver.set_stream(hs, st) != 0) return cudaErrorNotSupported;
+  const int n = (int)N;
+  int lwork = 0;
+  if (g_solver.getrf_buf(hs, n, n, M, n, &lwork) != 0) return cudaErrorNotSupported;
+  // workspace: lwork doubles, N pivots, one info word (grown on a new largest N only)
+  const size_t need = (size_t)lwork * sizeof(double) + (size_t)N * sizeof(int) + 256;
+  if (need > g_solver.work_bytes[dev]) {
+    if (g_solver.work[dev]) {
+      if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
+      cudaFree(g_solver.work[dev]);
+    }
+    g_solver.work[dev] = nullptr;
+    g_solver.work_bytes[dev] = 0;
+    if ((err = cudaMalloc(&g_solver.work[dev], need)) != cudaSuccess) return err;
+    g_solver.work_bytes[dev] = need;
+  }
+  double* work = g_solver.work[dev];
+  int* ipiv = reinterpret_cast<int*>(work + lwork);
+  int* info = ipiv + N;
+  if (g_solver.getrf(hs, n, n, M, n, work, ipiv, info) != 0) return cudaErrorUnknown;
+  const dim3 tg((unsigned)((N + 31) / 32), (unsigned)((N + 31) / 32)), tb(32, 8);
+  k_transpose<<<tg, tb, 0, st>>>(B, scratch, N, nullptr);              // B, column-major
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (g_solver.getrs(hs, 1 /* op T */, n, n, M, n, ipiv, scratch, n, info) != 0) return cudaErrorUnknown;
+  k_transpose<<<tg, tb, 0, st>>>(scratch, B, N, flag);                 // R, row-major
   return cudaGetLastError();
 }
 

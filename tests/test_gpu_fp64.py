@@ -272,6 +272,21 @@ def test_pade26_matches_oracle(h, api, n, norm, nonnormal):
     assert rel_fro(to_host(out), want) < 1e-12
 
 
+def test_pade26_beyond_single_cta_solve(h, api):
+    """N > 1024: the comparator's solve goes through the blocked library LU."""
+    A = W.gaussian(1500, 11, 8.0)
+    out = empty_like_dev(1500)
+    try:
+        info = h.expm(to_dev(A), out, 0.0, api.SCHEME_PADE26)
+    except api.BBCError as e:
+        if e.code == api.UNSUPPORTED:
+            pytest.skip("no cuSOLVER on this machine")
+        raise
+    want, oi = O.expm(A, "pade26")
+    assert (info.m, info.s, info.products) == (oi.m, oi.s, oi.products)
+    assert rel_fro(to_host(out), want) < 1e-12
+
+
 def test_pade26_split_products(h, api):
     A = W.gaussian(200, 9, 5.0)
     out = empty_like_dev(200)
