@@ -24,6 +24,7 @@ def main():
     ap.add_argument("--precision", choices=("fp64", "ozaki"), default="fp64")
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--upper", action="store_true", help="upper triangular operands (triangle products)")
     a = ap.parse_args()
 
     import torch
@@ -52,8 +53,13 @@ def main():
         print("done", a)
         return
     h = api.Handle(0)
-    A = torch.from_numpy(W.gaussian(a.n, 1, a.norm)).cuda()
-    B = torch.from_numpy(W.gaussian(a.n, 2, a.norm)).cuda()
+    if a.upper:
+        A = torch.from_numpy(W.nonnormal_upper(a.n, 1, a.norm)).cuda()
+        B = torch.from_numpy(W.nonnormal_upper(a.n, 2, a.norm)).cuda()
+        flags |= api.UPPER
+    else:
+        A = torch.from_numpy(W.gaussian(a.n, 1, a.norm)).cuda()
+        B = torch.from_numpy(W.gaussian(a.n, 2, a.norm)).cuda()
     C = torch.empty_like(A)
     for _ in range(a.reps):
         if a.kernel == "gemm":
