@@ -39,7 +39,7 @@ PI = {1: 0, 2: 1, 4: 2, 8: 3, 12: 4, 18: 5}
 # DRAM traffic per launch of the dominant kernels from one ncu capture each (profiles/),
 # valid only while the kernel source is the one that was captured.
 NCU_TRAFFIC = {
-    "gemm_ozaki.cu": ("2ba53ed868d103c31deaee82924d1eaf310fcd1c975b60e3987881e56a4fcefa", 4096, 4.628172e9 + 0.152834e9),
+    "gemm_ozaki.cu": ("af04ce3f651cfac7a7636124c81820e10587593ffe5ec37557b4d89247f243b4", 4096, ((3.986145e9 + 0.177863e9) + (1.467322e9 + 0.107599e9)) / 2),
     "gemm_f64.cu": ("c1965ca226ec4ee76ccab7620c3105f1abf10d5ba9ea3047e862e9126f56b6a5", 4096, 3.733487e9 + 0.133997312e9),
     "batched.cu": ("3f86258f8371369fa84e7c05b2e817d5299e265d45b46618f23f4add0ce661b4", 512, 3.662761e9 + 1.816421e9),
 }
@@ -359,7 +359,8 @@ def run_dense(args, torch, dist, api, rank, world, local):
         roof = {"bound": "tensor", "achieved": executed, "peak": peak, "unit": "TFLOP/s",
                 "frac": executed / peak,
                 "traffic": ncu_traffic("gemm_ozaki.cu", n) if args.slices == 6 else None,
-                "traffic_note": "ncu capture of one product at 6 slices (profiles/k_ozaki_pair_dense4096.md)",
+                "traffic_note": "mean of ncu captures of one dense and one triangle product at 6 slices "
+                                "(the workload's launch mix is half and half; profiles/k_ozaki_pair_dense4096.md)",
                 "kernel": f"k_ozaki_pair ({args.slices} BF16 slices: {pairs} slice products per FP64 product)",
                 "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS)" if "bf16_tflops" in pk
                                 else "fallback 1.9 PFLOP/s bf16"),
