@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--u", choices=("double", "single"), default="double",
+                    help="batch workload: backward-error target of the (m, s) selection, 2^-53 or 2^-24 "
+                         "(Table 2's single-precision thresholds)")
     ap.add_argument("--selector", choices=("plain", "learned", "alpha"), default="learned",
                     help="(m, s) selection of the batch workload")
     return ap.parse_args()
@@ -413,18 +416,29 @@ def run_batch(args, torch, dist, api, rank, world, local, mats):
     flags = (api.PREC_OZAKI if split else 0) | sel_flag
     order = api.batch_order([A.shape[0] for A in mats])
     mats = [mats[i] for i in order]
-    ins = [torch.from_numpy(A).cuda() for A in mats]
-    outs = [torch.empty_like(a) for a in ins]
+    # the matrices back to back in one device buffer (inputs) and one more (outputs), so that an
+    # end-to-end step moves the whole batch with one copy each way
+    sizes = [A.size for A in mats]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    dtype_t = torch.from_numpy(mats[0]).dtype
+    din = torch.empty(int(offs[-1]), dtype=dtype_t, device="cuda")
+    dout = torch.empty_like(din)
+    for A, o in zip(mats, offs[:-1]):
+        din[int(o):int(o) + A.size].copy_(torch.from_numpy(A.ravel()))
+    ins = [din[int(o):int(o) + A.size].view(A.shape) for A, o in zip(mats, offs[:-1])]
+    outs = [dout[int(o):int(o) + A.size].view(A.shape) for A, o in zip(mats, offs[:-1])]
     batch = api.Batch(ins, outs)
     stream = torch.cuda.Stream()
 
-    def capture(fl):
+    u_batch = 2.0 ** -24 if args.u == "single" else 0.0
+
+    def capture(fl, tol=u_batch):
         with torch.cuda.stream(stream):
-            h.expm_batched(batch, flags=fl, stream=stream)  # warm-up outside the capture
+            h.expm_batched(batch, tol=tol, flags=fl, stream=stream)  # warm-up outside the capture
             torch.cuda.synchronize()
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream):
-                h.expm_batched(batch, flags=fl, stream=stream)
+                h.expm_batched(batch, tol=tol, flags=fl, stream=stream)
         return g
 
     graph = capture(flags)
@@ -450,7 +464,7 @@ def run_batch(args, torch, dist, api, rank, world, local, mats):
 
     plain = None
     if flags != 0 and not args.no_fp64_compare:
-        g64 = capture(0)
+        g64 = capture(0, 0.0)
         g64.replay()
         ms64 = timed(torch, dist, world, cur, g64.replay, 1)
         inf64 = batch.infos()
@@ -466,21 +480,20 @@ def run_batch(args, torch, dist, api, rank, world, local, mats):
 
     e2e = None
     if not args.no_e2e:
-        hin = [torch.from_numpy(A).pin_memory() for A in mats]
-        hout = [torch.empty_like(a).pin_memory() for a in hin]
+        hin = din.cpu().pin_memory()           # the whole batch, packed, in pinned host memory
+        hout = torch.empty_like(hin).pin_memory()
         e2e_steps = max(1, min(args.steps, 2))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            for a, d in zip(hin, ins):
-                d.copy_(a, non_blocking=True)
+            din.copy_(hin, non_blocking=True)   # host -> device, one copy
             graph.replay()
-            for d, o in zip(outs, hout):
-                o.copy_(d, non_blocking=True)
+            hout.copy_(dout, non_blocking=True)  # device -> host, one copy
             torch.cuda.synchronize()
         te = time.perf_counter() - t0
         e2e = {"value": len(mats) * e2e_steps * world / te, "unit": "expm/s", "h2d_bytes_per_step": bytes_io // 2,
-               "d2h_bytes_per_step": bytes_io // 2, "steps": e2e_steps}
+               "d2h_bytes_per_step": bytes_io // 2, "steps": e2e_steps,
+               "api": "bbc_expm_batched on the packed batch, one pinned copy each way per step"}
     cpu = cpu_batch_sample(mats[::max(1, len(mats) // 200)]) if (rank == 0 and world == 1
                                                                  and not args.no_cpu_baseline) else None
     h.close()
@@ -512,7 +525,8 @@ def run_batch(args, torch, dist, api, rank, world, local, mats):
                    "count": len(mats) * world, "products_per_step": products, "statuses_not_ok": bad,
                    "parallelism": f"{world} ranks, LPT shards of the batch, no collective" if world > 1 else "single",
                    "precision": args.precision, "selector": args.selector,
-                   "graph": "one persistent kernel per step, replayed from a CUDA graph", "u": "2^-53",
+                   "graph": "one persistent kernel per step, replayed from a CUDA graph",
+                   "u": "2^-24" if args.u == "single" else "2^-53",
                    "autotuner": tuning,
                    "l2": "per-CTA binary64 work slots; inputs+outputs 3.7 GB per step (larger than L2)"},
         "tflops_logical": logical,
