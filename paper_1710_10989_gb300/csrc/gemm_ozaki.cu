@@ -1,24 +1,11 @@
 // gemm_ozaki.cu -- FP64 products computed exactly from BF16 slices on the
-// tcgen05 tensor cores (an error-free splitting in the manner of Ozaki et al.).
+// tcgen05 tensor cores (an error-free splitting in the manner of Ozaki et al.;
+// the slices and their scales come from slices.cu).
 //
 // Why: the scaling-and-squaring cost is the number of dense products (Section 1,
 // Section 4 of Bader-Blanes-Casas). GB300 runs FP64 at ~1.25 TFLOP/s but dense
 // BF16 at ~2 PFLOP/s, so a product rebuilt from k^2/2 BF16 products is far
 // faster than one FP64 product, and it is exact up to the slicing.
-//
-// Splitting. Row i of P gets a power-of-two scale 2^e_i with max_k |P_ik| < 2^(e_i-1);
-// column j of Q gets 2^f_j likewise. Each scaled entry is rounded to a fixed-point
-// integer with 8k fractional bits and cut into k balanced base-256 digits
-// d_0..d_{k-1} (|d_0| <= 128, |d_p| <= 128): P_ik ~ sum_p d_p 2^(e_i - 8(p+1)).
-// Digits are small integers, exact in BF16. The extraction is pure integer work
-// on the FP64 bit pattern (no FP64 arithmetic: the FP64 pipe is the slow one).
-//
-// Diagonal deflation. The scheme's operands (B_j = b_0j I + ..., T = I + X + ...)
-// are dominated by their diagonal, which would set the row and column scales
-// and leave the off-diagonal entries ~10 fewer bits. So the diagonals are taken
-// out before slicing (P = D_P + P', Q = D_Q + Q') and added back exactly in the
-// epilogue: P Q = P'Q' + D_P Q + P D_Q - D_P D_Q (elementwise: P_ii Q_ij +
-// P_ij Q_jj - [i = j] P_ii Q_jj).
 //
 // Exact products. Pairs (p, q) with g = p + q <= k - 1 are kept (the triangle),
 // C_ij = 2^(e_i + f_j - 16) sum_g 2^(-8g) S_g with S_g = sum_{p+q=g} sum_k d^P d^Q,
@@ -35,7 +22,8 @@
 //    That FP32 sum of up to ~10^5 terms loses roughly 2^-16 of itself, i.e. about
 //    2^-56 of the result. (With the exact/FP32 boundary one group lower, at g = 4,
 //    the same loss showed up as ~1e-14 relative error per product at N = 4096.)
-//  C_ij = 2^(e_i + f_j - 48) (R + 2^-8 LOW).
+//  C_ij = 2^(e_i + f_j - 48) (R + 2^-8 LOW), to which the epilogue adds back the
+//  diagonals the slices left out: + P_ii Q_ij + P_ij Q_jj - [i = j] P_ii Q_jj.
 //
 // The product kernel, k_ozaki_pair, is described at its definition: CTA pairs
 // (tcgen05.mma.cta_group::2) on persistent 256 x 128 output tiles, TMA-fed.
@@ -54,17 +42,19 @@
 #include <mutex>
 
 #include "internal.h"
+#include "slices.h"
 
 namespace bbc {
 namespace {
 
-constexpr int TILE = 128;          // rows per CTA and columns of an output tile
+using slices::OzLayout;
+using slices::layout;
+constexpr int TILE = slices::PAD;  // rows per CTA and columns of an output tile
 constexpr int KSTEP = 64;          // BF16 elements per 128-byte swizzle row
 constexpr int CHUNK_STEPS = 16;    // 16 x 64 = 1024 K per exact FP32 chunk
 constexpr int G_EXACT = 5;         // groups 0..4 are summed exactly
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;  // 2 s per wait
-constexpr unsigned int STATUS_NONFINITE = 1u;  // bits of the handle's status word
-constexpr unsigned int STATUS_TIMEOUT = 2u;
+constexpr unsigned int STATUS_TIMEOUT = 2u;    // bit of the handle's status word
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -119,169 +109,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// ------------------------------------------------------------ digit extraction
-// Biased exponent field of x; subnormals and zero report 1 and 0 respectively
-// through the same rule max(E, 1) used below. Non-finite -> 0x7FF.
-__device__ __forceinline__ int exp_field(double x) {
-  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
-}
-
-// round(x * 2^(8k - e)) for |x| < 2^(e-1), with e = Emax - 1021 (Emax the largest
-// biased exponent in the row/column): integer shift of the 53-bit significand.
-__device__ __forceinline__ long long fixed_point(double x, int Emax, int k) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  int E = (int)((bits >> 52) & 0x7FF);
-  unsigned long long M = bits & 0xFFFFFFFFFFFFFull;
-  if (E == 0) E = 1; else M |= 1ull << 52;
-  const int sh = 8 * k - 54 - (Emax - E);  // value * 2^(8k - e) = M * 2^sh
-  long long X;
-  if (sh >= 0) X = (long long)(M << sh);
-  else if (sh > -60) X = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
-  else X = 0;
-  return (bits >> 63) ? -X : X;
-}
-
-// Exact BF16 bit pattern of a small integer d (|d| <= 256).
-__device__ __forceinline__ uint32_t bf16_of_int(int d) {
-  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;  // exact for |d| < 2^22
-  return (uint32_t)__float_as_uint(f) >> 16;
-}
-
-// Balanced base-256 digits, most significant first, as BF16 bit patterns.
-template <int K>
-__device__ __forceinline__ void digits(long long X, uint32_t (&out)[K]) {
-#pragma unroll
-  for (int p = K - 1; p >= 1; --p) {
-    const long long low = ((X + 128) & 255) - 128;
-    out[p] = bf16_of_int((int)low);
-    X = (X - low) >> 8;
-  }
-  out[0] = bf16_of_int((int)X);
-}
-
-// The literal split (BBC_PREC_SPLIT): x scaled by the row's (column's) power of
-// two 2^-(Emax - 1021), so |x| < 1/2, then K BF16 terms, each the rounding to
-// nearest of what the earlier terms left (floating-point splitting, no common
-// fixed point: each term keeps its own exponent).
-template <int K>
-__device__ __forceinline__ void float_terms(double x, int Emax, uint32_t (&out)[K]) {
-  double r = ldexp(x, -(Emax - 1021));
-#pragma unroll
-  for (int p = 0; p < K; ++p) {
-    const __nv_bfloat16 b = __double2bfloat16(r);
-    out[p] = (uint32_t)__bfloat16_as_ushort(b);
-    r -= (double)__bfloat162float(b);
-  }
-}
-template <int K, bool FLT>
-__device__ __forceinline__ void terms(double x, int Emax, uint32_t (&out)[K]) {
-  if (FLT) float_terms<K>(x, Emax, out);
-  else digits<K>(fixed_point(x, Emax, K), out);
-}
-
-// P (N x N, row-major FP64) -> K slice planes [K][Rp][Kp] of BF16 digits with
-// row exponents. One warp per row; padding rows/columns are written as zeros.
-template <int K, bool FLT>
-__global__ void __launch_bounds__(256)
-k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, uint16_t* __restrict__ planes,
-             int* __restrict__ erow, double* __restrict__ pdiag, unsigned int* __restrict__ status) {
-  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= Rp) return;
-  const size_t plane = (size_t)Rp * Kp;
-  uint32_t* out = reinterpret_cast<uint32_t*>(planes);  // bf16 pairs
-  int Emax = 0;
-  bool bad = false;
-  if (row < N) {
-    for (int64_t j = lane; j < N; j += 32) {
-      const int E = (j == row) ? 0 : exp_field(__ldg(P + row * N + j));
-      bad |= (E == 0x7FF);
-      Emax = max(Emax, E);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) Emax = max(Emax, __shfl_xor_sync(0xffffffffu, Emax, off));
-    bad = __any_sync(0xffffffffu, bad);
-  }
-  if (bad == false && row < N) {  // the diagonal itself may be non-finite
-    const int Ed = (lane == 0) ? exp_field(__ldg(P + row * N + row)) : 0;
-    bad = __any_sync(0xffffffffu, Ed == 0x7FF);
-  }
-  if (bad && lane == 0) atomicOr(status, STATUS_NONFINITE);
-  if (lane == 0) {
-    erow[row] = (row < N && !bad) ? Emax - 1021 : 0;
-    pdiag[row] = (row < N && !bad) ? __ldg(P + row * N + row) : 0.0;
-  }
-  Emax = max(Emax, 1);
-  for (int64_t j = 2 * lane; j < Kp; j += 64) {
-    uint32_t d0[K], d1[K];
-    const double x0 = (row < N && j < N && j != row && !bad) ? __ldg(P + row * N + j) : 0.0;
-    const double x1 = (row < N && j + 1 < N && j + 1 != row && !bad) ? __ldg(P + row * N + j + 1) : 0.0;
-    terms<K, FLT>(x0, Emax, d0);
-    terms<K, FLT>(x1, Emax, d1);
-    const size_t idx = ((size_t)row * Kp + j) >> 1;
-#pragma unroll
-    for (int p = 0; p < K; ++p) out[p * (plane >> 1) + idx] = d0[p] | (d1[p] << 16);
-  }
-}
-
-// Largest biased exponent per column of Q (fexp zeroed beforehand).
-__global__ void __launch_bounds__(256)
-k_col_maxexp(const double* __restrict__ Q, int64_t N, int64_t rows_per, int* __restrict__ fexp) {
-  const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  if (j >= N) return;
-  const int64_t r0 = (int64_t)blockIdx.y * rows_per;
-  const int64_t r1 = min(N, r0 + rows_per);
-  int m = 0;
-  for (int64_t i = r0; i < r1; ++i) {
-    const int E = exp_field(__ldg(Q + i * N + j));
-    m = max(m, (i == j && E != 0x7FF) ? 0 : E);  // the diagonal is deflated (but still checked)
-  }
-  atomicMax(fexp + j, m);
-}
-
-// Q (N x N) -> K planes of Q^T digits [K][Rp][Kp] (plane row j holds column j of
-// Q) with column exponents fcol. 32 x 32 tiles transposed through shared memory.
-template <int K, bool FLT>
-__global__ void __launch_bounds__(256)
-k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, const int* __restrict__ fexp,
-             uint16_t* __restrict__ planes, int* __restrict__ fcol, double* __restrict__ qdiag,
-             unsigned int* __restrict__ status) {
-  __shared__ uint16_t tile[K][32][34];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t i0 = (int64_t)blockIdx.x * 32;  // rows of Q (the K dimension)
-  const int64_t j0 = (int64_t)blockIdx.y * 32;  // columns of Q
-  const int64_t j = j0 + tx;
-  const int Ej = (j < N) ? fexp[j] : 0;
-  const bool bad = (Ej == 0x7FF);
-  if (blockIdx.x == 0 && ty == 0 && j < Rp) {
-    fcol[j] = (j < N && !bad) ? Ej - 1021 : 0;
-    qdiag[j] = (j < N && !bad) ? __ldg(Q + j * N + j) : 0.0;
-    if (bad) atomicOr(status, STATUS_NONFINITE);
-  }
-  const int Emax = max(Ej, 1);
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int il = ty + 8 * r;
-    const int64_t i = i0 + il;
-    const double x = (i < N && j < N && i != j && !bad) ? __ldg(Q + i * N + j) : 0.0;
-    uint32_t d[K];
-    terms<K, FLT>(x, Emax, d);
-#pragma unroll
-    for (int p = 0; p < K; ++p) tile[p][tx][il] = (uint16_t)d[p];
-  }
-  __syncthreads();
-  const size_t plane = (size_t)Rp * Kp;
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int jl = ty + 8 * r;
-    const int64_t jj = j0 + jl, ii = i0 + tx;
-    if (jj < Rp && ii < Kp) {
-#pragma unroll
-      for (int p = 0; p < K; ++p) planes[p * plane + (size_t)jj * Kp + ii] = tile[p][jl][tx];
-    }
-  }
-}
 
 // ------------------------------------------------------------ the product kernel
 // k_ozaki_pair: a cluster of two CTAs computes 256 x 128 output tiles with
@@ -827,88 +654,7 @@ bool make_map(CUtensorMap* m, void* base, int64_t Rp, int64_t Kp, int k, int box
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int64_t padded(int64_t N) { return (N + TILE - 1) / TILE * TILE; }
-
-template <int K, bool FLT>
-cudaError_t split_both(const double* P, const double* Q, int64_t N, int64_t Rp, uint16_t* Ps, uint16_t* Qs,
-                       int* erow, int* fcol, int* fexp, double* pdiag, double* qdiag, unsigned int* status,
-                       cudaStream_t st) {
-  k_split_rows<K, FLT><<<(unsigned)((Rp + 7) / 8), 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
-  cudaError_t err = cudaMemsetAsync(fexp, 0, (size_t)N * sizeof(int), st);
-  if (err != cudaSuccess) return err;
-  const int64_t colblocks = (N + 255) / 256;
-  int64_t slabs = (304 + colblocks - 1) / colblocks;
-  slabs = std::min<int64_t>(slabs, (N + 63) / 64);
-  const int64_t rows_per = (N + slabs - 1) / slabs;
-  k_col_maxexp<<<dim3((unsigned)colblocks, (unsigned)slabs), 256, 0, st>>>(Q, N, rows_per, fexp);
-  k_split_cols<K, FLT><<<dim3((unsigned)(Rp / 32), (unsigned)(Rp / 32)), 256, 0, st>>>(Q, N, Rp, Rp, fexp, Qs, fcol,
-                                                                                   qdiag, status);
-  return cudaGetLastError();
-}
-
 }  // namespace
-
-bool ozaki_supported(int64_t N) { return N >= 1 && N <= 16384; }
-
-// Layout of the workspace: 256 reserved bytes, erow[Rp], fcol[Rp], fexp[Rp], the
-// deflated diagonals pdiag[Rp], qdiag[Rp], then the P planes and the Q^T planes,
-// each k x Rp x Rp BF16.
-size_t ozaki_workspace_bytes(int64_t N, int slices) {
-  const int64_t Rp = padded(N);
-  return 256 + 3 * (size_t)Rp * sizeof(int) + 256 + 2 * (size_t)Rp * sizeof(double) + 256 +
-         2 * (size_t)slices * Rp * Rp * 2;
-}
-
-namespace {
-struct OzLayout {
-  int64_t Rp;
-  int* erow;
-  int* fcol;
-  int* fexp;
-  double* pdiag;
-  double* qdiag;
-  uint16_t* Ps;
-  uint16_t* Qs;
-};
-OzLayout layout(void* work, int64_t N, int slices) {
-  OzLayout L;
-  L.Rp = padded(N);
-  uint8_t* w = static_cast<uint8_t*>(work);
-  L.erow = reinterpret_cast<int*>(w + 256);
-  L.fcol = L.erow + L.Rp;
-  L.fexp = L.fcol + L.Rp;
-  size_t off = 256 + 3 * (size_t)L.Rp * sizeof(int);
-  off = (off + 255) / 256 * 256;
-  L.pdiag = reinterpret_cast<double*>(w + off);
-  L.qdiag = L.pdiag + L.Rp;
-  off += 2 * (size_t)L.Rp * sizeof(double);
-  off = (off + 255) / 256 * 256;
-  L.Ps = reinterpret_cast<uint16_t*>(w + off);
-  L.Qs = L.Ps + (size_t)slices * L.Rp * L.Rp;
-  return L;
-}
-}  // namespace
-
-template <bool FLT>
-cudaError_t split_k(const double* P, const double* Q, int64_t N, int slices, const OzLayout& L, unsigned int* flag,
-                    cudaStream_t st) {
-  switch (slices) {
-    case 2: return split_both<2, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 3: return split_both<3, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 4: return split_both<4, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 5: return split_both<5, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 6: return split_both<6, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 7: return split_both<7, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    default: return split_both<8, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-  }
-}
-
-cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices, void* work, unsigned int* flag,
-                        cudaStream_t st, bool literal) {
-  if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
-  const OzLayout L = layout(work, N, slices);
-  return literal ? split_k<true>(P, Q, N, slices, L, flag, st) : split_k<false>(P, Q, N, slices, L, flag, st);
-}
 
 namespace {
 // Clusters of two k_ozaki_pair CTAs that fit on the device at once (cached per device).

@@ -1,0 +1,279 @@
+// slices.cu -- the operands of a split-precision product cut into BF16 slices
+// (an error-free splitting in the manner of Ozaki et al.; the products that use
+// them are in gemm_ozaki.cu).
+//
+// Splitting. Row i of P gets a power-of-two scale 2^e_i with max_k |P_ik| < 2^(e_i-1);
+// column j of Q gets 2^f_j likewise. Each scaled entry is rounded to a fixed-point
+// integer with 8k fractional bits and cut into k balanced base-256 digits
+// d_0..d_{k-1} (|d_0| <= 128, |d_p| <= 128): P_ik ~ sum_p d_p 2^(e_i - 8(p+1)).
+// Digits are small integers, exact in BF16. The extraction is pure integer work
+// on the FP64 bit pattern (no FP64 arithmetic: the FP64 pipe is the slow one).
+//
+// Diagonal deflation. The scheme's operands (B_j = b_0j I + ..., T = I + X + ...)
+// are dominated by their diagonal, which would set the row and column scales
+// and leave the off-diagonal entries ~10 fewer bits. So the diagonals are taken
+// out before slicing (P = D_P + P', Q = D_Q + Q') and added back exactly in the
+// epilogue: P Q = P'Q' + D_P Q + P D_Q - D_P D_Q (elementwise: P_ii Q_ij +
+// P_ij Q_jj - [i = j] P_ii Q_jj).
+//
+// The literal split (BBC_PREC_SPLIT) writes, instead of digits, K BF16 terms of the
+// scaled value, each the rounding of what the earlier ones left.
+//
+// HBM-bound kernels: per product they read the two FP64 operands (twice each:
+// once for the scale exponents) and write 2 k BF16 planes.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "slices.h"
+
+namespace bbc {
+namespace {
+
+using slices::OzLayout;
+using slices::layout;
+using slices::STATUS_NONFINITE;
+using slices::padded;
+
+// Biased exponent field of x; subnormals and zero report 1 and 0 respectively
+// through the same rule max(E, 1) used below. Non-finite -> 0x7FF.
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// round(x * 2^(8k - e)) for |x| < 2^(e-1), with e = Emax - 1021 (Emax the largest
+// biased exponent in the row/column): integer shift of the 53-bit significand.
+__device__ __forceinline__ long long fixed_point(double x, int Emax, int k) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  int E = (int)((bits >> 52) & 0x7FF);
+  unsigned long long M = bits & 0xFFFFFFFFFFFFFull;
+  if (E == 0) E = 1; else M |= 1ull << 52;
+  const int sh = 8 * k - 54 - (Emax - E);  // value * 2^(8k - e) = M * 2^sh
+  long long X;
+  if (sh >= 0) X = (long long)(M << sh);
+  else if (sh > -60) X = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
+  else X = 0;
+  return (bits >> 63) ? -X : X;
+}
+
+// Exact BF16 bit pattern of a small integer d (|d| <= 256).
+__device__ __forceinline__ uint32_t bf16_of_int(int d) {
+  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;  // exact for |d| < 2^22
+  return (uint32_t)__float_as_uint(f) >> 16;
+}
+
+// Balanced base-256 digits, most significant first, as BF16 bit patterns.
+template <int K>
+__device__ __forceinline__ void digits(long long X, uint32_t (&out)[K]) {
+#pragma unroll
+  for (int p = K - 1; p >= 1; --p) {
+    const long long low = ((X + 128) & 255) - 128;
+    out[p] = bf16_of_int((int)low);
+    X = (X - low) >> 8;
+  }
+  out[0] = bf16_of_int((int)X);
+}
+
+// The literal split (BBC_PREC_SPLIT): x scaled by the row's (column's) power of
+// two 2^-(Emax - 1021), so |x| < 1/2, then K BF16 terms, each the rounding to
+// nearest of what the earlier terms left (floating-point splitting, no common
+// fixed point: each term keeps its own exponent).
+template <int K>
+__device__ __forceinline__ void float_terms(double x, int Emax, uint32_t (&out)[K]) {
+  double r = ldexp(x, -(Emax - 1021));
+#pragma unroll
+  for (int p = 0; p < K; ++p) {
+    const __nv_bfloat16 b = __double2bfloat16(r);
+    out[p] = (uint32_t)__bfloat16_as_ushort(b);
+    r -= (double)__bfloat162float(b);
+  }
+}
+template <int K, bool FLT>
+__device__ __forceinline__ void terms(double x, int Emax, uint32_t (&out)[K]) {
+  if (FLT) float_terms<K>(x, Emax, out);
+  else digits<K>(fixed_point(x, Emax, K), out);
+}
+
+// P (N x N, row-major FP64) -> K slice planes [K][Rp][Kp] of BF16 digits with
+// row exponents. One warp per row; padding rows/columns are written as zeros.
+template <int K, bool FLT>
+__global__ void __launch_bounds__(256)
+k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, uint16_t* __restrict__ planes,
+             int* __restrict__ erow, double* __restrict__ pdiag, unsigned int* __restrict__ status) {
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= Rp) return;
+  const size_t plane = (size_t)Rp * Kp;
+  uint32_t* out = reinterpret_cast<uint32_t*>(planes);  // bf16 pairs
+  int Emax = 0;
+  bool bad = false;
+  if (row < N) {
+    const double* pr = P + row * N;
+    int64_t j = lane;
+    for (; j + 96 < N; j += 128) {  // four independent loads in flight per lane
+      const double a0 = __ldg(pr + j), a1 = __ldg(pr + j + 32), a2 = __ldg(pr + j + 64), a3 = __ldg(pr + j + 96);
+      const int E0 = (j == row) ? 0 : exp_field(a0), E1 = (j + 32 == row) ? 0 : exp_field(a1);
+      const int E2 = (j + 64 == row) ? 0 : exp_field(a2), E3 = (j + 96 == row) ? 0 : exp_field(a3);
+      bad |= (E0 == 0x7FF) | (E1 == 0x7FF) | (E2 == 0x7FF) | (E3 == 0x7FF);
+      Emax = max(max(Emax, max(E0, E1)), max(E2, E3));
+    }
+    for (; j < N; j += 32) {
+      const int E = (j == row) ? 0 : exp_field(__ldg(pr + j));
+      bad |= (E == 0x7FF);
+      Emax = max(Emax, E);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) Emax = max(Emax, __shfl_xor_sync(0xffffffffu, Emax, off));
+    bad = __any_sync(0xffffffffu, bad);
+  }
+  if (bad == false && row < N) {  // the diagonal itself may be non-finite
+    const int Ed = (lane == 0) ? exp_field(__ldg(P + row * N + row)) : 0;
+    bad = __any_sync(0xffffffffu, Ed == 0x7FF);
+  }
+  if (bad && lane == 0) atomicOr(status, STATUS_NONFINITE);
+  if (lane == 0) {
+    erow[row] = (row < N && !bad) ? Emax - 1021 : 0;
+    pdiag[row] = (row < N && !bad) ? __ldg(P + row * N + row) : 0.0;
+  }
+  Emax = max(Emax, 1);
+  const bool live = row < N && !bad;
+  auto elem = [&](int64_t c) -> double {
+    return (live && c < N && c != row) ? __ldg(P + row * N + c) : 0.0;
+  };
+  for (int64_t j = 2 * lane; j < Kp; j += 128) {  // two pairs per lane per pass: four loads in flight
+    const int64_t j2 = j + 64;
+    const double x0 = elem(j), x1 = elem(j + 1);
+    const double x2 = (j2 < Kp) ? elem(j2) : 0.0, x3 = (j2 < Kp) ? elem(j2 + 1) : 0.0;
+    uint32_t d0[K], d1[K];
+    terms<K, FLT>(x0, Emax, d0);
+    terms<K, FLT>(x1, Emax, d1);
+    const size_t idx = ((size_t)row * Kp + j) >> 1;
+#pragma unroll
+    for (int p = 0; p < K; ++p) out[p * (plane >> 1) + idx] = d0[p] | (d1[p] << 16);
+    if (j2 < Kp) {
+      terms<K, FLT>(x2, Emax, d0);
+      terms<K, FLT>(x3, Emax, d1);
+#pragma unroll
+      for (int p = 0; p < K; ++p) out[p * (plane >> 1) + idx + 32] = d0[p] | (d1[p] << 16);
+    }
+  }
+}
+
+// Largest biased exponent per column of Q (fexp zeroed beforehand).
+__global__ void __launch_bounds__(256)
+k_col_maxexp(const double* __restrict__ Q, int64_t N, int64_t rows_per, int* __restrict__ fexp) {
+  const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (j >= N) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per;
+  const int64_t r1 = min(N, r0 + rows_per);
+  int m = 0;
+  for (int64_t i = r0; i < r1; ++i) {
+    const int E = exp_field(__ldg(Q + i * N + j));
+    m = max(m, (i == j && E != 0x7FF) ? 0 : E);  // the diagonal is deflated (but still checked)
+  }
+  atomicMax(fexp + j, m);
+}
+
+// Q (N x N) -> K planes of Q^T digits [K][Rp][Kp] (plane row j holds column j of
+// Q) with column exponents fcol. 64 x 32 tiles (rows x columns of Q) transposed
+// through shared memory: each thread keeps eight loads in flight, and each warp
+// writes a plane row's 64 digits as one 128-byte line.
+template <int K, bool FLT>
+__global__ void __launch_bounds__(256)
+k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, const int* __restrict__ fexp,
+             uint16_t* __restrict__ planes, int* __restrict__ fcol, double* __restrict__ qdiag,
+             unsigned int* __restrict__ status) {
+  __shared__ __align__(16) uint16_t tile[K][32][66];  // [plane][column of Q][row of Q], rows padded
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * 64;  // rows of Q (the K dimension)
+  const int64_t j0 = (int64_t)blockIdx.y * 32;  // columns of Q
+  const int64_t j = j0 + tx;
+  const int Ej = (j < N) ? fexp[j] : 0;
+  const bool bad = (Ej == 0x7FF);
+  if (blockIdx.x == 0 && ty == 0 && j < Rp) {
+    fcol[j] = (j < N && !bad) ? Ej - 1021 : 0;
+    qdiag[j] = (j < N && !bad) ? __ldg(Q + j * N + j) : 0.0;
+    if (bad) atomicOr(status, STATUS_NONFINITE);
+  }
+  const int Emax = max(Ej, 1);
+  double x[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int64_t i = i0 + ty + 8 * r;
+    x[r] = (i < N && j < N && i != j && !bad) ? __ldg(Q + i * N + j) : 0.0;
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    uint32_t d[K];
+    terms<K, FLT>(x[r], Emax, d);
+#pragma unroll
+    for (int p = 0; p < K; ++p) tile[p][tx][ty + 8 * r] = (uint16_t)d[p];
+  }
+  __syncthreads();
+  const size_t plane = (size_t)Rp * Kp;
+  uint32_t* out = reinterpret_cast<uint32_t*>(planes);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int jl = ty + 8 * r;
+    const int64_t jj = j0 + jl, ii = i0 + 2 * tx;
+    if (jj < Rp && ii < Kp) {
+#pragma unroll
+      for (int p = 0; p < K; ++p)
+        out[(p * plane + (size_t)jj * Kp + ii) >> 1] = *reinterpret_cast<const uint32_t*>(&tile[p][jl][2 * tx]);
+    }
+  }
+}
+
+template <int K, bool FLT>
+cudaError_t split_both(const double* P, const double* Q, int64_t N, int64_t Rp, uint16_t* Ps, uint16_t* Qs,
+                       int* erow, int* fcol, int* fexp, double* pdiag, double* qdiag, unsigned int* status,
+                       cudaStream_t st) {
+  k_split_rows<K, FLT><<<(unsigned)((Rp + 7) / 8), 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
+  cudaError_t err = cudaMemsetAsync(fexp, 0, (size_t)N * sizeof(int), st);
+  if (err != cudaSuccess) return err;
+  const int64_t colblocks = (N + 255) / 256;
+  int64_t slabs = (304 + colblocks - 1) / colblocks;
+  slabs = std::min<int64_t>(slabs, (N + 63) / 64);
+  const int64_t rows_per = (N + slabs - 1) / slabs;
+  k_col_maxexp<<<dim3((unsigned)colblocks, (unsigned)slabs), 256, 0, st>>>(Q, N, rows_per, fexp);
+  k_split_cols<K, FLT><<<dim3((unsigned)(Rp / 64), (unsigned)(Rp / 32)), 256, 0, st>>>(Q, N, Rp, Rp, fexp, Qs, fcol,
+                                                                                   qdiag, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool ozaki_supported(int64_t N) { return N >= 1 && N <= 16384; }
+
+// Bytes of the layout in slices.h.
+size_t ozaki_workspace_bytes(int64_t N, int slices) {
+  const int64_t Rp = padded(N);
+  return 256 + 3 * (size_t)Rp * sizeof(int) + 256 + 2 * (size_t)Rp * sizeof(double) + 256 +
+         2 * (size_t)slices * Rp * Rp * 2;
+}
+
+
+template <bool FLT>
+cudaError_t split_k(const double* P, const double* Q, int64_t N, int slices, const OzLayout& L, unsigned int* flag,
+                    cudaStream_t st) {
+  switch (slices) {
+    case 2: return split_both<2, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 3: return split_both<3, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 4: return split_both<4, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 5: return split_both<5, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 6: return split_both<6, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    case 7: return split_both<7, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    default: return split_both<8, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+  }
+}
+
+cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices, void* work, unsigned int* flag,
+                        cudaStream_t st, bool literal) {
+  if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
+  const OzLayout L = layout(work, N, slices);
+  return literal ? split_k<true>(P, Q, N, slices, L, flag, st) : split_k<false>(P, Q, N, slices, L, flag, st);
+}
+
+}  // namespace bbc
