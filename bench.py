@@ -591,6 +591,7 @@ def run_small(args, torch, dist, api, rank, world, local):
     A = W.small_case()
     h = api.Handle(local)
     h.batch_reserve(64)
+    csize, _ = h.batch_launch_shape(1)   # one matrix: a cluster of CTAs shares it
     a = torch.from_numpy(A).cuda()
     o = torch.empty_like(a)
     batch = api.Batch([a], [o])
@@ -628,7 +629,7 @@ def run_small(args, torch, dist, api, rank, world, local):
         "metric": METRICS["small"], "value": 1e6 / us_graph, "unit": "expm/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC["small"], "exp_per_step": reps},
+        "config": {"workload": WORKLOAD_DESC["small"], "exp_per_step": reps, "ctas_per_matrix": csize},
         "us_per_expm_graph": us_graph, "single_call": us_call,
         "roofline": {"bound": "latency", "achieved": flops / (us_graph * 1e-6) / 1e12, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": flops / (us_graph * 1e-6) / 1e12 / FP64_PEAK_TFLOPS,

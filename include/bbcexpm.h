@@ -229,6 +229,13 @@ int bbc_batch_tune(bbc_handle h, int64_t max_n, double tol, void* stream, uint32
 /* Install a tuning (from bbc_batch_tune, possibly cached): ctas 0 = the reserved count. */
 int bbc_batch_set_tuning(bbc_handle h, uint32_t split_mask, int ctas);
 
+/* How bbc_expm_batched would launch a batch of `count` matrices (host query, no
+ * GPU work): *csize = CTAs sharing each matrix (1, or a thread-block cluster of
+ * 2, 4, 8 or 16 CTAs on distinct SMs when the batch is small enough to leave SMs
+ * idle at one CTA per matrix) and *grid = CTAs launched. Needs
+ * bbc_batch_reserve; BBC_INVALID_ARG for count < 1 or null outputs. */
+int bbc_batch_launch_shape(bbc_handle h, int64_t count, int* csize, int* grid);
+
 /* ---- the (m, s)-proposing network (SURVEY-level extension: the paper selects
  * (m, s) from ||A||_1 alone; a proposal is only ever used once the backward-error
  * bound certifies it). A 2-hidden-layer ReLU MLP in FP32 with parameters as one

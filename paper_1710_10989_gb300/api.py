@@ -86,6 +86,7 @@ _SIGS = {
     "bbc_profile_flops": [_vp, _int, _dp],
     "bbc_batch_tune": [_vp, _i64, _dbl, _vp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int)],
     "bbc_batch_set_tuning": [_vp, ctypes.c_uint32, _int],
+    "bbc_batch_launch_shape": [_vp, ctypes.c_int64, ctypes.POINTER(_int), ctypes.POINTER(_int)],
 }
 KERNEL_PRODUCT, KERNEL_NORM, KERNEL_LINCOMB, KERNEL_SPLIT, KERNEL_BATCHED, KERNEL_ALL = 0, 1, 2, 3, 4, -1
 DTYPE_F64, DTYPE_F32 = 0, 1
@@ -200,6 +201,12 @@ class Handle:
 
     def batch_set_tuning(self, split_mask: int, ctas: int) -> None:
         _check(_lib.bbc_batch_set_tuning(self._h, split_mask & 0xFFFFFFFF, ctas))
+
+    def batch_launch_shape(self, count: int) -> tuple:
+        """(CTAs per matrix, CTAs launched) of a batch of `count` matrices."""
+        c, g = _int(), _int()
+        _check(_lib.bbc_batch_launch_shape(self._h, count, ctypes.byref(c), ctypes.byref(g)))
+        return c.value, g.value
 
     def profile_flops(self, kind: int = KERNEL_ALL) -> float:
         """Algorithmic flops of a kernel class since profile_enable (products: 2 N^3

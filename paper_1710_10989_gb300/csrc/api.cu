@@ -42,6 +42,7 @@ struct bbc_handle_s {
   bool batch_split = false;       // reservation includes the split-precision scratch
   uint32_t batch_split_mask = 0xFFFFFFFFu;  // tuned: size buckets ((N-1)/8) that use split products
   int batch_grid = 0;                       // tuned persistent CTA count (0: the reserved count)
+  BatchClusters batch_cl;                   // cluster shapes for small batches
   void* batch_work = nullptr;
   int64_t io_n = 0;               // N the host-call staging buffers are sized for
   double* io = nullptr;           // 4 * N * N doubles: device copies of two inputs and two outputs
@@ -997,6 +998,17 @@ int bbc_batch_set_tuning(bbc_handle h, uint32_t split_mask, int ctas) {
   return BBC_OK;
 }
 
+int bbc_batch_launch_shape(bbc_handle h, int64_t count, int* csize, int* grid) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (count < 1 || !csize || !grid) return fail(BBC_INVALID_ARG, "bad launch-shape query");
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (!h->batch_work) return fail(BBC_INVALID_ARG, "call bbc_batch_reserve first");
+  const int ctas = (h->batch_grid > 0 && h->batch_grid <= h->batch_ctas) ? h->batch_grid : h->batch_ctas;
+  *csize = batched_cluster_size(&h->batch_cl, count, ctas, grid);
+  return BBC_OK;
+}
+
 int bbc_mlp_sizes(int in, int hid, int out, int64_t B, int64_t* n_params, int64_t* ws_floats) {
   if (in < 1 || hid < 1 || out < 1 || B < 0 || !n_params || !ws_floats) return fail(BBC_INVALID_ARG, "bad MLP sizes");
   *n_params = mlp_param_count(in, hid, out);
@@ -1047,6 +1059,7 @@ int bbc_batch_reserve(bbc_handle h, int64_t max_n, int flags) {
     const int ctas = batched_ctas(h->device);
     BBC_CUDA(cudaMalloc(&h->batch_work, batched_workspace_bytes(nmax, ctas, want_split)));
     BBC_CUDA(batched_upload_programs());
+    BBC_CUDA(batched_cluster_probe(h->device, &h->batch_cl));
     h->batch_ctas = ctas;
     h->batch_nmax = nmax;
     h->batch_split = want_split;
@@ -1111,7 +1124,7 @@ int bbc_selector_data_batched(bbc_handle h, const void* const* dA, const int64_t
   cudaStream_t st = (cudaStream_t)stream;
   LaunchScope scope(h, BBC_KERNEL_BATCHED, st);
   const cudaError_t e = batched_launch(dA, nullptr, dNs, count, h->batch_nmax, dtype, theta, h->batch_work,
-                                       h->batch_ctas, dInfo, st, &sel);
+                                       h->batch_ctas, dInfo, st, &sel, false, 0xFFFFFFFFu, &h->batch_cl);
   if (e != cudaSuccess) return cuda_fail(e, "selector data launch");
   return BBC_OK;
 }
@@ -1157,7 +1170,7 @@ int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, in
   LaunchScope scope(h, BBC_KERNEL_BATCHED, st);
   const int ctas = (h->batch_grid > 0 && h->batch_grid <= h->batch_ctas) ? h->batch_grid : h->batch_ctas;
   const cudaError_t e = batched_launch(dA, dOut, dNs, count, h->batch_nmax, dtype, theta, h->batch_work,
-                                       ctas, dInfo, st, psel, split, h->batch_split_mask);
+                                       ctas, dInfo, st, psel, split, h->batch_split_mask, &h->batch_cl);
   if (e != cudaSuccess) return cuda_fail(e, "batched launch");
   return BBC_OK;
 }

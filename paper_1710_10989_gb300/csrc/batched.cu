@@ -31,6 +31,8 @@
 //           either bound (the closed-form rule the network is compared with);
 //  data     no exponential: features and exact ||A^k||_1, k = 1..3, for training.
 #include <math.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "bbcexpm.h"
@@ -94,6 +96,7 @@ struct BatchArgs {
   int prec;                // 0: products on the FP64 pipe; 1: 4-slice BF16 mma.sync products (N <= 256)
   uint32_t split_mask;     // prec 1: bit b set = matrices with (N - 1) / 8 == b use split products
   uint32_t* ozwork;        // per-CTA slice scratch, OZB_WORDS words each (prec 1)
+  int csize;               // CTAs per matrix: 1, or the size of the thread-block cluster sharing it
 };
 
 namespace {
@@ -107,57 +110,141 @@ __device__ int least_squarings_dev(double norm, double th) {
   return s;
 }
 
-// 64 x 64 output tiles, 16-deep K slabs, 256 threads (4 x 4 each, stride 16).
+// Slot matrices are rewritten during the launch (by other CTAs of a cluster
+// too), so they are read with ordinary loads, which the barriers' release /
+// acquire order after those writes, never through the read-only (.nc) path,
+// which nothing orders (hence no __ldg and no const __restrict__ on slot
+// pointers in this file).
+__device__ __forceinline__ double ldslot(const double* p) { return *p; }
+
+// The fused epilogue of the batched path: the same arithmetic as
+// apply_epilogue, with the matrices the outputs read loaded together (one L2
+// round trip instead of one per term). An output that overwrites a matrix that a
+// later output of the same element reads updates the loaded value, which is what
+// reading it in order would give.
+struct EpiMasks {
+  unsigned used;             // bit k: some output reads Y[k]
+  unsigned alias[MAX_OUT];   // bit k: output o writes the matrix Y[k]
+};
+__device__ __forceinline__ EpiMasks epi_masks(const Epilogue& e) {
+  EpiMasks m = {};
+  for (int o = 0; o < e.nout; ++o)
+    for (int t = 0; t < e.o[o].nt; ++t) m.used |= 1u << e.o[o].slot[t];
+  for (int o = 0; o < e.nout; ++o)
+    for (int k = 0; k < MAX_Y; ++k)
+      if (((m.used >> k) & 1u) && e.Y[k] == e.o[o].out) m.alias[o] |= 1u << k;
+  return m;
+}
+__device__ __forceinline__ void epi_batched(const Epilogue& e, const EpiMasks& m, int64_t N, int64_t row,
+                                            int64_t col, double v) {
+  const int64_t idx = row * N + col;
+  double y[MAX_Y];
+#pragma unroll
+  for (int k = 0; k < MAX_Y; ++k) y[k] = ((m.used >> k) & 1u) ? ldslot(e.Y[k] + idx) : 0.0;
+  bool bad = false;
+#pragma unroll 1
+  for (int o = 0; o < e.nout; ++o) {
+    const EpiOut& q = e.o[o];
+    double r = q.cv * v;
+    if (row == col) r += q.cI;
+#pragma unroll 1
+    for (int t = 0; t < q.nt; ++t) {
+      const int sl = q.slot[t];
+      double yv = y[0];
+#pragma unroll
+      for (int k = 1; k < MAX_Y; ++k) yv = (sl == k) ? y[k] : yv;
+      r = fma(q.c[t], yv, r);
+    }
+    q.out[idx] = r;
+    bad |= !isfinite(r);
+#pragma unroll
+    for (int k = 0; k < MAX_Y; ++k)
+      if ((m.alias[o] >> k) & 1u) y[k] = r;
+  }
+  if (bad && e.flag) atomicOr(e.flag, 1u);
+}
+
+// Output tiles of T x T (T = 64, 32 or 16), 16-deep K slabs, 256 threads
+// (R x R each with R = T / 16, stride 16); the next slab's loads are issued
+// before the current slab's FMAs. Tiles part, part + parts, ... of the product:
+// a cluster of `parts` CTAs shares one matrix. Every element sums k in the same
+// order whatever T, so the result does not depend on the partition.
 struct GemmSmem {
   double As[16][64];
   double Bs[16][64];
+  EpiMasks em;               // of the epilogue of the product in flight
 };
 
-__device__ void block_gemm_f64(const double* __restrict__ P, const double* __restrict__ Q, int N, double alpha,
-                               const Epilogue& e, GemmSmem& sm) {
+template <int T>
+__device__ void block_gemm_f64_t(const double* P, const double* Q, int N, double alpha, const Epilogue& e,
+                                 GemmSmem& sm, int part, int parts) {
+  constexpr int R = T / 16;
   const int t = threadIdx.x, tx = t % 16, ty = t / 16;
-  const int tiles = (N + 63) / 64;
-  for (int tile = 0; tile < tiles * tiles; ++tile) {
-    const int m0 = (tile / tiles) * 64, n0 = (tile % tiles) * 64;
-    double acc[4][4];
+  const int tiles = (N + T - 1) / T;
+  const EpiMasks& em = sm.em;
+  for (int tile = part; tile < tiles * tiles; tile += parts) {
+    const int m0 = (tile / tiles) * T, n0 = (tile % tiles) * T;
+    double acc[R][R];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < R; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
+    double pa[R], pb[R];
+    auto fetch = [&](int k0) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int r = t / 16 + 16 * q, c = t % 16;  // P tile T x 16
+        pa[q] = (m0 + r < N && k0 + c < N) ? ldslot(P + (int64_t)(m0 + r) * N + k0 + c) : 0.0;
+        const int r2 = t / T + (256 / T) * q, c2 = t % T;  // Q tile 16 x T
+        pb[q] = (k0 + r2 < N && n0 + c2 < N) ? ldslot(Q + (int64_t)(k0 + r2) * N + n0 + c2) : 0.0;
+      }
+    };
+    fetch(0);
     for (int k0 = 0; k0 < N; k0 += 16) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = t / 16 + 16 * q, c = t % 16;  // P tile 64 x 16
-        sm.As[c][r] = (m0 + r < N && k0 + c < N) ? P[(int64_t)(m0 + r) * N + k0 + c] : 0.0;
-        const int r2 = t / 64 + 4 * q, c2 = t % 64;  // Q tile 16 x 64
-        sm.Bs[r2][c2] = (k0 + r2 < N && n0 + c2 < N) ? Q[(int64_t)(k0 + r2) * N + n0 + c2] : 0.0;
+      for (int q = 0; q < R; ++q) {
+        sm.As[t % 16][t / 16 + 16 * q] = pa[q];
+        sm.Bs[t / T + (256 / T) * q][t % T] = pb[q];
       }
       __syncthreads();
+      if (k0 + 16 < N) fetch(k0 + 16);
 #pragma unroll
       for (int kk = 0; kk < 16; ++kk) {
-        double a[4], b[4];
+        double a[R], b[R];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = sm.As[kk][ty + 16 * i];
+        for (int i = 0; i < R; ++i) a[i] = sm.As[kk][ty + 16 * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = sm.Bs[kk][tx + 16 * j];
+        for (int j = 0; j < R; ++j) b[j] = sm.Bs[kk][tx + 16 * j];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < R; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
       }
       __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R; ++i) {
       const int row = m0 + ty + 16 * i;
       if (row >= N) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < R; ++j) {
         const int col = n0 + tx + 16 * j;
-        if (col < N) apply_epilogue(e, N, row, col, alpha * acc[i][j]);
+        if (col < N) epi_batched(e, em, N, row, col, alpha * acc[i][j]);
       }
     }
   }
+}
+
+// The largest tile that still gives every CTA of the cluster a tile.
+__device__ void block_gemm_f64(const double* P, const double* Q, int N, double alpha,
+                               const Epilogue& e, GemmSmem& sm, int part, int parts) {
+  const int t64 = (N + 63) / 64, t32 = (N + 31) / 32;
+  if (t64 * t64 >= parts)
+    block_gemm_f64_t<64>(P, Q, N, alpha, e, sm, part, parts);
+  else if (t32 * t32 >= parts)
+    block_gemm_f64_t<32>(P, Q, N, alpha, e, sm, part, parts);
+  else
+    block_gemm_f64_t<16>(P, Q, N, alpha, e, sm, part, parts);
 }
 
 // ---------------------------------------------------------------------------
@@ -211,8 +298,8 @@ __device__ __forceinline__ void ozb_digits(long long X, uint32_t (&d)[OZB_K]) {
 
 // P' rows -> Ps[p][Np][Np/2] and Q' columns -> Qt[q][Np][Np/2] (words of two BF16
 // digits, K contiguous). Returns false (CTA-uniformly) if an operand is not finite.
-__device__ bool block_split_oz(const double* __restrict__ P, const double* __restrict__ Q, int N, int Np,
-                               uint32_t* __restrict__ Ps, uint32_t* __restrict__ Qt, OzbSmem& o) {
+__device__ bool block_split_oz(const double* P, const double* Q, int N, int Np, uint32_t* Ps, uint32_t* Qt,
+                               OzbSmem& o) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int half = Np / 2;
   const size_t plane = (size_t)Np * half;
@@ -223,7 +310,7 @@ __device__ bool block_split_oz(const double* __restrict__ P, const double* __res
     bool bad = false;
     if (i < N)
       for (int j = lane; j < N; j += 32) {
-        const int E = ozb_expf(P[(int64_t)i * N + j]);
+        const int E = ozb_expf(ldslot(P + (int64_t)i * N + j));
         bad |= (E == 0x7FF);
         if (j != i) em = max(em, E);
       }
@@ -232,7 +319,7 @@ __device__ bool block_split_oz(const double* __restrict__ P, const double* __res
     if (lane == 0) {
       if (bad) o.bad = 1;
       o.rexp[i] = max(em, 1);
-      o.pdiag[i] = (i < N) ? P[(int64_t)i * N + i] : 0.0;
+      o.pdiag[i] = (i < N) ? ldslot(P + (int64_t)i * N + i) : 0.0;
     }
   }
   for (int j = tid; j < Np; j += BATCH_THREADS) {
@@ -240,20 +327,20 @@ __device__ bool block_split_oz(const double* __restrict__ P, const double* __res
     bool bad = false;
     if (j < N)
       for (int i = 0; i < N; ++i) {
-        const int E = ozb_expf(Q[(int64_t)i * N + j]);
+        const int E = ozb_expf(ldslot(Q + (int64_t)i * N + j));
         bad |= (E == 0x7FF);
         if (i != j) em = max(em, E);
       }
     if (bad) o.bad = 1;
     o.cexp[j] = max(em, 1);
-    o.qdiag[j] = (j < N) ? Q[(int64_t)j * N + j] : 0.0;
+    o.qdiag[j] = (j < N) ? ldslot(Q + (int64_t)j * N + j) : 0.0;
   }
   __syncthreads();
   if (o.bad) return false;
   for (int idx = tid; idx < Np * half; idx += BATCH_THREADS) {
     const int i = idx / half, j = 2 * (idx % half);
-    const double x0 = (i < N && j < N && j != i) ? P[(int64_t)i * N + j] : 0.0;
-    const double x1 = (i < N && j + 1 < N && j + 1 != i) ? P[(int64_t)i * N + j + 1] : 0.0;
+    const double x0 = (i < N && j < N && j != i) ? ldslot(P + (int64_t)i * N + j) : 0.0;
+    const double x1 = (i < N && j + 1 < N && j + 1 != i) ? ldslot(P + (int64_t)i * N + j + 1) : 0.0;
     uint32_t d0[OZB_K], d1[OZB_K];
     ozb_digits(ozb_fixed(x0, o.rexp[i]), d0);
     ozb_digits(ozb_fixed(x1, o.rexp[i]), d1);
@@ -262,8 +349,8 @@ __device__ bool block_split_oz(const double* __restrict__ P, const double* __res
   }
   for (int idx = tid; idx < Np * half; idx += BATCH_THREADS) {
     const int j = idx / half, i = 2 * (idx % half);
-    const double x0 = (i < N && j < N && i != j) ? Q[(int64_t)i * N + j] : 0.0;
-    const double x1 = (i + 1 < N && j < N && i + 1 != j) ? Q[(int64_t)(i + 1) * N + j] : 0.0;
+    const double x0 = (i < N && j < N && i != j) ? ldslot(Q + (int64_t)i * N + j) : 0.0;
+    const double x1 = (i + 1 < N && j < N && i + 1 != j) ? ldslot(Q + (int64_t)(i + 1) * N + j) : 0.0;
     uint32_t d0[OZB_K], d1[OZB_K];
     ozb_digits(ozb_fixed(x0, o.cexp[j]), d0);
     ozb_digits(ozb_fixed(x1, o.cexp[j]), d1);
@@ -284,14 +371,15 @@ __device__ __forceinline__ void ozb_mma(float (&c)[4], const uint32_t (&a)[4], u
 
 // alpha * (P Q) with the fused epilogue, from the slices of block_split_oz.
 // Warp tasks of 32 x 16 outputs (two m16 x two n8 tiles), 10 slice pairs.
-__device__ void block_gemm_oz(const uint32_t* __restrict__ Ps, const uint32_t* __restrict__ Qt,
-                              const double* __restrict__ P, const double* __restrict__ Q, int N, int Np,
-                              double alpha, const Epilogue& e, const OzbSmem& o) {
+__device__ void block_gemm_oz(const uint32_t* Ps, const uint32_t* Qt, const double* P, const double* Q, int N, int Np,
+                              double alpha, const Epilogue& e, const EpiMasks& em, const OzbSmem& o, int part,
+                              int parts) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
   const int half = Np / 2;
   const size_t plane = (size_t)Np * half;
   const int tn = Np / 16, tasks = (Np / 32) * tn;
-  for (int task = warp; task < tasks; task += BATCH_THREADS / 32) {
+  constexpr int WARPS = BATCH_THREADS / 32;
+  for (int task = part * WARPS + warp; task < tasks; task += parts * WARPS) {
     const int i0 = (task / tn) * 32, j0 = (task % tn) * 16;
     float acc[OZB_K][2][2][4];
 #pragma unroll
@@ -349,32 +437,67 @@ __device__ void block_gemm_oz(const uint32_t* __restrict__ Ps, const uint32_t* _
           const double scl = (ex >= -1022 && ex <= 1023) ? __longlong_as_double((long long)(ex + 1023) << 52)
                                                         : ldexp(1.0, ex);
           const double pii = o.pdiag[row], qjj = o.qdiag[col];
-          double v = fma(pii, Q[(int64_t)row * N + col], (double)R * scl);
-          v = fma(P[(int64_t)row * N + col], qjj, v);
+          double v = fma(pii, ldslot(Q + (int64_t)row * N + col), (double)R * scl);
+          v = fma(ldslot(P + (int64_t)row * N + col), qjj, v);
           if (row == col) v = fma(-pii, qjj, v);
-          apply_epilogue(e, N, row, col, alpha * v);
+          epi_batched(e, em, N, row, col, alpha * v);
         }
   }
 }
 
-__device__ void block_lincomb(int N, const Epilogue& e) {
-  for (int idx = threadIdx.x; idx < N * N; idx += BATCH_THREADS) apply_epilogue(e, N, idx / N, idx % N, 0.0);
+__device__ void block_lincomb(int N, const Epilogue& e, GemmSmem& sm, int part, int parts) {
+  if (threadIdx.x == 0) sm.em = epi_masks(e);
+  __syncthreads();
+  const EpiMasks& em = sm.em;
+  for (int idx = part * BATCH_THREADS + threadIdx.x; idx < N * N; idx += parts * BATCH_THREADS)
+    epi_batched(e, em, N, idx / N, idx % N, 0.0);
 }
 
 // One product of the program: split precision when asked and N <= 256 (and the
-// operands are finite), else the FP64 pipe.
+// operands are finite), else the FP64 pipe. In a cluster, CTA `part` of `parts`
+// forms its share of the output tiles (each CTA splits the operands into its own
+// scratch, so no slice plane crosses CTAs).
 __device__ void block_product(const BatchArgs& a, const double* P, const double* Q, int N, double alpha,
-                              const Epilogue& e, GemmSmem& sm, OzbSmem& oz) {
+                              const Epilogue& e, GemmSmem& sm, OzbSmem& oz, int part, int parts) {
+  if (threadIdx.x == 0) sm.em = epi_masks(e);
+  __syncthreads();
   if (a.prec == 1 && N <= OZB_NMAX && ((a.split_mask >> ((N - 1) >> 3)) & 1u)) {
     const int Np = (N + 31) / 32 * 32;
     uint32_t* Ps = a.ozwork + (size_t)blockIdx.x * OZB_WORDS;
     uint32_t* Qt = Ps + OZB_WORDS / 2;
     if (block_split_oz(P, Q, N, Np, Ps, Qt, oz)) {
-      block_gemm_oz(Ps, Qt, P, Q, N, Np, alpha, e, oz);
+      block_gemm_oz(Ps, Qt, P, Q, N, Np, alpha, e, sm.em, oz, part, parts);
       return;
     }
   }
-  block_gemm_f64(P, Q, N, alpha, e, sm);
+  block_gemm_f64(P, Q, N, alpha, e, sm, part, parts);
+}
+
+// Barrier over the CTAs sharing a matrix (the CTA itself when csize == 1). The
+// cluster barrier's release / acquire orders each CTA's global-memory writes
+// before the other CTAs' reads.
+__device__ __forceinline__ void csync(int csize) {
+  if (csize > 1)
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  else
+    __syncthreads();
+}
+
+// 32-bit word at `p` in the shared memory of CTA `rank` of this cluster.
+__device__ __forceinline__ uint32_t cluster_map(const void* p, int rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(remote)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+  return remote;
+}
+__device__ __forceinline__ int cluster_load(const int* p, int rank) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(cluster_map(p, rank)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void cluster_or(unsigned int* p, int rank, unsigned int v) {
+  asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(cluster_map(p, rank)), "r"(v) : "memory");
 }
 
 // max_j sum_i |M_ij| over an N x N binary64 matrix (one column per thread).
@@ -382,7 +505,7 @@ __device__ double block_norm1(const double* M, int N, double* red) {
   double best = 0.0;
   for (int j = threadIdx.x; j < N; j += BATCH_THREADS) {
     double s = 0.0;
-    for (int i = 0; i < N; ++i) s += fabs(M[(int64_t)i * N + j]);
+    for (int i = 0; i < N; ++i) s += fabs(ldslot(M + (int64_t)i * N + j));
     best = (s > best || isnan(s)) ? s : best;
   }
   for (int off = 16; off > 0; off >>= 1) {
@@ -413,7 +536,7 @@ __device__ void block_features(const double* A, int N, double norm1, float* y0, 
     for (int i = warp; i < N; i += BATCH_THREADS / 32) {
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
       for (int j = lane; j < N; j += 32) {
-        const float a = (float)A[(int64_t)i * N + j];
+        const float a = (float)ldslot(A + (int64_t)i * N + j);
         a0 = fmaf(a, src[4 * j + 0], a0);
         a1 = fmaf(a, src[4 * j + 1], a1);
         a2 = fmaf(a, src[4 * j + 2], a2);
@@ -496,17 +619,26 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
   __shared__ OzbSmem s_oz;
 
   const int tid = threadIdx.x;
+  // csize CTAs (one thread-block cluster) share each matrix: the cluster's slots,
+  // its queue entry taken by rank 0, every product and element-wise pass split
+  // by rank; the scalar work (norms, selection, features) is done by each CTA
+  // from the same data, so all agree without exchanging it.
+  const int csize = args.csize, rank = (int)(blockIdx.x % csize);
   const size_t nn_max = (size_t)args.nmax * args.nmax;
-  double* slots = args.work + (size_t)blockIdx.x * BATCH_SLOTS * nn_max;
+  double* slots = args.work + (size_t)(blockIdx.x / csize) * BATCH_SLOTS * nn_max;
 
   while (true) {
-    if (tid == 0) s_idx = (int)atomicAdd(args.counter, 1u);
-    __syncthreads();
+    if (tid == 0 && rank == 0) s_idx = (int)atomicAdd(args.counter, 1u);
+    csync(csize);
+    if (csize > 1) {
+      if (tid == 0 && rank != 0) s_idx = cluster_load(&s_idx, 0);
+      csync(csize);  // rank 0's entry is read everywhere before it changes (or its CTA exits)
+    }
     const int64_t idx = s_idx;
     if (idx >= args.count) break;
     const int64_t N64 = args.Ns[idx];
     if (N64 < 1 || N64 > args.nmax) {  // not served: report and move on
-      if (tid == 0 && args.info) {
+      if (tid == 0 && rank == 0 && args.info) {
         bbc_info inf = {};
         inf.status = BBC_INVALID_ARG;
         args.info[idx] = inf;
@@ -517,17 +649,49 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
     const int N = (int)N64;
     double* A64 = slots + (size_t)BSL_A * nn_max;
 
-    // ---- a1: load A as binary64 and take ||A||_1 (one column per thread)
+    // ---- a1: load A as binary64 and take ||A||_1. G threads share a column
+    // (G = 4, 2, 1 for N <= 64, 128, larger; thread g sums rows g, g + G, ...,
+    // then the G partial sums add in order), and each thread issues 8 loads
+    // before its stores: a store may alias the next load for all the compiler
+    // knows, so one load per store would cost a memory round trip per element.
+    const int G = N <= 64 ? 4 : (N <= 128 ? 2 : 1);
+    const int CW = BATCH_THREADS / G;  // columns per pass
+    const int g = tid / CW, jj = tid % CW;
+    double* colpart = reinterpret_cast<double*>(&s_y[0][0]);  // G x CW partial sums
+    const void* Ain = args.A[idx];
     double colmax = 0.0;
-    for (int j = tid; j < N; j += BATCH_THREADS) {
+    for (int j0 = 0; j0 < N; j0 += CW) {
+      const int j = j0 + jj;
       double s = 0.0;
-      for (int i = 0; i < N; ++i) {
-        const double v = args.dtype == 1 ? (double)((const float*)args.A[idx])[(int64_t)i * N + j]
-                                         : ((const double*)args.A[idx])[(int64_t)i * N + j];
-        A64[(int64_t)i * N + j] = v;
-        s += fabs(v);
+      if (j < N) {
+        const bool own = (j % csize) == rank;
+        for (int i0 = g; i0 < N; i0 += 8 * G) {
+          double v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int64_t e = (int64_t)(i0 + u * G) * N + j;
+            v[u] = i0 + u * G >= N ? 0.0
+                   : args.dtype == 1 ? (double)static_cast<const float*>(Ain)[e]
+                                     : static_cast<const double*>(Ain)[e];
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * G;
+            if (i < N) {
+              if (own) A64[(int64_t)i * N + j] = v[u];
+              s += fabs(v[u]);
+            }
+          }
+        }
       }
-      colmax = (s > colmax || isnan(s)) ? s : colmax;
+      if (G > 1) {
+        colpart[g * CW + jj] = s;
+        __syncthreads();
+        if (g == 0)
+          for (int k = 1; k < G; ++k) s += colpart[k * CW + jj];
+        __syncthreads();
+      }
+      if (g == 0 && j < N) colmax = (s > colmax || isnan(s)) ? s : colmax;
     }
     for (int off = 16; off > 0; off >>= 1) {
       const double o = __shfl_xor_sync(0xffffffffu, colmax, off);
@@ -547,7 +711,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
       s_sel = SEL_PLAIN;
       s_status = isfinite(nrm) ? BBC_OK : BBC_NONFINITE_INPUT;
     }
-    __syncthreads();
+    csync(csize);  // A64 complete
     if (s_status == BBC_OK && (args.mode == MODE_LEARNED || args.mode == MODE_DATA))
       block_features(A64, N, s_norm, s_y[0], s_y[1], s_est, s_feat);
     if (s_status == BBC_OK && args.mode == MODE_LEARNED) {
@@ -576,8 +740,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
         }
         __syncthreads();
         // A^2 = A A, A^3 = A^2 A (split products in split mode; FP64 for training data)
-        block_product(args, k == 0 ? A64 : W0p, A64, N, 1.0, s_epi, sm, s_oz);
-        __syncthreads();
+        block_product(args, k == 0 ? A64 : W0p, A64, N, 1.0, s_epi, sm, s_oz, rank, csize);
+        csync(csize);
         const double nk = block_norm1(slots + (size_t)k * nn_max, N, s_red);
         if (tid == 0) s_pnorm[k + 1] = nk;
       }
@@ -615,7 +779,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
     }
     __syncthreads();
     if (args.mode == MODE_DATA) {
-      if (tid == 0) {
+      if (tid == 0 && rank == 0) {
         const bool ok = s_status == BBC_OK;
         args.norms_out[idx * 4 + 0] = ok ? s_norm : NAN;
         for (int k = 1; k < 3; ++k) args.norms_out[idx * 4 + k] = ok ? s_pnorm[k] : NAN;
@@ -633,7 +797,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
       continue;
     }
     if (s_status != BBC_OK) {
-      if (tid == 0 && args.info) {
+      if (tid == 0 && rank == 0 && args.info) {
         bbc_info inf = {};
         inf.norm1 = s_norm;
         inf.status = s_status;
@@ -678,15 +842,15 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
       }
       __syncthreads();
       if (st.P < 0) {
-        block_lincomb(N, s_epi);
+        block_lincomb(N, s_epi, sm, rank, csize);
       } else {
         double alpha = 1.0;
         for (int p = 0; p < st.alpha_pow; ++p) alpha *= sig;
         const double* P = slots + (size_t)(st.P == SL_A ? BSL_A : st.P) * nn_max;
         const double* Q = slots + (size_t)(st.Q == SL_A ? BSL_A : st.Q) * nn_max;
-        block_product(args, P, Q, N, alpha, s_epi, sm, s_oz);
+        block_product(args, P, Q, N, alpha, s_epi, sm, s_oz, rank, csize);
       }
-      __syncthreads();
+      csync(csize);
     }
 
     // ---- a9: s squarings, ping-pong between T and the squaring slot
@@ -702,24 +866,39 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
         s_epi.o[0].nt = 0;
       }
       __syncthreads();
-      block_product(args, src, src, N, 1.0, s_epi, sm, s_oz);
-      __syncthreads();
+      block_product(args, src, src, N, 1.0, s_epi, sm, s_oz, rank, csize);
+      csync(csize);
       src = dst;
     }
 
     // ---- a10: output in the caller's type, status, info
-    for (int e = tid; e < N * N; e += BATCH_THREADS) {
-      const double v = src[e];
-      if (args.dtype == 1) {
-        const float f = (float)v;
-        ((float*)args.Out[idx])[e] = f;
-        if (!isfinite(f)) s_flag = 1u;
-      } else {
-        ((double*)args.Out[idx])[e] = v;
+    {
+      void* outp = args.Out[idx];
+      const int NN = N * N, step = csize * BATCH_THREADS;
+      for (int e0 = rank * BATCH_THREADS + tid; e0 < NN; e0 += 8 * step) {
+        double v[8];  // 8 loads in flight before the stores (as in a1)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = e0 + u * step < NN ? ldslot(src + e0 + u * step) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + u * step;
+          if (e >= NN) break;
+          if (args.dtype == 1) {
+            const float f = (float)v[u];
+            static_cast<float*>(outp)[e] = f;
+            if (!isfinite(f)) s_flag = 1u;
+          } else {
+            static_cast<double*>(outp)[e] = v[u];
+          }
+        }
       }
     }
     __syncthreads();
-    if (tid == 0 && args.info) {
+    if (csize > 1) {  // overflow seen by any CTA of the cluster -> rank 0's flag
+      if (tid == 0 && rank != 0 && s_flag) cluster_or(&s_flag, 0, 1u);
+      csync(csize);
+    }
+    if (tid == 0 && rank == 0 && args.info) {
       bbc_info inf = {};
       inf.m = s_m;
       inf.s = s;
@@ -804,9 +983,77 @@ cudaError_t batched_upload_programs() {
   return cudaMemcpyToSymbol(c_progs_pre, pre, sizeof pre);
 }
 
+// Cluster shapes for small batches: a dynamic shared-memory request that leaves
+// room for one CTA per SM (the CTAs of a cluster then sit on distinct SMs, each
+// with its own FP64 pipe) and how many clusters of 2, 4, 8, 16 CTAs fit at once.
+// Called outside stream capture (at reservation).
+cudaError_t batched_cluster_probe(int device, BatchClusters* out) {
+  *out = BatchClusters{};
+  int sms = 0, smem_sm = 0, optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  cudaFuncAttributes fa = {};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_batched_expm);
+  if (e != cudaSuccess) return e;
+  const int stat = (int)fa.sharedSizeBytes;
+  const int dyn = smem_sm / 2 + 1024 - stat;
+  if (dyn < 0 || stat + dyn > optin) return cudaSuccess;  // no cluster mode
+  e = cudaFuncSetAttribute(k_batched_expm, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batched_expm, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  out->sms = sms;
+  out->dyn_smem = dyn;
+  for (int lg = 1; lg <= 4; ++lg) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at = {};
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = 1u << lg;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(1u << lg);
+    cfg.blockDim = dim3(BATCH_THREADS);
+    cfg.dynamicSmemBytes = (size_t)dyn;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_batched_expm, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    out->max_active[lg] = n;
+  }
+  return cudaSuccess;
+}
+
+// CTAs per matrix for a batch of `count`: the cluster size (1, 2, 4, 8, 16) with
+// the fewest FP64-pipe rounds, ceil(count / clusters) / size, counting only
+// batches that leave SMs idle at one CTA per matrix. *grid gets the CTA count.
+int batched_cluster_size(const BatchClusters* cl, int64_t count, int ctas, int* grid) {
+  *grid = ctas;
+  if (!cl || cl->sms <= 0 || count < 1 || count > cl->sms / 2) return 1;
+  int best_c = 1;
+  double best = (double)((count + ctas - 1) / ctas);
+  for (int lg = 1; lg <= 4; ++lg) {
+    const int c = 1 << lg;
+    const int64_t ncl = std::min<int64_t>(std::min<int64_t>(count, cl->max_active[lg]), ctas / c);
+    if (ncl < 1) continue;
+    const double cost = (double)((count + ncl - 1) / ncl) / c;
+    if (cost < best) {
+      best = cost;
+      best_c = c;
+      *grid = (int)(ncl * c);
+    }
+  }
+  return best_c;
+}
+
 cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t* Ns, int64_t count, int64_t nmax,
                            int dtype, const double* theta, void* work, int ctas, bbc_info* info, cudaStream_t st,
-                           const BatchSelector* sel, bool split, uint32_t split_mask) {
+                           const BatchSelector* sel, bool split, uint32_t split_mask, const BatchClusters* cl) {
   static const int deg[BATCH_PROGS] = {1, 2, 4, 8, 12, 18};
   static const int prod[BATCH_PROGS] = {0, 1, 2, 3, 4, 5};
   BatchArgs a = {};
@@ -840,10 +1087,27 @@ cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t
       return cudaErrorInvalidValue;
     if (a.mode == MODE_DATA && (!a.feat_out || !a.norms_out)) return cudaErrorInvalidValue;
   }
+  int grid = ctas;
+  a.csize = batched_cluster_size(cl, count, ctas, &grid);
   cudaError_t err = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st);
   if (err != cudaSuccess) return err;
-  k_batched_expm<<<ctas, BATCH_THREADS, 0, st>>>(a);
-  return cudaGetLastError();
+  if (a.csize == 1) {
+    k_batched_expm<<<ctas, BATCH_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at = {};
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = (unsigned)a.csize;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(BATCH_THREADS);
+  cfg.dynamicSmemBytes = (size_t)cl->dyn_smem;
+  cfg.stream = st;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_batched_expm, a);
 }
 
 // Calibration matrices for the batched autotuner: count matrices of size N with

@@ -131,10 +131,20 @@ struct BatchSelector {
   float* feat_out;          // training data: count x 5
   double* norms_out;        // training data: count x 4
 };
+// Small batches (at most half as many matrices as SMs) may run with a cluster of
+// CTAs per matrix; the shapes that fit are probed once, outside stream capture.
+struct BatchClusters {
+  int sms = 0;              // 0: no cluster mode
+  int dyn_smem = 0;         // dynamic shared memory per CTA that keeps one CTA per SM
+  int max_active[5] = {};   // resident clusters of 2^i CTAs (index 0 unused)
+};
+cudaError_t batched_cluster_probe(int device, BatchClusters* out);
+int batched_cluster_size(const BatchClusters* cl, int64_t count, int ctas, int* grid);
 cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t* Ns, int64_t count,
                            int64_t nmax, int dtype, const double* theta, void* work, int ctas,
                            bbc_info* info, cudaStream_t st, const BatchSelector* sel = nullptr,
-                           bool split = false, uint32_t split_mask = 0xFFFFFFFFu);
+                           bool split = false, uint32_t split_mask = 0xFFFFFFFFu,
+                           const BatchClusters* cl = nullptr);
 // count N x N binary64 calibration matrices (uniform entries, 1-norm about norm1).
 cudaError_t calibration_matrices(double* out, int64_t N, int64_t count, uint64_t seed, double norm1, cudaStream_t st);
 

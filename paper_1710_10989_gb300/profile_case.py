@@ -25,6 +25,8 @@ def main():
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--upper", action="store_true", help="upper triangular operands (triangle products)")
+    ap.add_argument("--small", action="store_true",
+                    help="--kernel batched on --count copies of the 64 x 64 single-matrix case (binary64)")
     a = ap.parse_args()
 
     import torch
@@ -34,7 +36,7 @@ def main():
 
     flags = api.PREC_FP64 if a.precision == "fp64" else api.PREC_OZAKI | api.ozaki_slices(a.slices)
     if a.kernel == "batched":  # the batched workload's distribution, binary32 storage
-        mats = W.batch_matrices(a.count)
+        mats = [W.small_case()] * a.count if a.small else W.batch_matrices(a.count)
         h = api.Handle(0)
         bflags = 0 if a.precision == "fp64" else api.PREC_OZAKI
         h.batch_reserve(256, bflags)
