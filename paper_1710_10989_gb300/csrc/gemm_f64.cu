@@ -5,11 +5,13 @@
 // product of the method (Section 1: the cost unit of scaling and squaring) is
 // therefore bound by the FP64 pipe, not by HBM: with 64 x 64 tiles each operand
 // element is re-read N/64 times from L2, far below what the FP64 pipe can
-// consume. The kernel keeps the schedule simple: 64 x 64 x 16 tiles (32 x 32 for
-// small N, to spread a 64 x 64 matrix over more SMs), 256 threads, each thread a
-// 4 x 4 (2 x 2) register block with rows/columns strided by 16 so that shared
-// memory reads are conflict-free and epilogue accesses coalesce, and the next
-// K-slab prefetched into registers while the current one is multiplied.
+// consume. The kernel keeps the schedule simple: 64 x 64 x 16 tiles (32 x 32 up
+// to N = 512 and 16 x 16 up to N = 256, to spread small matrices over more SMs),
+// 256 threads, each thread a 4 x 4 (2 x 2, 1 x 1) register block with rows and
+// columns strided by 16 so that shared memory reads are conflict-free and
+// epilogue accesses coalesce, and the next K-slab prefetched into registers
+// while the current one is multiplied. Every element sums k in the same order
+// whatever the tile, so the tile choice changes no result.
 #include "internal.h"
 
 namespace bbc {
@@ -109,7 +111,10 @@ k_gemm_f64(const double* __restrict__ P, const double* __restrict__ Q, int64_t N
 
 cudaError_t gemm_f64(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
                      cudaStream_t st, bool upper) {
-  if (N <= 512) {
+  if (N <= 256) {  // 16 x 16 tiles: a 64 x 64 product on 16 SMs, 256 x 256 on all of them
+    dim3 grid((unsigned)((N + 15) / 16), (unsigned)((N + 15) / 16));
+    k_gemm_f64<16, 16><<<grid, THREADS, 0, st>>>(P, Q, N, alpha, e, upper ? 1 : 0);
+  } else if (N <= 512) {
     dim3 grid((unsigned)((N + 31) / 32), (unsigned)((N + 31) / 32));
     k_gemm_f64<32, 32><<<grid, THREADS, 0, st>>>(P, Q, N, alpha, e, upper ? 1 : 0);
   } else {
