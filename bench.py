@@ -585,9 +585,32 @@ def run_compare(args, torch, dist, api, rank, world, local):
     }
 
 
+def cpu_small_sample(A):
+    """The oracle on the 64 x 64 case (paper's scheme): one thread and all threads,
+    repeated for about a second each."""
+    from oracle import oracle as O
+    O.theta_array("new")
+    full = O.num_threads()
+    res = {}
+    for cores in (1, full):
+        O.set_num_threads(cores)
+        O.expm(A, "new")
+        n, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < 1.0:
+            O.expm(A, "new")
+            n += 1
+        res[cores] = n / (time.perf_counter() - t0)
+    O.set_num_threads(full)
+    return {"value": res[full], "unit": "expm/s", "cores": full, "kind": "oracle",
+            "single_core": res[1],
+            "sample": f"oracle exp(A) of the 64 x 64 case, repeated for 1 s on {full} threads and on 1"}
+
+
 def run_small(args, torch, dist, api, rank, world, local):
-    """One 64 x 64 matrix: graph-replayed single exp(A) (batched kernel, count 1)
-    and the plain bbc_expm call (two host synchronisations)."""
+    """One 64 x 64 matrix: graph-replayed exp(A) through the batched kernel (count 1:
+    a cluster of CTAs shares the matrix, (m, s) chosen on the device), the three
+    methods graph-replayed at their (m, s) through bbc_expm_fixed_async, and the
+    plain bbc_expm call (host synchronisations included)."""
     A = W.small_case()
     h = api.Handle(local)
     h.batch_reserve(64)
@@ -612,9 +635,11 @@ def run_small(args, torch, dist, api, rank, world, local):
     ms = timed(torch, dist, world, cur, graph.replay, args.steps)
     clk = clocks.stop()
     us_graph = ms * 1e3 / (args.steps * reps)
-    # single calls of bbc_expm (two host synchronisations each): the paper's scheme,
+    # single calls of bbc_expm (two host synchronisations each), and the same method
+    # at its (m, s) graph-replayed through bbc_expm_fixed_async: the paper's scheme,
     # Paterson-Stockmeyer and the Pade r_26 comparator on the same matrix
-    us_call = {}
+    us_call, us_async = {}, {}
+    status = torch.zeros(1, dtype=torch.int32, device=a.device)
     for name, fl in (("new", api.SCHEME_NEW), ("ps", api.SCHEME_PS), ("pade26", api.SCHEME_PADE26)):
         for _ in range(5):
             h.expm(a, o, 0.0, fl, cur)
@@ -623,18 +648,33 @@ def run_small(args, torch, dist, api, rank, world, local):
             info = h.expm(a, o, 0.0, fl, cur)
         us_call[name] = {"us": (time.perf_counter() - t0) / 50 * 1e6, "m": info.m, "s": info.s,
                          "products": info.products}
+        with torch.cuda.stream(stream):
+            h.expm_fixed_async(a, o, info.m, info.s, fl | api.DENSE, stream=stream, status=status)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                for _ in range(reps):
+                    h.expm_fixed_async(a, o, info.m, info.s, fl | api.DENSE, stream=stream, status=status)
+        for _ in range(args.warmup):
+            g.replay()
+        ms_a = timed(torch, dist, world, cur, g.replay, args.steps)
+        if int(status.item()) != 0:
+            raise RuntimeError(f"{name}: status {int(status.item())}")
+        us_async[name] = {"us": ms_a * 1e3 / (args.steps * reps), "m": info.m, "s": info.s,
+                          "expm_per_s": args.steps * reps / (ms_a / 1e3)}
     h.close()
+    cpu = cpu_small_sample(A) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     flops = 2.0 * 64 ** 3 * 5
     return {
         "metric": METRICS["small"], "value": 1e6 / us_graph, "unit": "expm/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC["small"], "exp_per_step": reps, "ctas_per_matrix": csize},
-        "us_per_expm_graph": us_graph, "single_call": us_call,
+        "us_per_expm_graph": us_graph, "graph_fixed": us_async, "single_call": us_call,
         "roofline": {"bound": "latency", "achieved": flops / (us_graph * 1e-6) / 1e12, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": flops / (us_graph * 1e-6) / 1e12 / FP64_PEAK_TFLOPS,
                      "traffic": None},
-        "cpu_baseline": None, "e2e": None, "gpu_launches": 2 * reps * args.steps, "clocks": clk,
+        "cpu_baseline": cpu, "e2e": None, "gpu_launches": 2 * reps * args.steps, "clocks": clk,
     }
 
 

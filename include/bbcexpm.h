@@ -75,8 +75,8 @@ typedef enum {
  * diagonal of exp(A) is exp(a_ii), the superdiagonal a divided difference of
  * exp). bbc_info.structure reports which path ran. The Pade comparator stays dense. */
 #define BBC_DENSE 0x4000   /* treat A as dense: no structure detection */
-#define BBC_UPPER 0x8000   /* bbc_gemm only: the caller guarantees P and Q are upper
-                              triangular; the product then sums only k in [i, j] */
+#define BBC_UPPER 0x8000   /* bbc_gemm and bbc_expm_fixed_async only: the caller guarantees
+                              the operands are upper triangular; products then sum only k in [i, j] */
 
 typedef struct bbc_handle_s* bbc_handle;
 
@@ -152,6 +152,18 @@ int bbc_taylor(bbc_handle h, const double* dA, int64_t N, int m, int s, double* 
  * tol <= 0 selects u = 2^-53. info (may be NULL) receives the outcome. */
 int bbc_expm(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol, int flags,
              void* stream, bbc_info* info);
+
+/* As bbc_expm_fixed with no host synchronisation and no allocation while the
+ * stream is being captured, so that it can be replayed from a CUDA graph
+ * (call it once outside the capture to size the workspace for N and the
+ * precision). No norm is read and no structure detected: A is dense unless
+ * flags hold BBC_UPPER (the caller's guarantee). dStatus (device word, may be
+ * NULL) receives, stream-ordered, bit 0 = a non-finite value in the result
+ * (a non-finite input ends there too), bit 1 = a bounded device wait expired.
+ * BBC_INVALID_ARG for a capture with too small a workspace; BBC_UNSUPPORTED for a
+ * captured Pade comparator beyond N = 1024 (its solve allocates). */
+int bbc_expm_fixed_async(bbc_handle h, const double* dA, int64_t N, double* dOut, int m, int s, int flags,
+                         void* stream, unsigned int* dStatus);
 
 /* As bbc_expm with (m, s) fixed by the caller instead of selected. */
 int bbc_expm_fixed(bbc_handle h, const double* dA, int64_t N, double* dOut, int m, int s,

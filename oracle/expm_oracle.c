@@ -53,6 +53,15 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* cap on those threads (n >= 1), for single-core and all-core timings */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 static long long g_products = 0;
 long long orc_product_count(void) { return g_products; }
 void orc_reset_product_count(void) { g_products = 0; }

@@ -56,6 +56,7 @@ def lib() -> ctypes.CDLL:
         L.orc_set_mutation.argtypes = [ctypes.c_int]
         L.orc_product_count.restype = ctypes.c_longlong
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
         L.orc_power_norms.argtypes = [i64, dp, dp]
         L.orc_select_certified.argtypes = [dp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int)]
@@ -172,6 +173,11 @@ def product_count() -> int:
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Cap the threads of the oracle's products (timing only; results do not change)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def power_norms(A) -> np.ndarray:

@@ -67,6 +67,7 @@ _SIGS = {
     "bbc_taylor": [_vp, _vp, _i64, _int, _int, _vp, _int, _vp, _ip],
     "bbc_expm": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_fixed": [_vp, _vp, _i64, _vp, _int, _int, _int, _vp, ctypes.POINTER(Info)],
+    "bbc_expm_fixed_async": [_vp, _vp, _i64, _vp, _int, _int, _int, _vp, _vp],
     "bbc_expm_host": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_host_many": [_vp, _vp, _vp, _i64, _vp, _dbl, _int, _vp, _vp],
     "bbc_batch_reserve": [_vp, _i64, _int],
@@ -276,6 +277,18 @@ class Handle:
         info = Info()
         _check(_lib.bbc_expm_fixed(self._h, pa, n, po, m, s, flags, _stream(stream), ctypes.byref(info)))
         return info
+
+    def expm_fixed_async(self, A, out, m: int, s: int, flags: int = 0, stream=None, status=None) -> None:
+        """Graph-capturable exp(A) at fixed (m, s); status: optional int32 CUDA tensor
+        (one element) receiving the status bits, stream-ordered."""
+        pa, n = _mat(A, "A")
+        po, _ = _mat(out, "out")
+        ps = None
+        if status is not None:
+            if not status.is_cuda or status.numel() < 1 or status.element_size() != 4:
+                raise ValueError("status: need a 4-byte CUDA tensor")
+            ps = status.data_ptr()
+        _check(_lib.bbc_expm_fixed_async(self._h, pa, n, po, m, s, flags, _stream(stream), ps))
 
     def expm_host(self, A, out, tol: float = 0.0, flags: int = 0, stream=None) -> Info:
         """A, out: host tensors/arrays (float64, C-contiguous, square)."""

@@ -731,6 +731,32 @@ int bbc_expm_fixed(bbc_handle h, const double* dA, int64_t N, double* dOut, int 
   return BBC_OK;
 }
 
+int bbc_expm_fixed_async(bbc_handle h, const double* dA, int64_t N, double* dOut, int m, int s, int flags,
+                         void* stream, unsigned int* dStatus) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!dA || !dOut || N <= 0) return fail(BBC_INVALID_ARG, "bad expm arguments");
+  if (overlaps(dA, dOut, N)) return fail(BBC_INVALID_ARG, "output aliases the input");
+  if ((rc = check_flags(flags))) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  BBC_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {  // nothing may be allocated inside a capture
+    if (N > h->slots_n || (split_prec(flags) && ozaki_workspace_bytes(N, split_slices(flags)) > h->ozaki_bytes))
+      return fail(BBC_INVALID_ARG, "workspace too small: run this N and precision once before the capture");
+    if ((flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE26 && N > 1024)
+      return fail(BBC_UNSUPPORTED, "the Pade comparator beyond N = 1024 cannot be captured");
+  } else if ((rc = ensure_workspace(h, N, flags))) {
+    return rc;
+  }
+  BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
+  if ((rc = run_expm(h, dA, N, dOut, m, s, flags, st, nullptr, (flags & BBC_UPPER) != 0))) return rc;
+  if (dStatus)
+    BBC_CUDA(cudaMemcpyAsync(dStatus, h->dflag, sizeof(unsigned int), cudaMemcpyDeviceToDevice, st));
+  return BBC_OK;
+}
+
 int bbc_expm(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol, int flags,
              void* stream, bbc_info* info) {
   int rc = begin(h);

@@ -262,7 +262,11 @@ def test_small_workload_pade26(h, api):
     assert rel_fro(to_host(out), want) < 1e-13
 
 
-@pytest.mark.parametrize("n,norm,nonnormal", [(96, 20.0, False), (300, 100.0, True), (257, 0.3, False)])
+# N <= 112: the shared-memory solve (one CTA per 4 right-hand sides, each factoring M);
+# 113..1024: the one-CTA global-memory solve
+@pytest.mark.parametrize("n,norm,nonnormal", [(1, 0.5, False), (7, 3.0, False), (96, 20.0, False),
+                                              (112, 40.0, False), (113, 5.0, True), (300, 100.0, True),
+                                              (257, 0.3, False)])
 def test_pade26_matches_oracle(h, api, n, norm, nonnormal):
     A = W.nonnormal_upper(n, 7, norm) if nonnormal else W.gaussian(n, 8, norm)
     out = empty_like_dev(n)
