@@ -68,7 +68,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("dense4096", "batch", "small", "large", "learned", "compare4096"),
+    ap.add_argument("--workload", choices=("dense4096", "batch", "small", "large", "learned", "compare4096",
+                                           "complex2048"),
                     default="dense4096")
     ap.add_argument("--precision", choices=("ozaki", "fp64"), default="ozaki")
     ap.add_argument("--slices", type=int, default=6,
@@ -181,6 +182,8 @@ METRICS = {
     "small": "expm/s (single 64x64 exp(A), FP64, graph-replayed)",
     "learned": "expm/s (4096 held-out matrices N in 16..512, learned certified (m,s) selection)",
     "compare4096": "expm/s (dense 4096x4096 exp(A), new Taylor scheme; Paterson-Stockmeyer and Pade r_26 beside it)",
+    "complex2048": "expm/s (dense complex 2048x2048 exp(A) via the 4096x4096 real form, rel. Frobenius error vs "
+                   "the complex oracle)",
 }
 WORKLOAD_DESC = {
     "dense4096": "dense{n}: 6 Gaussian N(0,1)/sqrt(N) (seeds 1-6) + 6 non-normal upper-triangular "
@@ -190,6 +193,7 @@ WORKLOAD_DESC = {
              "half V diag(lambda) V^-1 (cond(V)=1e3), seed 7",
     "small": "small64: N(0,1) seed 0, 1-norm 1.0, (m,s) = (18,0)",
     "compare4096": "the six Gaussian matrices of dense4096 (seeds 1-6, 1-norms 0.01,0.1,1,5,20,100)",
+    "complex2048": "complex{n}: (N(0,1) + i N(0,1)) entries, seeds 201-203, complex 1-norms 0.5, 5, 50",
     "learned": "4096 held-out matrices (GPU generator, seed 12): N uniform 16..512, 1-norms log-uniform "
                "[1e-3, 1e2], half Gaussian, half V diag(lambda) V^-1 (cond(V)=1e3)",
 }
@@ -606,6 +610,93 @@ def cpu_small_sample(A):
             "sample": f"oracle exp(A) of the 64 x 64 case, repeated for 1 s on {full} threads and on 1"}
 
 
+def complex_workload(n):
+    mats = []
+    for seed, norm in ((201, 0.5), (202, 5.0), (203, 50.0)):
+        rng = np.random.default_rng(seed)
+        A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        mats.append(A * (norm / np.max(np.sum(np.abs(A), axis=0))))
+    return mats
+
+
+def run_complex(args, torch, dist, api, rank, world, local):
+    """Complex A through bbc_expm_complex (the 2N x 2N real form on the real
+    path): the chosen product precision and FP64 beside it, errors against the
+    complex oracle on the first (cheapest) matrix."""
+    n = args.n or 2048
+    mats = complex_workload(n)
+    h = api.Handle(local)
+    stream = torch.cuda.current_stream()
+    flags = flags_for(api, args.precision, args.slices)
+    dA = [torch.from_numpy(A).cuda() for A in mats]
+    dO = [torch.empty_like(a) for a in dA]
+    infos = []
+
+    def step():
+        infos.clear()
+        for a, o in zip(dA, dO):
+            infos.append(h.expm_complex(a, o, 0.0, flags, stream))
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    h.profile_enable(True)
+    clocks.start()
+    ms = timed(torch, dist, world, stream, step, args.steps)
+    clk = clocks.stop()
+    launches, _ = h.profile_read(api.KERNEL_ALL)
+    prod_launches, prod_ms = h.profile_read(api.KERNEL_PRODUCT)
+    prod_flops = h.profile_flops(api.KERNEL_PRODUCT)
+    h.profile_enable(False)
+    value = len(mats) * args.steps * world / (ms / 1e3)
+    f64 = flags_for(api, "fp64", 0)
+    dF = [torch.empty_like(a) for a in dA]
+
+    def step64():
+        for a, o in zip(dA, dF):
+            h.expm_complex(a, o, 0.0, f64, stream)
+    step64()
+    ms64 = timed(torch, dist, world, stream, step64, 1)
+    diffs = [float(torch.linalg.norm(o - f) / torch.linalg.norm(f)) for o, f in zip(dO, dF)]
+    err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import complex_oracle as CO
+        t0 = time.perf_counter()
+        want, _ = CO.expm(mats[0])
+        dt = time.perf_counter() - t0
+        got = dO[0].cpu().numpy()
+        err = {"rel_fro_vs_complex_oracle_first": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+               "oracle_seconds": dt}
+    pk = peaks()
+    avg_ms = prod_ms / max(1, prod_launches)
+    fpl = prod_flops / max(1, prod_launches)
+    logical = fpl / (avg_ms / 1e3) / 1e12
+    if args.precision == "fp64":
+        roof = {"bound": "alu", "achieved": logical, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": logical / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_gemm_f64<64,64> on the real form"}
+    else:
+        pairs = args.slices * (args.slices + 1) // 2
+        peak = pk.get("bf16_tflops", 1899.1)
+        ex = pairs * logical
+        roof = {"bound": "tensor", "achieved": ex, "peak": peak, "unit": "TFLOP/s", "frac": ex / peak,
+                "traffic": None, "kernel": f"k_ozaki_pair ({args.slices} slices) on the real form",
+                "logical_fp64_tflops": logical}
+    h.close()
+    return {
+        "metric": METRICS["complex2048"], "value": value, "unit": "expm/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.slices}-slices(exact sums)->f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC["complex2048"].format(n=n), "n": n, "real_form_n": 2 * n,
+                   "ms": [(i.m, i.s) for i in infos], "precision": args.precision},
+        "roofline": roof, "error": err,
+        "plain_fp64": {"value": len(mats) * world / (ms64 / 1e3), "unit": "expm/s",
+                       "max_rel_fro_diff_vs_chosen": max(diffs)},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
+    }
+
+
 def run_small(args, torch, dist, api, rank, world, local):
     """One 64 x 64 matrix: graph-replayed exp(A) through the batched kernel (count 1:
     a cluster of CTAs shares the matrix, (m, s) chosen on the device), the three
@@ -792,6 +883,8 @@ def main():
         line = run_small(args, torch, dist, api, rank, world, local)
     elif args.workload == "learned":
         line = run_learned(args, torch, dist, api, rank, world, local)
+    elif args.workload == "complex2048":
+        line = run_complex(args, torch, dist, api, rank, world, local)
     elif args.workload == "compare4096":
         line = run_compare(args, torch, dist, api, rank, world, local)
     else:

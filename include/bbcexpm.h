@@ -153,6 +153,18 @@ int bbc_taylor(bbc_handle h, const double* dA, int64_t N, int m, int s, double* 
 int bbc_expm(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol, int flags,
              void* stream, bbc_info* info);
 
+/* dOut = exp(dA) for complex A (Section 2 states the problem over C):
+ * dA, dOut hold N x N complex numbers row-major with real and imaginary parts
+ * interleaved (C99 double complex, numpy / torch complex128), 16-byte aligned,
+ * device memory, not overlapping. (m, s) follow the theta rule on the complex
+ * 1-norm (column sums of moduli); the products run on the 2N x 2N real form
+ * [[Re A, -Im A], [Im A, Re A]] in the precision and scheme of `flags` (real
+ * paths unchanged: about twice the flops of complex products), and exp(A) is
+ * read back from its left column blocks. bbc_info.norm1 is the complex 1-norm.
+ * Errors as bbc_expm; BBC_UPPER is rejected (no triangular path for complex A). */
+int bbc_expm_complex(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol, int flags,
+                     void* stream, bbc_info* info);
+
 /* As bbc_expm_fixed with no host synchronisation and no allocation while the
  * stream is being captured, so that it can be replayed from a CUDA graph
  * (call it once outside the capture to size the workspace for N and the

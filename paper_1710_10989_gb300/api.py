@@ -68,6 +68,7 @@ _SIGS = {
     "bbc_expm": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_fixed": [_vp, _vp, _i64, _vp, _int, _int, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_fixed_async": [_vp, _vp, _i64, _vp, _int, _int, _int, _vp, _vp],
+    "bbc_expm_complex": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_host": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_host_many": [_vp, _vp, _vp, _i64, _vp, _dbl, _int, _vp, _vp],
     "bbc_batch_reserve": [_vp, _i64, _int],
@@ -276,6 +277,20 @@ class Handle:
         po, _ = _mat(out, "out")
         info = Info()
         _check(_lib.bbc_expm_fixed(self._h, pa, n, po, m, s, flags, _stream(stream), ctypes.byref(info)))
+        return info
+
+    def expm_complex(self, A, out, tol: float = 0.0, flags: int = 0, stream=None) -> Info:
+        """exp(A) for a square contiguous complex128 CUDA tensor A into `out` (same shape)."""
+        import torch
+        for t, name in ((A, "A"), (out, "out")):
+            if (not t.is_cuda or t.dtype != torch.complex128 or t.dim() != 2 or t.shape[0] != t.shape[1]
+                    or not t.is_contiguous()):
+                raise ValueError(f"{name}: need a contiguous square complex128 CUDA tensor")
+        if out.shape != A.shape:
+            raise ValueError("out: shape differs from A")
+        info = Info()
+        _check(_lib.bbc_expm_complex(self._h, A.data_ptr(), A.shape[0], out.data_ptr(), tol, flags,
+                                     _stream(stream), ctypes.byref(info)))
         return info
 
     def expm_fixed_async(self, A, out, m: int, s: int, flags: int = 0, stream=None, status=None) -> None:

@@ -43,6 +43,8 @@ struct bbc_handle_s {
   uint32_t batch_split_mask = 0xFFFFFFFFu;  // tuned: size buckets ((N-1)/8) that use split products
   int batch_grid = 0;                       // tuned persistent CTA count (0: the reserved count)
   BatchClusters batch_cl;                   // cluster shapes for small batches
+  double* cplx = nullptr;         // complex calls: two (2N)^2 real forms and the norm partials
+  int64_t cplx_n = 0;
   void* batch_work = nullptr;
   int64_t io_n = 0;               // N the host-call staging buffers are sized for
   double* io = nullptr;           // 4 * N * N doubles: device copies of two inputs and two outputs
@@ -550,6 +552,7 @@ int bbc_destroy(bbc_handle h) {
   cudaFree(h->ozaki);
   cudaFree(h->io);
   cudaFree(h->batch_work);
+  cudaFree(h->cplx);
   if (h->copy_in) cudaStreamDestroy(h->copy_in);
   if (h->copy_out) cudaStreamDestroy(h->copy_out);
   for (int k = 0; k < 2; ++k) {
@@ -754,6 +757,71 @@ int bbc_expm_fixed_async(bbc_handle h, const double* dA, int64_t N, double* dOut
   if ((rc = run_expm(h, dA, N, dOut, m, s, flags, st, nullptr, (flags & BBC_UPPER) != 0))) return rc;
   if (dStatus)
     BBC_CUDA(cudaMemcpyAsync(dStatus, h->dflag, sizeof(unsigned int), cudaMemcpyDeviceToDevice, st));
+  return BBC_OK;
+}
+
+int bbc_expm_complex(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol, int flags,
+                     void* stream, bbc_info* info) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!dA || !dOut || N <= 0) return fail(BBC_INVALID_ARG, "bad expm arguments");
+  if ((reinterpret_cast<uintptr_t>(dA) | reinterpret_cast<uintptr_t>(dOut)) & 15)
+    return fail(BBC_INVALID_ARG, "complex arrays must be 16-byte aligned");
+  {
+    const char* pa = (const char*)dA;
+    const char* pb = (const char*)dOut;
+    const size_t bytes = (size_t)2 * N * N * sizeof(double);
+    if (pa < pb + bytes && pb < pa + bytes) return fail(BBC_INVALID_ARG, "output aliases the input");
+  }
+  const double u = tol > 0 ? tol : std::ldexp(1.0, -53);
+  if (!valid_u(u)) return fail(BBC_INVALID_ARG, "tol out of range [2^-60, 2^-5]");
+  if ((rc = check_flags(flags))) return rc;
+  if (flags & BBC_UPPER) return fail(BBC_INVALID_ARG, "BBC_UPPER is not defined for complex calls");
+  std::lock_guard<std::mutex> lk(h->mu);
+  if ((rc = ensure_workspace(h, 2 * N, flags))) return rc;
+  if (N > h->cplx_n) {
+    if (h->cplx) BBC_CUDA(cudaFree(h->cplx));
+    h->cplx = nullptr;
+    h->cplx_n = 0;
+    BBC_CUDA(cudaMalloc(&h->cplx, ((size_t)8 * N * N + (size_t)complex_norm_partial_len(N)) * sizeof(double)));
+    h->cplx_n = N;
+  }
+  double* E = h->cplx;
+  double* Eout = E + (size_t)4 * N * N;
+  double* partial = Eout + (size_t)4 * N * N;
+  cudaStream_t st = (cudaStream_t)stream;
+  bbc_info loc{};
+  bbc_info* inf = info ? info : &loc;
+  memset(inf, 0, sizeof *inf);
+  {
+    LaunchScope scope(h, BBC_KERNEL_NORM, st);
+    const cudaError_t e = complex_norm1(dA, N, partial, h->dnorm, st);
+    if (e != cudaSuccess) return cuda_fail(e, "complex norm1");
+  }
+  double* hs = (double*)h->hstage;
+  BBC_CUDA(cudaMemcpyAsync(hs, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
+  BBC_CUDA(cudaStreamSynchronize(st));
+  inf->norm1 = hs[0];
+  if (!std::isfinite(inf->norm1)) {
+    inf->status = BBC_NONFINITE_INPUT;
+    return fail(BBC_NONFINITE_INPUT, "input holds a non-finite value");
+  }
+  int m, s;
+  select_ms(inf->norm1, u, flags & BBC_SCHEME_MASK, &m, &s);
+  BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
+  {
+    LaunchScope scope(h, BBC_KERNEL_LINCOMB, st);
+    const cudaError_t e = complex_embed(dA, N, E, st);
+    if (e != cudaSuccess) return cuda_fail(e, "complex embedding");
+  }
+  if ((rc = run_expm(h, E, 2 * N, Eout, m, s, flags, st, inf, false))) return rc;
+  {
+    LaunchScope scope(h, BBC_KERNEL_LINCOMB, st);
+    const cudaError_t e = complex_extract(Eout, N, dOut, h->dflag, st);
+    if (e != cudaSuccess) return cuda_fail(e, "complex extraction");
+  }
+  if ((rc = finish_status(h, st, &inf->status))) return rc;
+  if (inf->status) return fail(inf->status, "result holds a non-finite value");
   return BBC_OK;
 }
 

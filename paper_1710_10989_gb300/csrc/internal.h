@@ -103,6 +103,14 @@ cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double al
                           bool literal = false);
 bool ozaki_supported(int64_t N);
 
+// Complex A (interleaved real and imaginary parts, N x N row-major, 16-byte
+// aligned) through its real form E = [[Re A, -Im A], [Im A, Re A]] (complex.cu).
+// complex_norm1 needs complex_norm_partial_len(N) doubles of `partial`.
+int64_t complex_norm_partial_len(int64_t N);
+cudaError_t complex_norm1(const double* A, int64_t N, double* partial, double* dNorm, cudaStream_t st);
+cudaError_t complex_embed(const double* A, int64_t N, double* E, cudaStream_t st);
+cudaError_t complex_extract(const double* E, int64_t N, double* out, unsigned int* flag, cudaStream_t st);
+
 // Solve M X = B in place (X overwrites B, M is destroyed) (pade.cu). N > 1024 goes
 // through cuSOLVER (loaded at run time) and needs an N x N scratch matrix.
 cudaError_t lu_solve_inplace(double* M, double* B, int64_t N, unsigned int* flag, cudaStream_t st,
