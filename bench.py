@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=("dense4096", "batch", "small", "large", "learned", "compare4096",
-                                           "complex2048"),
+                                           "complex2048", "integrator"),
                     default="dense4096")
     ap.add_argument("--precision", choices=("ozaki", "fp64"), default="ozaki")
     ap.add_argument("--slices", type=int, default=6,
@@ -184,6 +184,8 @@ METRICS = {
     "compare4096": "expm/s (dense 4096x4096 exp(A), new Taylor scheme; Paterson-Stockmeyer and Pade r_26 beside it)",
     "complex2048": "expm/s (dense complex 2048x2048 exp(A) via the 4096x4096 real form, rel. Frobenius error vs "
                    "the complex oracle)",
+    "integrator": "system-steps/s (Lie-Euler steps Y <- exp(h Omega) Y, 4096 skew-symmetric systems N in 8..64, "
+                  "one persistent launch per step)",
 }
 WORKLOAD_DESC = {
     "dense4096": "dense{n}: 6 Gaussian N(0,1)/sqrt(N) (seeds 1-6) + 6 non-normal upper-triangular "
@@ -194,6 +196,8 @@ WORKLOAD_DESC = {
     "small": "small64: N(0,1) seed 0, 1-norm 1.0, (m,s) = (18,0)",
     "compare4096": "the six Gaussian matrices of dense4096 (seeds 1-6, 1-norms 0.01,0.1,1,5,20,100)",
     "complex2048": "complex{n}: (N(0,1) + i N(0,1)) entries, seeds 201-203, complex 1-norms 0.5, 5, 50",
+    "integrator": "4096 systems, seed 31: N uniform on {8,...,64}, h Omega = skew part of N(0,1) scaled to "
+                  "1-norms log-uniform [0.01, 3], Y_0 orthogonal (QR), binary64",
     "learned": "4096 held-out matrices (GPU generator, seed 12): N uniform 16..512, 1-norms log-uniform "
                "[1e-3, 1e2], half Gaussian, half V diag(lambda) V^-1 (cond(V)=1e3)",
 }
@@ -697,6 +701,76 @@ def run_complex(args, torch, dist, api, rank, world, local):
     }
 
 
+def run_integrator(args, torch, dist, api, rank, world, local):
+    """Lie-Euler steps of many orthogonal systems at once: Y_i <- exp(h Omega_i) Y_i
+    in place through bbc_expm_apply_batched, 10 steps per graph replay."""
+    count = 4096
+    rng = np.random.default_rng(31)
+    ns = rng.integers(1, 9, size=count) * 8
+    norms = np.exp(rng.uniform(np.log(0.01), np.log(3.0), size=count))
+    gens, ys = [], []
+    for n, v in zip(ns, norms):
+        G = rng.standard_normal((n, n))
+        S = G - G.T
+        gens.append(S * (v / np.max(np.sum(np.abs(S), axis=0))))
+        ys.append(np.linalg.qr(rng.standard_normal((n, n)))[0])
+    order = api.batch_order([int(n) for n in ns])
+    h = api.Handle(local)
+    h.batch_reserve(64)
+    dG = [torch.from_numpy(gens[i]).cuda() for i in order]
+    dY = [torch.from_numpy(ys[i].copy()).cuda() for i in order]
+    b = api.Batch(dG, dY, rhs=dY)
+    stream = torch.cuda.Stream()
+    per_replay = 10
+    with torch.cuda.stream(stream):
+        h.expm_apply_batched(b, stream=stream)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(per_replay):
+                h.expm_apply_batched(b, stream=stream)
+    cur = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        g.replay()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = timed(torch, dist, world, cur, g.replay, args.steps)
+    clk = clocks.stop()
+    infos = b.infos()
+    drift = max(float(torch.linalg.norm(y.T @ y - torch.eye(y.shape[0], dtype=y.dtype, device=y.device)))
+                for y in dY[::64])
+    products = sum(i["products"] for i in infos)
+    nsorted = [int(ns[i]) for i in order]
+    flops_launch = sum(2.0 * n ** 3 * inf["products"] for n, inf in zip(nsorted, infos))
+    achieved = flops_launch * per_replay * args.steps / (ms / 1e3) / 1e12
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        k = 64
+        t0 = time.perf_counter()
+        for i in range(k):
+            O.expm(gens[i], "new")[0] @ ys[i]
+        dt = time.perf_counter() - t0
+        cpu = {"value": k / dt, "unit": "system-steps/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"oracle exp(h Omega) Y for the first {k} systems in {dt:.2f} s"}
+    h.close()
+    steps_total = count * per_replay * args.steps * world
+    return {
+        "metric": METRICS["integrator"], "value": steps_total / (ms / 1e3), "unit": "system-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC["integrator"], "count": count, "lie_euler_steps_per_replay": per_replay,
+                   "products_per_launch": products},
+        "orthogonality_drift_max": drift,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_batched_expm (FP64 products, one CTA per system)",
+                     "flops_per_launch": flops_launch},
+        "cpu_baseline": cpu, "e2e": None,
+        "gpu_launches": 2 * per_replay * args.steps, "clocks": clk,
+    }
+
+
 def run_small(args, torch, dist, api, rank, world, local):
     """One 64 x 64 matrix: graph-replayed exp(A) through the batched kernel (count 1:
     a cluster of CTAs shares the matrix, (m, s) chosen on the device), the three
@@ -883,6 +957,8 @@ def main():
         line = run_small(args, torch, dist, api, rank, world, local)
     elif args.workload == "learned":
         line = run_learned(args, torch, dist, api, rank, world, local)
+    elif args.workload == "integrator":
+        line = run_integrator(args, torch, dist, api, rank, world, local)
     elif args.workload == "complex2048":
         line = run_complex(args, torch, dist, api, rank, world, local)
     elif args.workload == "compare4096":

@@ -236,6 +236,17 @@ int bbc_batch_order(const int64_t* hNs, int64_t count, int64_t* hOrder);
 int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, int64_t count, void* const* dOut,
                      int dtype, double tol, int flags, void* stream, bbc_info* dInfo);
 
+/* Out_i = exp(A_i) B_i for every i: one step Y <- exp(h Omega) Y of an
+ * exponential (Lie-group / Magnus) integrator per matrix, in the same
+ * persistent launch as bbc_expm_batched (arguments and semantics as there).
+ * dB: device array of count device pointers, B_i of the same size and type as
+ * A_i. B_i is read before Out_i is written, so Out_i may be B_i (the update in
+ * place); Out_i must not overlap A_i. The product with B_i runs in the same
+ * precision as the others and counts in bbc_info.products. */
+int bbc_expm_apply_batched(bbc_handle h, const void* const* dA, const void* const* dB, const int64_t* dNs,
+                           int64_t count, void* const* dOut, int dtype, double tol, int flags, void* stream,
+                           bbc_info* dInfo);
+
 /* Autotuner of bbc_expm_batched (needs bbc_batch_reserve with BBC_PREC_OZAKI).
  * Times, on this GPU, calibration batches the library generates itself (entries
  * uniform on [-1, 1), 1-norm about 5, two matrices per resident CTA per size):

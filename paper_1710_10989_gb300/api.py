@@ -74,6 +74,7 @@ _SIGS = {
     "bbc_batch_reserve": [_vp, _i64, _int],
     "bbc_batch_order": [ctypes.POINTER(ctypes.c_int64), _i64, ctypes.POINTER(ctypes.c_int64)],
     "bbc_expm_batched": [_vp, _vp, _vp, _i64, _vp, _int, _dbl, _int, _vp, _vp],
+    "bbc_expm_apply_batched": [_vp, _vp, _vp, _vp, _i64, _vp, _int, _dbl, _int, _vp, _vp],
     "bbc_mlp_sizes": [_int, _int, _int, _i64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "bbc_mlp_forward": [_vp, _int, _int, _int, _vp, _i64, _vp, _vp, _vp],
     "bbc_mlp_grad": [_vp, _int, _int, _int, _vp, _vp, _i64, _vp, _vp, _vp, _vp],
@@ -241,6 +242,14 @@ class Handle:
                                      batch.o_ptrs.data_ptr(), batch.dtype, tol, flags, _stream(stream),
                                      batch.info.data_ptr()))
 
+    def expm_apply_batched(self, batch: "Batch", tol: float = 0.0, flags: int = 0, stream=None) -> None:
+        """Out_i = exp(A_i) B_i for a Batch built with `rhs` (Out_i may be B_i)."""
+        if batch.b_ptrs is None:
+            raise ValueError("the batch has no right-hand sides (Batch(..., rhs=[...]))")
+        _check(_lib.bbc_expm_apply_batched(self._h, batch.a_ptrs.data_ptr(), batch.b_ptrs.data_ptr(),
+                                           batch.ns.data_ptr(), batch.count, batch.o_ptrs.data_ptr(),
+                                           batch.dtype, tol, flags, _stream(stream), batch.info.data_ptr()))
+
     def workspace_size(self, n: int, flags: int = 0) -> int:
         b = ctypes.c_size_t()
         _check(_lib.bbc_workspace_size(self._h, n, 0, flags, ctypes.byref(b)))
@@ -347,12 +356,12 @@ class Batch:
     """Device-side descriptor arrays for bbc_expm_batched, built from lists of
     CUDA tensors (inputs and outputs stay owned by the caller)."""
 
-    def __init__(self, inputs, outputs=None):
+    def __init__(self, inputs, outputs=None, rhs=None):
         import torch
         if outputs is None:  # feature / norm extraction only
             outputs = inputs
-        if len(inputs) != len(outputs):
-            raise ValueError("inputs and outputs differ in length")
+        if len(inputs) != len(outputs) or (rhs is not None and len(rhs) != len(inputs)):
+            raise ValueError("inputs, outputs and right-hand sides differ in length")
         dt = inputs[0].dtype if inputs else torch.float32
         for a, o in zip(inputs, outputs):
             if not (a.is_cuda and o.is_cuda and a.dtype == dt and o.dtype == dt and a.is_contiguous()
@@ -365,6 +374,12 @@ class Batch:
         self.ns = torch.tensor([a.shape[0] for a in inputs], dtype=torch.int64, device="cuda")
         self.a_ptrs = torch.tensor([a.data_ptr() for a in inputs], dtype=torch.int64, device="cuda")
         self.o_ptrs = torch.tensor([o.data_ptr() for o in outputs], dtype=torch.int64, device="cuda")
+        self.b_ptrs = None
+        if rhs is not None:
+            for a, b in zip(inputs, rhs):
+                if not (b.is_cuda and b.dtype == dt and b.is_contiguous() and b.shape == a.shape):
+                    raise ValueError("right-hand sides: need contiguous CUDA tensors shaped and typed as the inputs")
+            self.b_ptrs = torch.tensor([b.data_ptr() for b in rhs], dtype=torch.int64, device="cuda")
         self.info = torch.zeros((max(1, self.count), ctypes.sizeof(Info) // 8), dtype=torch.float64,
                                 device="cuda")
 

@@ -1232,8 +1232,9 @@ int bbc_batch_order(const int64_t* hNs, int64_t count, int64_t* hOrder) {
   return BBC_OK;
 }
 
-int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, int64_t count, void* const* dOut,
-                     int dtype, double tol, int flags, void* stream, bbc_info* dInfo) {
+namespace {
+int expm_batched_impl(bbc_handle h, const void* const* dA, const void* const* dB, const int64_t* dNs, int64_t count,
+                      void* const* dOut, int dtype, double tol, int flags, void* stream, bbc_info* dInfo) {
   int rc = begin(h);
   if (rc) return rc;
   if (count < 0 || (count > 0 && (!dA || !dNs || !dOut))) return fail(BBC_INVALID_ARG, "bad batched arguments");
@@ -1264,9 +1265,22 @@ int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, in
   LaunchScope scope(h, BBC_KERNEL_BATCHED, st);
   const int ctas = (h->batch_grid > 0 && h->batch_grid <= h->batch_ctas) ? h->batch_grid : h->batch_ctas;
   const cudaError_t e = batched_launch(dA, dOut, dNs, count, h->batch_nmax, dtype, theta, h->batch_work,
-                                       ctas, dInfo, st, psel, split, h->batch_split_mask, &h->batch_cl);
+                                       ctas, dInfo, st, psel, split, h->batch_split_mask, &h->batch_cl, dB);
   if (e != cudaSuccess) return cuda_fail(e, "batched launch");
   return BBC_OK;
+}
+}  // namespace
+
+int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, int64_t count, void* const* dOut,
+                     int dtype, double tol, int flags, void* stream, bbc_info* dInfo) {
+  return expm_batched_impl(h, dA, nullptr, dNs, count, dOut, dtype, tol, flags, stream, dInfo);
+}
+
+int bbc_expm_apply_batched(bbc_handle h, const void* const* dA, const void* const* dB, const int64_t* dNs,
+                           int64_t count, void* const* dOut, int dtype, double tol, int flags, void* stream,
+                           bbc_info* dInfo) {
+  if (count > 0 && !dB) return fail(BBC_INVALID_ARG, "bad batched arguments");
+  return expm_batched_impl(h, dA, dB, dNs, count, dOut, dtype, tol, flags, stream, dInfo);
 }
 
 }  // extern "C"

@@ -77,6 +77,7 @@ enum { SEL_PLAIN = 0, SEL_LEARNED_NORM = 2, SEL_LEARNED_ALPHA = 3, SEL_LEARNED_R
 
 struct BatchArgs {
   const void* const* A;    // device array of device pointers
+  const void* const* B;    // may be null; else Out_i = exp(A_i) B_i (same type and size as A_i)
   void* const* Out;
   const int64_t* Ns;
   int64_t count;
@@ -871,6 +872,42 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
       src = dst;
     }
 
+    // ---- exp(A) B (the step of an exponential integrator): B_i copied into the
+    // A slot, free once the program has run (a copy, so Out_i may be B_i), then
+    // one more product into the other ping-pong buffer
+    int applied = 0;
+    if (args.B) {
+      const void* Bin = args.B[idx];
+      const int NN = N * N, step = csize * BATCH_THREADS;
+      for (int e0 = rank * BATCH_THREADS + tid; e0 < NN; e0 += 8 * step) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + u * step;
+          v[u] = e >= NN ? 0.0
+                 : args.dtype == 1 ? (double)static_cast<const float*>(Bin)[e] : static_cast<const double*>(Bin)[e];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (e0 + u * step < NN) A64[e0 + u * step] = v[u];
+      }
+      csync(csize);
+      double* dst = (src == Tslot) ? SQ : Tslot;
+      if (tid == 0) {
+        s_epi.nout = 1;
+        s_epi.flag = &s_flag;
+        s_epi.o[0].out = dst;
+        s_epi.o[0].cv = 1.0;
+        s_epi.o[0].cI = 0.0;
+        s_epi.o[0].nt = 0;
+      }
+      __syncthreads();
+      block_product(args, src, A64, N, 1.0, s_epi, sm, s_oz, rank, csize);
+      csync(csize);
+      src = dst;
+      applied = 1;
+    }
+
     // ---- a10: output in the caller's type, status, info
     {
       void* outp = args.Out[idx];
@@ -902,7 +939,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
       bbc_info inf = {};
       inf.m = s_m;
       inf.s = s;
-      inf.products = prog.products + s + extra_products;
+      inf.products = prog.products + s + extra_products + applied;
       inf.selector = s_sel;
       inf.norm1 = s_norm;
       inf.status = s_flag ? BBC_OVERFLOW : BBC_OK;
@@ -1053,11 +1090,13 @@ int batched_cluster_size(const BatchClusters* cl, int64_t count, int ctas, int* 
 
 cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t* Ns, int64_t count, int64_t nmax,
                            int dtype, const double* theta, void* work, int ctas, bbc_info* info, cudaStream_t st,
-                           const BatchSelector* sel, bool split, uint32_t split_mask, const BatchClusters* cl) {
+                           const BatchSelector* sel, bool split, uint32_t split_mask, const BatchClusters* cl,
+                           const void* const* B) {
   static const int deg[BATCH_PROGS] = {1, 2, 4, 8, 12, 18};
   static const int prod[BATCH_PROGS] = {0, 1, 2, 3, 4, 5};
   BatchArgs a = {};
   a.A = A;
+  a.B = B;
   a.Out = Out;
   a.Ns = Ns;
   a.count = count;
