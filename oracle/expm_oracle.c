@@ -34,7 +34,7 @@ typedef struct {
   double norm1;   /* ||A||_1 of the input */
 } orc_info;
 
-enum { ORC_NEW = 0, ORC_PS = 1, ORC_PADE26 = 2 };
+enum { ORC_NEW = 0, ORC_PS = 1, ORC_PADE26 = 2, ORC_PADE = 3 };
 
 /* ------------------------------------------------------------------------ */
 /* Planted mistakes for the negative-control tests (0 = none). Each code     */
@@ -478,12 +478,17 @@ int orc_pade(int64_t n, const double* X, int two_m, double* R) {
 /* ------------------------------------------------------------------------ */
 /* Selection of (m, s) (eq. theta with Tables 1-3)                          */
 /* theta[d] holds theta_d(u) for Taylor degree d (schemes NEW, PS) or for   */
-/* Pade order d = 2m (scheme PADE26 reads theta[26]); length >= 27.          */
+/* Pade order d = 2m (scheme PADE26 reads theta[26], scheme PADE theta[10]  */
+/* and theta[26]); length >= 27.                                            */
 /* ------------------------------------------------------------------------ */
 static const int NEW_DEG[6] = {1, 2, 4, 8, 12, 18};
 static const int NEW_PI[6] = {0, 1, 2, 3, 4, 5};   /* Table 3, new decomposition */
 static const int PS_DEG[7] = {1, 2, 4, 6, 9, 12, 16};
 static const int PS_PI[7] = {0, 1, 2, 3, 4, 5, 6}; /* Table 3, Paterson-Stockmeyer */
+/* r_10 and r_26 (eq. pade10, eq. pade26): 3 and 6 products, each plus one     */
+/* solve, whose cost is the same for both and so cannot change the choice      */
+static const int PADE_DEG[2] = {10, 26};
+static const int PADE_PI[2] = {3, 6};
 
 /* smallest s >= 0 with norm / 2^s <= th */
 static int min_squarings(double norm, double th) {
@@ -501,9 +506,9 @@ int orc_select(double norm, int scheme, const double* theta, int* m_out, int* s_
     *m_out = 26;
     *s_out = min_squarings(norm, theta[26]);
   } else {
-    const int* deg = scheme == ORC_NEW ? NEW_DEG : PS_DEG;
-    const int* pi = scheme == ORC_NEW ? NEW_PI : PS_PI;
-    const int cnt = scheme == ORC_NEW ? 6 : 7;
+    const int* deg = scheme == ORC_NEW ? NEW_DEG : scheme == ORC_PS ? PS_DEG : PADE_DEG;
+    const int* pi = scheme == ORC_NEW ? NEW_PI : scheme == ORC_PS ? PS_PI : PADE_PI;
+    const int cnt = scheme == ORC_NEW ? 6 : scheme == ORC_PS ? 7 : 2;
     int best_m = -1, best_s = 0, best_cost = 1 << 30;
     for (int i = 0; i < cnt; ++i) {
       const int s = min_squarings(norm, theta[deg[i]]);

@@ -13,7 +13,7 @@ import numpy as np
 from . import build as _build
 from . import theta as _theta
 
-SCHEMES = {"new": 0, "ps": 1, "pade26": 2}
+SCHEMES = {"new": 0, "ps": 1, "pade26": 2, "pade": 3}
 
 
 class _Info(ctypes.Structure):

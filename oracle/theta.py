@@ -130,12 +130,15 @@ def theta_pade(two_m: int, u: float = 2.0 ** -53) -> float:
 def theta_array(scheme: str, u: float = 2.0 ** -53) -> list[float]:
     """Length-27 array indexed by degree, as the C oracle's selection reads it.
     scheme 'new' / 'ps' fill Taylor degrees; 'pade26' fills index 26 with the
-    Pade threshold."""
+    Pade threshold; 'pade' fills indices 10 and 26."""
     out = [0.0] * 27
     if scheme in ("new", "ps"):
         for d in (1, 2, 4, 6, 8, 9, 12, 16, 18):
             out[d] = theta_taylor(d, u)
     elif scheme == "pade26":
+        out[26] = theta_pade(26, u)
+    elif scheme == "pade":
+        out[10] = theta_pade(10, u)
         out[26] = theta_pade(26, u)
     else:
         raise ValueError(scheme)

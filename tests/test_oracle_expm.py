@@ -9,7 +9,7 @@ import pytest
 from oracle import oracle as O
 from paper_1710_10989_gb300 import workloads as W
 
-SCHEMES = ("new", "ps", "pade26")
+SCHEMES = ("new", "ps", "pade26", "pade")
 
 
 def rel(a, b):
@@ -133,6 +133,12 @@ NEW_TABLE = [(0.01, (8, 0)), (0.1, (12, 0)), (0.5, (18, 0)), (1.0, (18, 0)), (5.
 PS_TABLE = [(0.01, (9, 0)), (0.1, (12, 0)), (1.0, (16, 1)), (5.0, (16, 3)), (100.0, (16, 8))]
 # Pade r_26 with theta_26 = 5.37 (Table 1): s = ceil(log2(norm/5.37)).
 PADE_TABLE = [(1.0, (26, 0)), (5.0, (26, 0)), (20.0, (26, 2)), (100.0, (26, 5))]
+# Pade r_10 or r_26 (3 or 6 products; the solve is common to both) with theta_10 = 0.254, theta_26 = 5.37:
+#   1: r_10 needs s = 2 (0.25 <= 0.254): cost 5 < r_26's 6 -> (10,2)
+#   2: r_10 s = 3 cost 6 = r_26 s = 0 cost 6 -> the smaller s: (26,0)
+#   20: r_10 s = 7 cost 10 ; r_26 s = 2 cost 8 -> (26,2)
+PADE_BOTH_TABLE = [(0.01, (10, 0)), (0.2, (10, 0)), (1.0, (10, 2)), (2.0, (26, 0)), (5.0, (26, 0)),
+                   (20.0, (26, 2)), (100.0, (26, 5))]
 
 
 def test_selection_tables():
@@ -142,6 +148,8 @@ def test_selection_tables():
         assert O.select(norm, "ps") == want, norm
     for norm, want in PADE_TABLE:
         assert O.select(norm, "pade26") == want, norm
+    for norm, want in PADE_BOTH_TABLE:
+        assert O.select(norm, "pade") == want, norm
 
 
 def test_selection_boundary_is_inclusive():
