@@ -562,7 +562,8 @@ def run_compare(args, torch, dist, api, rank, world, local):
     stream = torch.cuda.current_stream()
     split = api.PREC_OZAKI | api.ozaki_slices(6)
     methods = [("new", api.SCHEME_NEW, split), ("ps", api.SCHEME_PS, split), ("pade26", api.SCHEME_PADE26, split),
-               ("new_fp64", api.SCHEME_NEW, api.PREC_FP64), ("pade26_fp64", api.SCHEME_PADE26, api.PREC_FP64)]
+               ("pade", api.SCHEME_PADE, split), ("new_fp64", api.SCHEME_NEW, api.PREC_FP64),
+               ("pade26_fp64", api.SCHEME_PADE26, api.PREC_FP64), ("pade_fp64", api.SCHEME_PADE, api.PREC_FP64)]
     res = {}
     for name, scheme, prec in methods:
         rows = []
@@ -589,7 +590,9 @@ def run_compare(args, torch, dist, api, rank, world, local):
         "comparison": res,
         "wall_time_ratio_new_over_pade": {p: sum(r["ms"] for r in res[a]) / sum(r["ms"] for r in res[b])
                                           for p, a, b in (("split", "new", "pade26"),
-                                                          ("fp64", "new_fp64", "pade26_fp64"))},
+                                                          ("fp64", "new_fp64", "pade26_fp64"),
+                                                          ("split_r10_r26", "new", "pade"),
+                                                          ("fp64_r10_r26", "new_fp64", "pade_fp64"))},
     }
 
 
@@ -805,7 +808,8 @@ def run_small(args, torch, dist, api, rank, world, local):
     # Paterson-Stockmeyer and the Pade r_26 comparator on the same matrix
     us_call, us_async = {}, {}
     status = torch.zeros(1, dtype=torch.int32, device=a.device)
-    for name, fl in (("new", api.SCHEME_NEW), ("ps", api.SCHEME_PS), ("pade26", api.SCHEME_PADE26)):
+    for name, fl in (("new", api.SCHEME_NEW), ("ps", api.SCHEME_PS), ("pade26", api.SCHEME_PADE26),
+                     ("pade", api.SCHEME_PADE)):
         for _ in range(5):
             h.expm(a, o, 0.0, fl, cur)
         t0 = time.perf_counter()

@@ -46,6 +46,9 @@ typedef enum {
 #define BBC_SCHEME_NEW 0x0     /* reduced-product Taylor, degrees {1,2,4,8,12,18} (Section 3) */
 #define BBC_SCHEME_PS 0x1      /* Paterson-Stockmeyer Taylor, degrees {1,2,4,6,9,12,16} (eq. poli9) */
 #define BBC_SCHEME_PADE26 0x2  /* diagonal Pade r_26 (eq. pade26), the paper's comparator; N <= 1024 */
+#define BBC_SCHEME_PADE 0x3    /* diagonal Pade r_10 (eq. pade10, 3 products) or r_26 (6), whichever costs
+                                  fewer products + squarings (the solve is common to both), ties to
+                                  the smaller s */
 #define BBC_SCHEME_MASK 0xF
 #define BBC_PREC_FP64 0x00     /* every product on the FP64 pipe (DFMA) */
 #define BBC_PREC_OZAKI 0x10    /* products as exact BF16 slice products on tcgen05 tensor cores,

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libbbcexpm.so")
 
 OK, INVALID_ARG, NONFINITE_INPUT, OVERFLOW, CUDA_ERROR, TIMEOUT, UNSUPPORTED = range(7)
-SCHEME_NEW, SCHEME_PS, SCHEME_PADE26 = 0x0, 0x1, 0x2
+SCHEME_NEW, SCHEME_PS, SCHEME_PADE26, SCHEME_PADE = 0x0, 0x1, 0x2, 0x3
 PREC_FP64, PREC_OZAKI, PREC_SPLIT = 0x00, 0x10, 0x20
 SELECT_LEARNED, SELECT_ALPHA = 0x1000, 0x2000
 DENSE, UPPER = 0x4000, 0x8000

@@ -247,11 +247,12 @@ int select_ms(double norm, double u, int scheme, int* m, int* s) {
     *s = least_squarings(norm, theta_cached(-26, u));
     return BBC_OK;
   }
+  const bool pade = scheme == BBC_SCHEME_PADE;  // thresholds of r_2m, negative keys in the cache
   const int *deg, *prod;
   const int cnt = scheme_degrees(scheme, &deg, &prod);
   int bm = -1, bs = 0, bc = 1 << 30;
   for (int i = 0; i < cnt; ++i) {
-    const int si = least_squarings(norm, theta_cached(deg[i], u));
+    const int si = least_squarings(norm, theta_cached(pade ? -deg[i] : deg[i], u));
     const int cost = prod[i] + si;
     if (cost < bc || (cost == bc && si < bs)) { bc = cost; bm = deg[i]; bs = si; }
   }
@@ -390,7 +391,7 @@ int run_step(bbc_handle h, const StepS& st, int64_t N, const double* A, double* 
 int check_flags(int flags) {
   const int scheme = flags & BBC_SCHEME_MASK;
   const int prec = flags & BBC_PREC_MASK;
-  if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS && scheme != BBC_SCHEME_PADE26)
+  if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS && scheme != BBC_SCHEME_PADE26 && scheme != BBC_SCHEME_PADE)
     return fail(BBC_INVALID_ARG, "unknown scheme");
   if (prec != BBC_PREC_FP64 && prec != BBC_PREC_OZAKI && prec != BBC_PREC_SPLIT)
     return fail(BBC_INVALID_ARG, "unknown precision");
@@ -422,7 +423,7 @@ int run_expm(bbc_handle h, const double* A, int64_t N, double* Out, int m, int s
   if (!make_program(flags & BBC_SCHEME_MASK, m, s, &prog))
     return fail(BBC_INVALID_ARG, "degree not available in this scheme");
   if (s < 0 || s > 1100) return fail(BBC_INVALID_ARG, "squarings out of range");
-  const bool pade = (flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE26;
+  const bool pade = (flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE26 || (flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE;
   if (pade && N > 1024 && !lu_solve_large_available())
     return fail(BBC_UNSUPPORTED, "the Pade comparator beyond N = 1024 needs cuSOLVER, which is not available");
   if (pade) upper = false;
@@ -638,7 +639,7 @@ int bbc_theta_pade(int two_m, double u, double* theta) {
 
 int bbc_select(double norm1, double u, int scheme, int* m, int* s) {
   if (!m || !s || !valid_u(u)) return fail(BBC_INVALID_ARG, "bad selection query");
-  if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS && scheme != BBC_SCHEME_PADE26)
+  if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS && scheme != BBC_SCHEME_PADE26 && scheme != BBC_SCHEME_PADE)
     return fail(BBC_INVALID_ARG, "unknown scheme");
   if (!std::isfinite(norm1) || norm1 < 0) return fail(BBC_NONFINITE_INPUT, "norm not finite");
   return select_ms(norm1, u, scheme, m, s);
@@ -748,7 +749,7 @@ int bbc_expm_fixed_async(bbc_handle h, const double* dA, int64_t N, double* dOut
   if (cs != cudaStreamCaptureStatusNone) {  // nothing may be allocated inside a capture
     if (N > h->slots_n || (split_prec(flags) && ozaki_workspace_bytes(N, split_slices(flags)) > h->ozaki_bytes))
       return fail(BBC_INVALID_ARG, "workspace too small: run this N and precision once before the capture");
-    if ((flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE26 && N > 1024)
+    if (((flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE26 || (flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE) && N > 1024)
       return fail(BBC_UNSUPPORTED, "the Pade comparator beyond N = 1024 cannot be captured");
   } else if ((rc = ensure_workspace(h, N, flags))) {
     return rc;

@@ -36,8 +36,8 @@ const int NEW_DEG[6] = {1, 2, 4, 8, 12, 18};
 const int NEW_PROD[6] = {0, 1, 2, 3, 4, 5};
 const int PS_DEG[7] = {1, 2, 4, 6, 9, 12, 16};
 const int PS_PROD[7] = {0, 1, 2, 3, 4, 5, 6};
-const int PADE_DEG[1] = {26};
-const int PADE_PROD[1] = {6};
+const int PADE_DEG[2] = {10, 26};
+const int PADE_PROD[2] = {3, 6};
 
 double inv_factorial(int k) {
   double f = 1.0;
@@ -144,7 +144,8 @@ bool make_prefilled_program(int m, Program* p, int* a2_slot, int* a3_slot) {
 
 int scheme_degrees(int scheme, const int** deg, const int** products) {
   if (scheme == BBC_SCHEME_PS) { *deg = PS_DEG; *products = PS_PROD; return 7; }
-  if (scheme == BBC_SCHEME_PADE26) { *deg = PADE_DEG; *products = PADE_PROD; return 1; }
+  if (scheme == BBC_SCHEME_PADE26) { *deg = PADE_DEG + 1; *products = PADE_PROD + 1; return 1; }
+  if (scheme == BBC_SCHEME_PADE) { *deg = PADE_DEG; *products = PADE_PROD; return 2; }
   *deg = NEW_DEG; *products = NEW_PROD; return 6;
 }
 
@@ -154,7 +155,23 @@ bool make_program(int scheme, int m, int s, Program* p) {
   p->steps.clear();
   const double sig = std::ldexp(1.0, -s);     // X = sig * A
   const double sig2 = sig * sig;
-  if (scheme == BBC_SCHEME_PADE26) {           // eq. (pade26): numerator and denominator of r_26
+  if ((scheme == BBC_SCHEME_PADE26 || scheme == BBC_SCHEME_PADE) && m == 10) {  // eq. (pade10)
+    double b[6];                               // p_5(x) = sum b_j x^j, eq. (24), b_0 = 1
+    for (int j = 0; j <= 5; ++j) {
+      double v = inv_factorial(j);
+      for (int t = 0; t < j; ++t) v *= (double)(5 - t) / (double)(10 - t);
+      b[j] = v;
+    }
+    add(p, Step(SL_A, SL_A, sig2).out(Out(W0, 1.0)));                             // A2
+    add(p, Step(W0, W0, 1.0)                                                       // A4, and
+               .out(Out(W1, b[5], b[1]).t(W0, b[3]))                               // b5 A4 + b3 A2 + b1 I
+               .out(Out(W2, b[4], b[0]).t(W0, b[2])));                             // v5 = b4 A4 + b2 A2 + b0 I
+    add(p, Step(SL_A, W1, sig)                                                     // u5 = A (...), and
+               .out(Out(W8, -1.0).t(W2, 1.0))                                      // -u5 + v5
+               .out(Out(SL_T, 1.0).t(W2, 1.0)));                                   // u5 + v5
+    return true;                                                                   // then (-u + v) r = u + v
+  }
+  if (scheme == BBC_SCHEME_PADE26 || scheme == BBC_SCHEME_PADE) {  // eq. (pade26): r_26
     if (m != 26) return false;
     double b[14];                              // p_13(x) = sum b_j x^j, eq. (24), b_0 = 1
     for (int j = 0; j <= 13; ++j) {

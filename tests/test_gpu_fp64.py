@@ -276,6 +276,19 @@ def test_pade26_matches_oracle(h, api, n, norm, nonnormal):
     assert rel_fro(to_host(out), want) < 1e-12
 
 
+@pytest.mark.parametrize("norm,want", [(0.01, (10, 0)), (1.0, (10, 2)), (2.0, (26, 0)), (20.0, (26, 2))])
+def test_pade_scheme_selects_r10_or_r26(h, api, norm, want):
+    """BBC_SCHEME_PADE: r_10 (eq. pade10, 3 products) or r_26 (6 products), the
+    cheaper in products + squarings, against the oracle's same choice."""
+    A = W.gaussian(150, 12, norm)
+    out = empty_like_dev(150)
+    info = h.expm(to_dev(A), out, 0.0, api.SCHEME_PADE)
+    ref, oi = O.expm(A, "pade")
+    assert (info.m, info.s) == (oi.m, oi.s) == want
+    assert info.products == oi.products
+    assert rel_fro(to_host(out), ref) < 1e-12
+
+
 def test_pade26_beyond_single_cta_solve(h, api):
     """N > 1024: the comparator's solve goes through the blocked library LU."""
     A = W.gaussian(1500, 11, 8.0)
