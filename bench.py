@@ -479,6 +479,16 @@ def run_batch(args, torch, dist, api, rank, world, local, mats):
         inf64 = batch.infos()
         plain = {"value": len(mats) * world / (ms64 / 1e3), "unit": "expm/s", "steps": 1,
                  "mean_products": float(np.mean([i["products"] for i in inf64])), "form": "FP64 products, paper's rule"}
+        # the Pade comparator on the same batch (r_10 or r_26 by cost, FP64 products, one-CTA LU solve)
+        gp = capture(api.SCHEME_PADE, 0.0)
+        gp.replay()
+        msp = timed(torch, dist, world, cur, gp.replay, 1)
+        infp = batch.infos()
+        plain["pade_fp64"] = {"value": len(mats) * world / (msp / 1e3), "unit": "expm/s",
+                              "mean_products_plus_solve": float(np.mean([i["products"] for i in infp])),
+                              "r10_share": float(np.mean([i["m"] == 10 for i in infp])),
+                              "new_over_pade_time": ms64 / msp}
+        del gp
 
     # accuracy of the chosen form against the oracle on every 200th matrix
     from oracle import oracle as O

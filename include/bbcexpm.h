@@ -231,7 +231,10 @@ int bbc_batch_order(const int64_t* hNs, int64_t count, int64_t* hOrder);
  * Matrices are taken in array order by whichever CTA is free: put expensive
  * ones first (bbc_batch_order). Needs bbc_batch_reserve first; performs no
  * allocation and no host synchronisation (one memset and one kernel on
- * `stream`), so it can be captured in a CUDA graph. Scheme NEW only.
+ * `stream`), so it can be captured in a CUDA graph. Schemes NEW, and the Pade
+ * comparators PADE (r_10 or r_26 by cost) and PADE26, whose solve runs as
+ * Gaussian elimination with partial pivoting in one CTA per matrix; the
+ * learned and alpha selections serve scheme NEW only.
  * Products: FP64 (BBC_PREC_FP64), or with BBC_PREC_OZAKI (reserved with the
  * same flag) 4 BF16 slices on warp-level tensor-core MMAs with exact FP32
  * slice-group sums (about 32 significant bits per product; N_i <= 256, larger

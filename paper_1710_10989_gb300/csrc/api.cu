@@ -473,7 +473,11 @@ int run_expm(bbc_handle h, const double* A, int64_t N, double* Out, int m, int s
 
 // The batched path serves scheme NEW, with FP64 products or 4-slice split products.
 int batch_flags_ok(int flags) {
-  if ((flags & BBC_SCHEME_MASK) != BBC_SCHEME_NEW) return fail(BBC_UNSUPPORTED, "batched path: scheme NEW only");
+  const int scheme = flags & BBC_SCHEME_MASK;
+  if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PADE && scheme != BBC_SCHEME_PADE26)
+    return fail(BBC_UNSUPPORTED, "batched path: schemes NEW, PADE and PADE26");
+  if (scheme != BBC_SCHEME_NEW && (flags & BBC_SELECT_MASK))
+    return fail(BBC_UNSUPPORTED, "batched path: the learned and alpha selections serve scheme NEW");
   if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
     const int k = (flags >> 8) & 0xF;
     if (k != 0 && k != 4) return fail(BBC_UNSUPPORTED, "batched split products use 4 slices");
@@ -1265,8 +1269,12 @@ int expm_batched_impl(bbc_handle h, const void* const* dA, const void* const* dB
   cudaStream_t st = (cudaStream_t)stream;
   LaunchScope scope(h, BBC_KERNEL_BATCHED, st);
   const int ctas = (h->batch_grid > 0 && h->batch_grid <= h->batch_ctas) ? h->batch_grid : h->batch_ctas;
+  const int scheme = flags & BBC_SCHEME_MASK;
+  const int pade = scheme == BBC_SCHEME_PADE ? 1 : scheme == BBC_SCHEME_PADE26 ? 2 : 0;
+  const double theta_pade[2] = {theta_cached(-10, u), theta_cached(-26, u)};
   const cudaError_t e = batched_launch(dA, dOut, dNs, count, h->batch_nmax, dtype, theta, h->batch_work,
-                                       ctas, dInfo, st, psel, split, h->batch_split_mask, &h->batch_cl, dB);
+                                       ctas, dInfo, st, psel, split, h->batch_split_mask, &h->batch_cl, dB,
+                                       pade, theta_pade);
   if (e != cudaSuccess) return cuda_fail(e, "batched launch");
   return BBC_OK;
 }

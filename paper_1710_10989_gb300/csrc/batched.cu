@@ -69,6 +69,7 @@ struct BProg {
 
 __constant__ BProg c_progs[BATCH_PROGS];
 __constant__ BProg c_progs_pre[2];  // T12, T18 starting from A^2 (W0) and A^3 (W1), unscaled
+__constant__ BProg c_progs_pade[2]; // numerator and denominator of r_10 and r_26 (eq. pade10, eq. pade26)
 
 constexpr int NFEAT = 5;
 enum { MODE_PLAIN = 0, MODE_LEARNED = 1, MODE_ALPHA = 2, MODE_DATA = 3 };
@@ -98,6 +99,8 @@ struct BatchArgs {
   uint32_t split_mask;     // prec 1: bit b set = matrices with (N - 1) / 8 == b use split products
   uint32_t* ozwork;        // per-CTA slice scratch, OZB_WORDS words each (prec 1)
   int csize;               // CTAs per matrix: 1, or the size of the thread-block cluster sharing it
+  int pade;                // 0: Taylor (the paper's scheme); 1: Pade r_10 or r_26 by cost; 2: r_26 only
+  double theta_pade[2];    // theta_10, theta_26 (Pade thresholds)
 };
 
 namespace {
@@ -601,6 +604,77 @@ __device__ int block_mlp_argmax(const BatchArgs& a, const float* f, float* h1, f
   return best;
 }
 
+// The Pade comparator's solve (-u + v) R = u + v in one CTA: Gaussian
+// elimination with partial pivoting (largest |m_ik|, ties to the smaller row)
+// applied to M and the N right-hand sides B alike, then back substitution with
+// one right-hand side per thread; R overwrites B, M is destroyed. The paper
+// counts it as 4/3 of a product (Section 1). flag (may be null) is set when the
+// result is not finite.
+__device__ __noinline__ void block_lu_solve(double* M, double* B, int N, double* red, int* redi,
+                                            unsigned int* flag) {
+  __shared__ int s_piv, s_sing;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_sing = 0;
+  for (int k = 0; k < N; ++k) {
+    double best = -1.0;
+    int bi = N;
+    for (int i = k + tid; i < N; i += BATCH_THREADS) {
+      const double v = fabs(ldslot(M + (int64_t)i * N + k));
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { red[warp] = best; redi[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = -1.0;
+      int bb = N;
+      for (int w = 0; w < BATCH_THREADS / 32; ++w)
+        if (red[w] > bv || (red[w] == bv && redi[w] < bb)) { bv = red[w]; bb = redi[w]; }
+      s_piv = bb;
+      if (!(bv > 0.0)) s_sing = 1;
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != k && piv < N) {
+      for (int j = tid; j < 2 * N; j += BATCH_THREADS) {
+        double* base = j < N ? M : B;
+        const int c = j < N ? j : j - N;
+        const double t = base[(int64_t)k * N + c];
+        base[(int64_t)k * N + c] = base[(int64_t)piv * N + c];
+        base[(int64_t)piv * N + c] = t;
+      }
+    }
+    __syncthreads();
+    const double d = M[(int64_t)k * N + k];
+    for (int i = k + 1 + tid; i < N; i += BATCH_THREADS) M[(int64_t)i * N + k] /= d;
+    __syncthreads();
+    const int rows = N - k - 1, w = rows + N;
+    for (int e = tid; e < rows * w; e += BATCH_THREADS) {
+      const int i = k + 1 + e / w, c = e % w;
+      const double l = M[(int64_t)i * N + k];
+      if (c < rows) M[(int64_t)i * N + k + 1 + c] -= l * M[(int64_t)k * N + k + 1 + c];
+      else B[(int64_t)i * N + (c - rows)] -= l * B[(int64_t)k * N + (c - rows)];
+    }
+    __syncthreads();
+  }
+  bool bad = s_sing != 0;
+  for (int j = tid; j < N; j += BATCH_THREADS) {
+    for (int i = N - 1; i >= 0; --i) {
+      double x = B[(int64_t)i * N + j];
+      for (int t = i + 1; t < N; ++t) x -= M[(int64_t)i * N + t] * B[(int64_t)t * N + j];
+      x /= M[(int64_t)i * N + i];
+      B[(int64_t)i * N + j] = x;
+      bad |= !isfinite(x);
+    }
+  }
+  if (bad && flag) atomicOr(flag, 1u);
+  __syncthreads();
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchArgs args) {
@@ -608,6 +682,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
   __shared__ GemmSmem sm;
   __shared__ Epilogue s_epi;
   __shared__ double s_red[BATCH_THREADS / 32];
+  __shared__ int s_redi[BATCH_THREADS / 32];
   __shared__ int s_idx, s_m, s_s, s_prog, s_status, s_sel, s_pre;
   __shared__ double s_norm;
   __shared__ unsigned int s_flag;
@@ -755,6 +830,14 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
       const double alpha2 = s_pow ? fmax(sqrt(s_pnorm[1]), cbrt(s_pnorm[2])) * (1.0 + margin) : INFINITY;
       int bm = 0, bs = 0, bc = 1 << 30;
       bool done = false;
+      if (args.pade) {  // r_10 (3 products) or r_26 (6); the solve is common to both
+        for (int i = args.pade == 2 ? 1 : 0; i < 2; ++i) {
+          const int si = least_squarings_dev(nrm, args.theta_pade[i]);
+          const int cost = (i ? 6 : 3) + si;
+          if (cost < bc || (cost == bc && si < bs)) { bc = cost; bm = i; bs = si; }
+        }
+        done = true;
+      }
       if (args.mode == MODE_LEARNED && s_prop_m < BATCH_PROGS) {
         if (ldexp(nrm, -s_prop_s) <= args.theta[s_prop_m]) {
           bm = s_prop_m; bs = s_prop_s; done = true; s_sel = SEL_LEARNED_NORM;
@@ -774,9 +857,9 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
         if (args.mode == MODE_ALPHA) s_sel = SEL_ALPHA;
       }
       s_prog = bm;
-      s_m = args.deg[bm];
+      s_m = args.pade ? (bm ? 26 : 10) : args.deg[bm];
       s_s = bs;
-      s_pre = (s_pow && (args.deg[bm] == 12 || args.deg[bm] == 18)) ? 1 : 0;
+      s_pre = (!args.pade && s_pow && (args.deg[bm] == 12 || args.deg[bm] == 18)) ? 1 : 0;
     }
     __syncthreads();
     if (args.mode == MODE_DATA) {
@@ -809,7 +892,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
     }
     const int s = s_s;
     const double sig = ldexp(1.0, -s);
-    const BProg& prog = s_pre ? c_progs_pre[s_m == 18 ? 1 : 0] : c_progs[s_prog];
+    const BProg& prog = args.pade ? c_progs_pade[s_prog] : s_pre ? c_progs_pre[s_m == 18 ? 1 : 0] : c_progs[s_prog];
     const int extra_products = s_pow ? 2 : 0;
     double* Tslot = slots + (size_t)BSL_T * nn_max;
     double* SQ = slots + (size_t)SL_SQ * nn_max;
@@ -851,6 +934,13 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
         const double* Q = slots + (size_t)(st.Q == SL_A ? BSL_A : st.Q) * nn_max;
         block_product(args, P, Q, N, alpha, s_epi, sm, s_oz, rank, csize);
       }
+      csync(csize);
+    }
+
+    // Pade: W8 holds -u + v and T holds u + v; r = (-u + v)^-1 (u + v) overwrites T
+    // (one CTA of a cluster solves, the others wait)
+    if (args.pade) {
+      if (rank == 0) block_lu_solve(slots + (size_t)8 * nn_max, Tslot, N, s_red, s_redi, s == 0 ? &s_flag : nullptr);
       csync(csize);
     }
 
@@ -1017,7 +1107,16 @@ cudaError_t batched_upload_programs() {
     if (!make_prefilled_program(pm[i], &p, &a2, &a3) || a2 != 0 || a3 != 1 || !to_device_program(p, pm[i], &pre[i]))
       return cudaErrorInvalidValue;
   }
-  return cudaMemcpyToSymbol(c_progs_pre, pre, sizeof pre);
+  e = cudaMemcpyToSymbol(c_progs_pre, pre, sizeof pre);
+  if (e != cudaSuccess) return e;
+  BProg pd[2] = {};
+  const int pdeg[2] = {10, 26};
+  for (int i = 0; i < 2; ++i) {
+    Program p;
+    if (!make_program(BBC_SCHEME_PADE, pdeg[i], 0, &p) || !to_device_program(p, pdeg[i], &pd[i]))
+      return cudaErrorInvalidValue;
+  }
+  return cudaMemcpyToSymbol(c_progs_pade, pd, sizeof pd);
 }
 
 // Cluster shapes for small batches: a dynamic shared-memory request that leaves
@@ -1091,12 +1190,18 @@ int batched_cluster_size(const BatchClusters* cl, int64_t count, int ctas, int* 
 cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t* Ns, int64_t count, int64_t nmax,
                            int dtype, const double* theta, void* work, int ctas, bbc_info* info, cudaStream_t st,
                            const BatchSelector* sel, bool split, uint32_t split_mask, const BatchClusters* cl,
-                           const void* const* B) {
+                           const void* const* B, int pade, const double* theta_pade) {
   static const int deg[BATCH_PROGS] = {1, 2, 4, 8, 12, 18};
   static const int prod[BATCH_PROGS] = {0, 1, 2, 3, 4, 5};
   BatchArgs a = {};
   a.A = A;
   a.B = B;
+  a.pade = pade;
+  if (pade) {
+    if (!theta_pade) return cudaErrorInvalidValue;
+    a.theta_pade[0] = theta_pade[0];
+    a.theta_pade[1] = theta_pade[1];
+  }
   a.Out = Out;
   a.Ns = Ns;
   a.count = count;

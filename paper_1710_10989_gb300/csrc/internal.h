@@ -152,7 +152,8 @@ cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t
                            int64_t nmax, int dtype, const double* theta, void* work, int ctas,
                            bbc_info* info, cudaStream_t st, const BatchSelector* sel = nullptr,
                            bool split = false, uint32_t split_mask = 0xFFFFFFFFu,
-                           const BatchClusters* cl = nullptr, const void* const* B = nullptr);
+                           const BatchClusters* cl = nullptr, const void* const* B = nullptr,
+                           int pade = 0, const double* theta_pade = nullptr);
 // count N x N binary64 calibration matrices (uniform entries, 1-norm about norm1).
 cudaError_t calibration_matrices(double* out, int64_t N, int64_t count, uint64_t seed, double norm1, cudaStream_t st);
 
