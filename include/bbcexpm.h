@@ -156,6 +156,14 @@ int bbc_taylor(bbc_handle h, const double* dA, int64_t N, int m, int s, double* 
 int bbc_expm(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol, int flags,
              void* stream, bbc_info* info);
 
+/* Failure-detection self-test: one warp waits, with the bounded wait of the
+ * split-product kernel, on a device barrier that nothing ever completes. The
+ * wait gives up after about 2 s and reports it through the handle's status
+ * word, as a product whose partner CTA never arrived would; *status receives
+ * the outcome (BBC_TIMEOUT when the bound works) and the context stays usable.
+ * Returns BBC_OK when the call itself ran. Synchronises `stream`. */
+int bbc_selftest_wait(bbc_handle h, void* stream, int* status);
+
 /* dOut = exp(dA) for complex A (Section 2 states the problem over C):
  * dA, dOut hold N x N complex numbers row-major with real and imaginary parts
  * interleaved (C99 double complex, numpy / torch complex128), 16-byte aligned,

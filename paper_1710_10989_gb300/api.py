@@ -69,6 +69,7 @@ _SIGS = {
     "bbc_expm_fixed": [_vp, _vp, _i64, _vp, _int, _int, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_fixed_async": [_vp, _vp, _i64, _vp, _int, _int, _int, _vp, _vp],
     "bbc_expm_complex": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
+    "bbc_selftest_wait": [_vp, _vp, ctypes.POINTER(_int)],
     "bbc_expm_host": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_host_many": [_vp, _vp, _vp, _i64, _vp, _dbl, _int, _vp, _vp],
     "bbc_batch_reserve": [_vp, _i64, _int],
@@ -287,6 +288,12 @@ class Handle:
         info = Info()
         _check(_lib.bbc_expm_fixed(self._h, pa, n, po, m, s, flags, _stream(stream), ctypes.byref(info)))
         return info
+
+    def selftest_wait(self, stream=None) -> int:
+        """Status of a device wait that nothing completes (TIMEOUT when the bound works)."""
+        st = _int()
+        _check(_lib.bbc_selftest_wait(self._h, _stream(stream), ctypes.byref(st)))
+        return st.value
 
     def expm_complex(self, A, out, tol: float = 0.0, flags: int = 0, stream=None) -> Info:
         """exp(A) for a square contiguous complex128 CUDA tensor A into `out` (same shape)."""

@@ -765,6 +765,17 @@ int bbc_expm_fixed_async(bbc_handle h, const double* dA, int64_t N, double* dOut
   return BBC_OK;
 }
 
+int bbc_selftest_wait(bbc_handle h, void* stream, int* status) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!status) return fail(BBC_INVALID_ARG, "null status");
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
+  BBC_CUDA(wait_selftest(h->dflag, st));
+  return finish_status(h, st, status);
+}
+
 int bbc_expm_complex(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol, int flags,
                      void* stream, bbc_info* info) {
   int rc = begin(h);

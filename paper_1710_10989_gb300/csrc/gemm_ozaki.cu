@@ -209,6 +209,22 @@ __device__ __forceinline__ bool mbar_wait_warp_cl(uint64_t* bar, uint32_t parity
   if (__all_sync(0xffffffffu, mbar_try_wait_cl(bar, parity))) return true;
   return mbar_wait_warp_slow(bar, parity, cta_err, true);
 }
+// Self-test of failure detection: one warp waits, through the same bounded
+// wait as the product kernel, on an mbarrier that nothing ever arrives at. The
+// wait gives up after TIMEOUT_NS and the kernel records STATUS_TIMEOUT in the
+// status word and returns, as a product whose partner CTA never arrived would.
+__global__ void k_wait_selftest(unsigned int* status) {
+  __shared__ uint64_t bar;
+  __shared__ int err;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_warp(&bar, 0u, &err);
+  if (threadIdx.x == 0 && (!ok || err)) atomicOr(status, STATUS_TIMEOUT);
+}
 // One lane of the (converged) warp, chosen by the hardware.
 __device__ __forceinline__ bool elect_one() {
   uint32_t pred;
@@ -766,6 +782,12 @@ cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double al
                           void* work, unsigned int* flag, cudaStream_t st, bool upper, bool literal) {
   if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
   return launch_pair(layout(work, N, slices), P, Q, N, alpha, e, slices, flag, st, upper, literal);
+}
+
+cudaError_t wait_selftest(unsigned int* status, cudaStream_t st) {
+  if (!status) return cudaErrorInvalidValue;
+  k_wait_selftest<<<1, 32, 0, st>>>(status);
+  return cudaGetLastError();
 }
 
 }  // namespace bbc

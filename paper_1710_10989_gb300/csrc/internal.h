@@ -102,6 +102,9 @@ cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double al
                           int slices, void* work, unsigned int* flag, cudaStream_t st, bool upper = false,
                           bool literal = false);
 bool ozaki_supported(int64_t N);
+// One warp waits, with the product kernel's bounded wait, on an mbarrier that
+// nothing arrives at; about 2 s later bit 1 (timeout) of *status is set.
+cudaError_t wait_selftest(unsigned int* status, cudaStream_t st);
 
 // Complex A (interleaved real and imaginary parts, N x N row-major, 16-byte
 // aligned) through its real form E = [[Re A, -Im A], [Im A, Re A]] (complex.cu).

@@ -107,3 +107,17 @@ def test_capture_without_workspace_is_refused(api):
     torch.cuda.synchronize()
     assert float(y[0, 0]) == 1.0
     hh.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(h, api):
+    """Failure detection without a fault: a device wait that nothing completes
+    gives up after its bound (about 2 s), the status word says TIMEOUT, and the
+    next exp(A) on the same handle still matches the oracle."""
+    import time
+    t0 = time.perf_counter()
+    assert h.selftest_wait() == api.TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    A = W.small_case()
+    E, status = _capture_and_replay(h, api, A, 18, 0, api.SCHEME_NEW, replays=1)
+    want, _ = O.expm(A, "new", m=18, s=0)
+    assert status == 0 and rel_fro(E, want) < 1e-13
