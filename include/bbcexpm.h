@@ -39,7 +39,7 @@ typedef enum {
   BBC_OVERFLOW = 3,         /* the result holds a non-finite value */
   BBC_CUDA_ERROR = 4,       /* a CUDA call failed; bbc_last_error() has the text */
   BBC_TIMEOUT = 5,          /* a bounded device-side wait gave up */
-  BBC_UNSUPPORTED = 6       /* valid request this build or device cannot serve */
+  BBC_UNSUPPORTED = 6       /* valid request the library or device cannot serve */
 } bbc_status;
 
 /* flags: scheme in bits 0-3, product precision in bits 4-11. */
@@ -285,7 +285,7 @@ int bbc_batch_set_tuning(bbc_handle h, uint32_t split_mask, int ctas);
  * bbc_batch_reserve; BBC_INVALID_ARG for count < 1 or null outputs. */
 int bbc_batch_launch_shape(bbc_handle h, int64_t count, int* csize, int* grid);
 
-/* ---- the (m, s)-proposing network (SURVEY-level extension: the paper selects
+/* ---- the (m, s)-proposing network (an extension of the method: the paper selects
  * (m, s) from ||A||_1 alone; a proposal is only ever used once the backward-error
  * bound certifies it). A 2-hidden-layer ReLU MLP in FP32 with parameters as one
  * flat device array: W1[hid][in], b1[hid], W2[hid][hid], b2[hid], W3[out][hid],
