@@ -19,8 +19,9 @@
  *    stream). Calls that return a host-side result (bbc_info, a norm) wait
  *    for the stream once at the point that result is needed.
  *  - Every function returns a bbc_status; nothing throws across the ABI.
- *  - The library allocates device memory only in bbc_create, and in a call
- *    whose N needs a larger workspace than the handle holds (it grows then).
+ *  - The library allocates device memory only in bbc_create, bbc_batch_reserve
+ *    and a call whose N (or precision) needs a larger workspace than the
+ *    handle holds (it grows then); never inside a stream capture.
  */
 #ifndef BBCEXPM_H
 #define BBCEXPM_H
@@ -45,7 +46,9 @@ typedef enum {
 /* flags: scheme in bits 0-3, product precision in bits 4-11. */
 #define BBC_SCHEME_NEW 0x0     /* reduced-product Taylor, degrees {1,2,4,8,12,18} (Section 3) */
 #define BBC_SCHEME_PS 0x1      /* Paterson-Stockmeyer Taylor, degrees {1,2,4,6,9,12,16} (eq. poli9) */
-#define BBC_SCHEME_PADE26 0x2  /* diagonal Pade r_26 (eq. pade26), the paper's comparator; N <= 1024 */
+#define BBC_SCHEME_PADE26 0x2  /* diagonal Pade r_26 (eq. pade26), the paper's comparator; its solve
+                                  beyond N = 1024 uses cuSOLVER, loaded at run time (BBC_UNSUPPORTED
+                                  where it is absent) */
 #define BBC_SCHEME_PADE 0x3    /* diagonal Pade r_10 (eq. pade10, 3 products) or r_26 (6), whichever costs
                                   fewer products + squarings (the solve is common to both), ties to
                                   the smaller s */
@@ -84,7 +87,7 @@ typedef enum {
 typedef struct bbc_handle_s* bbc_handle;
 
 typedef struct {
-  int m;          /* Taylor degree used */
+  int m;          /* degree used: Taylor m, or 2m of the Pade approximant r_2m */
   int s;          /* squarings used */
   int products;   /* dense N x N products performed */
   int selector;   /* 0 = theta rule, 1 = caller-fixed (m, s) */
@@ -116,7 +119,9 @@ int bbc_theta_pade(int two_m, double u, double* theta);
 /* (m, s) selection (Section 4, Table 2, Table 3): minimise products(m) + s
  * subject to norm1 / 2^s <= theta_m(u), ties to the smaller s. Host-only.
  * `scheme` is BBC_SCHEME_NEW or BBC_SCHEME_PS; BBC_SCHEME_PADE26 gives m = 26
- * and the least s with norm1 / 2^s <= theta_26 (the paper's reference rule). */
+ * and the least s with norm1 / 2^s <= theta_26 (the paper's reference rule);
+ * BBC_SCHEME_PADE chooses r_10 (3 products) or r_26 (6) the same way on the
+ * Pade thresholds (m = 10 or 26). */
 int bbc_select(double norm1, double u, int scheme, int* m, int* s);
 
 /* ||A||_1 = max_j sum_i |a_ij| on the device. Writes the result to host
@@ -171,7 +176,8 @@ int bbc_selftest_wait(bbc_handle h, void* stream, int* status);
  * 1-norm (column sums of moduli); the products run on the 2N x 2N real form
  * [[Re A, -Im A], [Im A, Re A]] in the precision and scheme of `flags` (real
  * paths unchanged: about twice the flops of complex products), and exp(A) is
- * read back from its left column blocks. bbc_info.norm1 is the complex 1-norm.
+ * read back from its left column blocks. bbc_info.norm1 is the complex 1-norm;
+ * bbc_info.products counts products of the real form.
  * Errors as bbc_expm; BBC_UPPER is rejected (no triangular path for complex A). */
 int bbc_expm_complex(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol, int flags,
                      void* stream, bbc_info* info);
