@@ -224,8 +224,8 @@ int bbc_expm_host_many(bbc_handle h, const double* const* hA, const int64_t* Ns,
 #define BBC_DTYPE_F32 1
 
 /* Reserve the device workspace bbc_expm_batched needs for matrices up to
- * max_n x max_n (1 <= max_n <= 512) with `flags`. Allocates; call it before
- * any stream capture of bbc_expm_batched. */
+ * max_n x max_n (1 <= max_n <= 512) with `flags`, and probe which cluster
+ * shapes fit. Allocates; call it before any stream capture of bbc_expm_batched. */
 int bbc_batch_reserve(bbc_handle h, int64_t max_n, int flags);
 
 /* Host helper: an order of the `count` matrices with sizes hNs (host array)
@@ -243,7 +243,10 @@ int bbc_batch_order(const int64_t* hNs, int64_t count, int64_t* hOrder);
  *            products, ||A_i||_1 and status (BBC_INVALID_ARG for an N_i beyond
  *            the reservation, BBC_NONFINITE_INPUT, BBC_OVERFLOW).
  * Matrices are taken in array order by whichever CTA is free: put expensive
- * ones first (bbc_batch_order). Needs bbc_batch_reserve first; performs no
+ * ones first (bbc_batch_order). A batch of at most half as many matrices as
+ * SMs runs with a thread-block cluster of 2 to 16 CTAs per matrix, each CTA
+ * forming part of every product (bbc_batch_launch_shape reports the choice;
+ * the results are bit-identical either way). Needs bbc_batch_reserve first; performs no
  * allocation and no host synchronisation (one memset and one kernel on
  * `stream`), so it can be captured in a CUDA graph. Schemes NEW, and the Pade
  * comparators PADE (r_10 or r_26 by cost) and PADE26, whose solve runs as
