@@ -1,0 +1,55 @@
+"""Host-side checks of bench.py's JSON contract (no GPU): every workload the
+command line accepts has its metric and workload description, the descriptions
+that take the matrix size format, and a traffic record is reported only for the
+source it was measured on."""
+import hashlib
+import importlib.util
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+WORKLOADS = ("dense4096", "batch", "small", "large", "learned", "compare4096", "complex2048", "integrator")
+
+
+@pytest.mark.parametrize("workload", WORKLOADS)
+def test_every_workload_has_metric_and_description(bench, workload, monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", workload])
+    args = bench.parse()
+    assert args.workload == workload
+    assert bench.METRICS[workload]
+    assert bench.WORKLOAD_DESC[workload]
+
+
+def test_defaults_are_the_headline_run(bench, monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    args = bench.parse()
+    assert (args.gpus, args.workload, args.impl) == (1, "dense4096", "ours")
+    assert args.warmup >= 3 and args.steps >= 1
+
+
+@pytest.mark.parametrize("workload", ["dense4096", "large", "complex2048"])
+def test_sized_descriptions_format(bench, workload):
+    assert "4096" in bench.WORKLOAD_DESC[workload].format(n=4096)
+
+
+def test_traffic_record_follows_the_source(bench, monkeypatch):
+    src = "gemm_f64.cu"
+    path = os.path.join(ROOT, "paper_1710_10989_gb300", "csrc", src)
+    cur = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    monkeypatch.setitem(bench.NCU_TRAFFIC, src, (cur, 4096, 1.0e9))
+    assert bench.ncu_traffic(src, 4096) == 1.0e9
+    assert bench.ncu_traffic(src, 2048) is None          # another size: no record
+    monkeypatch.setitem(bench.NCU_TRAFFIC, src, ("0" * 64, 4096, 1.0e9))
+    assert bench.ncu_traffic(src, 4096) is None          # source changed since the capture
