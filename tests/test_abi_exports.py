@@ -83,3 +83,25 @@ def test_library_pade_selection_matches_oracle():
     import numpy as np
     for nrm in np.logspace(-3, 3, 200):
         assert api.select(float(nrm), scheme=api.SCHEME_PADE26) == O.select(float(nrm), "pade26")
+
+
+def declared_arities():
+    """{name: parameter count} of every bbc_ prototype in include/*.h."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", " ", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(bbc_\w+)\s*\(([^;{]*?)\)\s*;", text, re.S):
+            params = " ".join(m.group(2).split())
+            out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header():
+    """Each ctypes prototype of the binding takes as many arguments as the C
+    declaration, so no call marshals a shifted or missing argument."""
+    from paper_1710_10989_gb300 import api
+    arities = declared_arities()
+    assert len(arities) >= 10
+    for name, argtypes in api._SIGS.items():
+        assert name in arities, name
+        assert len(argtypes) == arities[name], (name, len(argtypes), arities[name])
