@@ -507,7 +507,9 @@ int orc_select(double norm, int scheme, const double* theta, int* m_out, int* s_
     *s_out = min_squarings(norm, theta[26]);
   } else {
     const int* deg = scheme == ORC_NEW ? NEW_DEG : scheme == ORC_PS ? PS_DEG : PADE_DEG;
-    const int* pi = scheme == ORC_NEW ? NEW_PI : scheme == ORC_PS ? PS_PI : PADE_PI;
+    static const int PADE_PI_MUT[2] = {6, 6};  /* planted (12): r_10 charged as r_26 */
+    const int* pi = scheme == ORC_NEW ? NEW_PI : scheme == ORC_PS ? PS_PI
+                    : (g_mutation == 12 ? PADE_PI_MUT : PADE_PI);
     const int cnt = scheme == ORC_NEW ? 6 : scheme == ORC_PS ? 7 : 2;
     int best_m = -1, best_s = 0, best_cost = 1 << 30;
     for (int i = 0; i < cnt; ++i) {

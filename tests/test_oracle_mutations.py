@@ -40,7 +40,9 @@ def _norm_and_selection_pins() -> bool:
     if O.norm1(np.array([[1.0, -2.0], [3.0, 4.0]])) != 6.0:
         return False
     table = [(0.01, (8, 0)), (0.1, (12, 0)), (5.0, (18, 3)), (100.0, (18, 7))]
-    return all(O.select(n, "new") == w for n, w in table)
+    pade = [(0.2, (10, 0)), (1.0, (10, 2)), (2.0, (26, 0)), (20.0, (26, 2))]
+    return (all(O.select(n, "new") == w for n, w in table)
+            and all(O.select(n, "pade") == w for n, w in pade))
 
 
 def _coefficient_pins() -> bool:
@@ -82,6 +84,7 @@ MUTATIONS = {
     9: "infinity-norm instead of 1-norm",
     10: "triangular path: superdiagonal without the divided difference of exp",
     11: "triangular path: exact diagonals not put back after the last squaring",
+    12: "Pade scheme: r_10 charged 6 products, as r_26",
 }
 
 
