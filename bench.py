@@ -99,13 +99,36 @@ def large_workload(n: int):
     return [W.large_case(i, n=n) for i in range(len(W.LARGE_NORMS))]
 
 
-def products_of(mats, u=2.0 ** -53) -> list[int]:
-    from paper_1710_10989_gb300 import api
+def products_of(mats, u=2.0 ** -53, select=None) -> list[int]:
+    """pi_m + s of each matrix's (m, s) by the theta rule: the library's selection,
+    or `select(norm, u)` (the reference arm passes the oracle's)."""
+    if select is None:
+        from paper_1710_10989_gb300 import api
+        select = api.select
     out = []
     for A in mats:
-        m, s = api.select(float(np.abs(A.astype(np.float64)).sum(axis=0).max()), u)
+        m, s = select(float(np.abs(A.astype(np.float64)).sum(axis=0).max()), u)
         out.append(PI[m] + s)
     return out
+
+
+# Order in which the reference arm's steps visit the twelve dense-workload matrices
+# (indices into dense_workload: 0-5 Gaussian, 6-11 upper triangular, norms ascending):
+# every run of four consecutive steps holds 28 products, the workload's mean of 7 per
+# matrix, so any number of steps that is a multiple of four samples the mix exactly.
+DENSE_CYCLE = (5, 6, 2, 9, 11, 0, 8, 3, 4, 7, 10, 1)
+# The pair the main arm's CPU-baseline leg times (and checks the timed form against):
+# the norm-100 Gaussian and the norm-100 upper-triangular matrix (12 products each).
+DENSE_CPU_SAMPLE = (5, 11)
+
+
+def dense_config(args, n: int, mats, prods, world: int) -> dict:
+    """The workload description both arms print (inputs and their (m, s) only)."""
+    return {"workload": WORKLOAD_DESC[args.workload].format(n=n),
+            "n": n, "matrices_per_step": len(mats), "products_per_step": sum(prods),
+            "u": "2^-53", "parallelism": "replicas" if world > 1 else "single",
+            "l2": f"inputs larger than L2 (each exp(A) streams ~10 N^2 FP64 buffers of "
+                  f"{n * n * 8 / 2 ** 20:.0f} MiB)"}
 
 
 class ClockSampler:
@@ -204,21 +227,29 @@ WORKLOAD_DESC = {
 
 
 # ------------------------------------------------------------------ CPU oracle legs
-def cpu_dense_sample(mats, prods):
-    """The oracle on the workload's first matrix (its cheapest), scaled by
-    products to expm/s of the whole workload."""
+def cpu_dense_sample(mats, prods, idx=DENSE_CPU_SAMPLE):
+    """The oracle, as it stands, on matrices `idx` of the workload (all host cores).
+    Its time per product is scaled to the workload's mean products per exp(A)
+    (the oracle's products all cost the same 2 N^3 triple loop); the sample's own
+    rate is reported beside it. Returns the baseline and the oracle's outputs."""
     from oracle import oracle as O
-    A = mats[0]
     O.theta_array("new")  # thresholds are constants: computed (and cached) before timing
+    outs, done = {}, 0
     t0 = time.perf_counter()
-    _, info = O.expm(A, "new")
+    for i in idx:
+        A = mats[i]
+        is_upper = not np.any(np.tril(A, -1))
+        outs[i], info = O.expm_upper(A, "new") if is_upper else O.expm(A, "new")
+        done += info.products
     dt = time.perf_counter() - t0
     mean_p = sum(prods) / len(prods)
-    return {"value": 1.0 / (dt / max(1, info.products) * mean_p), "unit": "expm/s",
-            "cores": O.num_threads(), "kind": "oracle",
-            "sample": (f"oracle exp(A) of the workload's first matrix (N={A.shape[0]}, 1-norm "
-                       f"{np.abs(A).sum(0).max():.3g}, {info.products} products) in {dt:.1f} s; scaled by "
-                       f"products to the workload's mean of {mean_p:.2f} products per exp(A)")}
+    cpu = {"value": 1.0 / (dt / done * mean_p), "unit": "expm/s", "cores": O.num_threads(), "kind": "oracle",
+           "value_of_sample": len(idx) / dt,
+           "sample": (f"oracle exp(A) of workload matrices {list(idx)} (N={mats[0].shape[0]}, 1-norms "
+                      f"{[round(float(np.abs(mats[i]).sum(0).max()), 3) for i in idx]}, {done} products in all) "
+                      f"in {dt:.1f} s on {O.num_threads()} threads; its seconds per product scaled to the "
+                      f"workload's mean of {mean_p:.2f} products per exp(A) (oracle selection)")}
+    return cpu, outs
 
 
 def cpu_batch_sample(mats, k=200):
@@ -234,32 +265,54 @@ def cpu_batch_sample(mats, k=200):
                       f"to binary64) in {dt:.1f} s"}
 
 
-def run_reference(args, rank: int):
+def run_reference(args, rank: int, world: int):
+    """The oracle as it stands on the host cores, on this arm's workload and config.
+    Dense workloads: each step is the oracle's exp(A) of the next matrix of the
+    workload (DENSE_CYCLE), value = matrices / seconds over the timed steps; no
+    library code is loaded. The CPU needs no warm-up: --warmup is accepted and not run."""
     if rank != 0:
         return
+    from oracle import oracle as O
     metric = METRICS[args.workload]
+    O.theta_array("new")
     if args.workload == "batch":
         mats = W.batch_matrices(min(args.count, 400))
-        leg = lambda: cpu_batch_sample(mats)  # noqa: E731
         cfg = {"workload": WORKLOAD_DESC["batch"], "count": args.count}
+        k, t_all = 0, 0.0
+        for st in range(args.steps):
+            A = mats[st % len(mats)].astype(np.float64)
+            t0 = time.perf_counter()
+            O.expm(A, "new")
+            t_all += time.perf_counter() - t0
+            k += 1
+        sample = f"one batch matrix per step (binary32 inputs promoted to binary64), {k} matrices"
     else:
         n = args.n or (W.LARGE_N if args.workload == "large" else 64 if args.workload == "small" else W.DENSE_N)
         mats = (large_workload(n) if args.workload == "large" else [W.small_case()] if args.workload == "small"
                 else dense_workload(n))
-        prods = products_of(mats)
-        leg = lambda: cpu_dense_sample(mats, prods)  # noqa: E731
-        cfg = {"workload": WORKLOAD_DESC[args.workload].format(n=n), "n": n, "matrices_per_step": len(mats)}
-    vals, r = [], None
-    for _ in range(args.steps):  # the CPU needs no warm-up steps; --warmup is accepted and not run
-        r = leg()
-        vals.append(r["value"])
-    value = statistics.median(vals)
+        prods = products_of(mats, select=lambda v, u: O.select(v, "new", u))
+        cfg = dense_config(args, n, mats, prods, world)
+        cycle = DENSE_CYCLE if len(mats) == len(DENSE_CYCLE) else tuple(range(len(mats)))
+        k, t_all, done = 0, 0.0, []
+        for st in range(args.steps):
+            i = cycle[st % len(cycle)]
+            A = mats[i]
+            is_upper = n > 1 and not np.any(np.tril(A, -1))
+            t0 = time.perf_counter()
+            _, info = O.expm_upper(A, "new") if is_upper else O.expm(A, "new")
+            t_all += time.perf_counter() - t0
+            done.append(info.products)
+            k += 1
+        sample = (f"one workload matrix per step, in the order {list(cycle)} (any four consecutive steps hold "
+                  f"the workload's mean of {sum(prods) / len(prods):.2f} products per exp(A)); {k} matrices, "
+                  f"{sum(done)} products")
+    value = k / t_all
     print(json.dumps({
         "impl": "reference", "metric": metric, "value": value, "unit": "expm/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-        "cpu_baseline": {"value": value, "unit": "expm/s", "cores": r["cores"], "kind": "oracle",
-                         "sample": "per step: " + r["sample"]},
+        "cpu_baseline": {"value": value, "unit": "expm/s", "cores": O.num_threads(), "kind": "oracle",
+                         "sample": sample, "seconds": t_all},
         "e2e": {"value": value, "unit": "expm/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
         flush=True)
 
@@ -379,7 +432,20 @@ def run_dense(args, torch, dist, api, rank, world, local):
                 "flops_per_launch": pairs * flops_per_product, "avg_launch_ms": avg_ms,
                 "launches": prod_launches, "logical_fp64_tflops": logical,
                 "split_ms_per_product": split_ms / max(1, split_launches / 3)}
-    cpu = cpu_dense_sample(mats, prods) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    # the CPU-baseline leg: the oracle timed on a sample of the workload; its outputs are
+    # also the reference the timed form's results are checked against (same (m, s))
+    cpu, oracle_check = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        idx = DENSE_CPU_SAMPLE if len(mats) == 12 else (0,)
+        cpu, outs = cpu_dense_sample(mats, prods, idx)
+        tol = 1e-12 if args.workload == "dense4096" else 1e-10
+        errs = []
+        for i in idx:
+            got = dO[i].cpu().numpy()
+            errs.append(float(np.linalg.norm(got - outs[i]) / np.linalg.norm(outs[i])))
+        oracle_check = {"matrices": list(idx), "rel_fro_vs_oracle": errs, "tolerance": tol,
+                        "tolerance_met": max(errs) <= tol}
+        del outs
     h.close()
     line = {
         "metric": METRICS[args.workload],
@@ -387,16 +453,13 @@ def run_dense(args, torch, dist, api, rank, world, local):
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.slices}-slices(exact sums)->f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC[args.workload].format(n=n),
-                   "n": n, "matrices_per_step": len(mats), "products_per_step": sum(prods),
-                   "scheme": "new (reduced-product Taylor)", "precision": args.precision,
-                   "slices": args.slices if args.precision != "fp64" else None, "u": "2^-53",
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "structure": "upper triangular inputs (the non-normal six) are detected in the 1-norm pass and "
-                                "run on the triangles, with the exact diagonal and superdiagonal put back "
-                                "(Section 5); the flop figures count the triangle products' own work",
-                   "l2": f"inputs larger than L2 (each exp(A) streams ~10 N^2 FP64 buffers of "
-                         f"{n * n * 8 / 2 ** 20:.0f} MiB)"},
+        "config": dense_config(args, n, mats, prods, world),
+        "form": {"scheme": "new (reduced-product Taylor)", "precision": args.precision,
+                 "slices": args.slices if args.precision != "fp64" else None,
+                 "structure": "upper triangular inputs (the non-normal six) are detected in the 1-norm pass and "
+                              "run on the triangles, with the exact diagonal and superdiagonal put back "
+                              "(Section 5); the flop figures count the triangle products' own work"},
+        "oracle_check": oracle_check,
         "tflops_logical": prod_flops * world / (ms / 1e3) / 1e12,
         "time_share": {"product_ms": prod_ms, "split_ms": split_ms, "norm_ms": norm_ms, "timed_ms": ms},
         "roofline": roof, "plain_fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -940,19 +1003,15 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        run_reference(args, rank)
+        run_reference(args, rank, world)
         return
-    # the batch is generated by spawned workers before CUDA starts in this process; with
+    # the batch is generated by spawned workers (safe before or after CUDA starts); with
     # several ranks the global batch is world x count matrices and each rank builds its
-    # longest-processing-time shard of it (weak scaling, no data-path collective)
+    # longest-processing-time shard of it on the cost N^3 (pi_m + s), (m, s) by the
+    # library's theta rule on each matrix's 1-norm (weak scaling, no data-path collective)
     mats = None
-    if args.workload == "batch":
-        if world == 1:
-            mats = W.batch_matrices(args.count)
-        else:
-            from paper_1710_10989_gb300 import sharding
-            ns, _ = W.batch_spec(count=args.count * world)
-            mats = W.batch_matrices_subset(sharding.shard_indices(ns, rank, world), count=args.count * world)
+    if args.workload == "batch" and world == 1:
+        mats = W.batch_matrices(args.count)
 
     import torch
     import torch.distributed as dist
@@ -965,6 +1024,12 @@ def main():
     if world > 1:
         dist.barrier()
     from paper_1710_10989_gb300 import api
+    if args.workload == "batch" and world > 1:
+        from paper_1710_10989_gb300 import sharding
+        ns, norms = W.batch_spec(count=args.count * world)
+        u = api.U_SINGLE if args.u == "single" else api.U_DOUBLE
+        prods = [PI[m] + s for m, s in (api.select(float(v), u) for v in norms)]
+        mats = W.batch_matrices_subset(sharding.shard_indices(ns, rank, world, prods), count=args.count * world)
     if args.workload == "batch":
         line = run_batch(args, torch, dist, api, rank, world, local, mats)
     elif args.workload == "small":

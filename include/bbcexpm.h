@@ -138,9 +138,10 @@ int bbc_norm1(bbc_handle h, const double* dA, int64_t N, void* stream, double* h
  *  dNorm  device, one double; receives ||A||_1 (cleared by the call itself)
  *  N      1 <= N <= 65536; larger N returns BBC_INVALID_ARG before any work
  * Scratch: a fixed 1 MiB array compiled into the library (held on every GPU
- * that loads it until the process exits). The first call on each device looks
- * up that array's device address (with the device current), so make the first
- * call on a device before any stream capture. All calls share the array:
+ * that loads it until the process exits). Every call looks up that array's
+ * device address on the current device; the first lookup on a device loads
+ * the library's device code there, so make the first call on a device before
+ * any stream capture. All calls share the array:
  * calls that may overlap on the GPU (other streams, other host threads) race
  * and must be serialised by the caller. Returns without waiting for the stream. */
 int bbc_norm1_noalloc(const double* dA, int64_t N, double* dNorm, void* stream);

@@ -140,41 +140,26 @@ cudaError_t exact_diagonals(const double* A, int64_t N, int q, double* T, cudaSt
 // handle's workspace. Every GPU that loads the library holds it (1 MiB) until
 // the process exits; all calls share it.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 namespace bbc {
 
 constexpr int64_t NOALLOC_SCRATCH_DOUBLES = 131072;  // 1 MiB
 static __device__ __align__(256) double g_norm1_scratch[NOALLOC_SCRATCH_DOUBLES];
 
-namespace {
-std::mutex g_noalloc_mu;
-constexpr int NOALLOC_MAX_DEVICES = 64;
-double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
-}  // namespace
-
 bool norm1_noalloc_fits(int64_t N) { return N >= 1 && norm1_partial_len(N) <= NOALLOC_SCRATCH_DOUBLES; }
 
-// Device address of the scratch array on the current device. In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// In host code the array's name is only a host-side stand-in, so its device
+// address on the current device is looked up (with that device current) and
+// passed to the kernels. The lookup is repeated on every call rather than
+// cached: it is a host-side table read once the module is loaded, and a cached
+// address would be stale after a device reset reloads the module. The first
+// lookup on a device loads the module, which is why the first call on a device
+// must come before any stream capture.
 cudaError_t norm1_noalloc(const double* A, int64_t N, double* dNorm, cudaStream_t st) {
   if (!norm1_noalloc_fits(N)) return cudaErrorInvalidValue;
-  int dev = 0;
-  cudaError_t err = cudaGetDevice(&dev);
-  if (err != cudaSuccess) return err;
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
   double* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      double* p = nullptr;
-      err = cudaGetSymbolAddress((void**)&p, g_norm1_scratch);
-      if (err != cudaSuccess) return err;
-      g_noalloc_ptr[dev] = p;
-    }
-    scratch = g_noalloc_ptr[dev];
-  }
+  const cudaError_t err = cudaGetSymbolAddress((void**)&scratch, g_norm1_scratch);
+  if (err != cudaSuccess) return err;
+  if (!scratch) return cudaErrorInvalidSymbol;
   // every partial sum the kernels read is written first by the same call, and
   // norm1() clears *dNorm before the maximum is taken: no stale state is used
   return norm1(A, N, scratch, dNorm, st);

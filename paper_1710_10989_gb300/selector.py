@@ -1,7 +1,9 @@
-"""Training and evaluation of the (m, s)-proposing network.
+"""Training of the (m, s)-proposing network.
 
     python -m paper_1710_10989_gb300.selector train [--count 1000000] [--epochs 8]
-    python -m paper_1710_10989_gb300.selector evaluate [--count 4096]
+
+(Held-out evaluation against the paper's rule and the alpha rule, with its
+accuracy check against the CPU oracle, is bench.py's learned workload.)
 
 Training matrices: the batched workload's families (half Gaussian, half
 V diag(lambda) V^-1 with cond_2(V) = 1e3, lambda ~ N(0, 4)) with N uniform on
@@ -169,86 +171,19 @@ def install(h, path=WEIGHTS):
     return net, meta
 
 
-def evaluate(args):
-    """Held-out matrices: plain rule vs network (certified) vs closed-form alpha rule."""
-    import torch
-
-    from oracle import oracle as O
-    from paper_1710_10989_gb300 import api
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(args.seed)
-    rng = np.random.default_rng(args.seed)
-    h = api.Handle(0)
-    h.batch_reserve(512)
-    install(h, args.weights)
-    mats = []
-    while len(mats) < args.count:
-        n = int(rng.integers(16, 513))
-        mats += list(gpu_matrices(torch, n, min(64, args.count - len(mats)), gen).unbind(0))
-    order = api.batch_order([A.shape[0] for A in mats])
-    mats = [mats[i].contiguous() for i in order]
-    res = {}
-    outs = {}
-    for name, flags in (("plain", 0), ("learned", api.SELECT_LEARNED), ("alpha", api.SELECT_ALPHA)):
-        o = [torch.empty_like(a) for a in mats]
-        b = api.Batch(mats, o)
-        h.expm_batched(b, flags=flags)
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record()
-        for _ in range(args.reps):
-            h.expm_batched(b, flags=flags)
-        t1.record()
-        torch.cuda.synchronize()
-        inf = b.infos()
-        sel = np.array([i["selector"] for i in inf])
-        res[name] = {"expm_per_s": len(mats) * args.reps / (t0.elapsed_time(t1) / 1e3),
-                     "mean_products": float(np.mean([i["products"] for i in inf])),
-                     "statuses_not_ok": int(sum(i["status"] != 0 for i in inf)),
-                     "fallback_rate": float(np.mean(sel == 4)) if name == "learned" else None,
-                     "accepted_by_norm": float(np.mean(sel == 2)) if name == "learned" else None,
-                     "accepted_by_alpha2": float(np.mean(sel == 3)) if name == "learned" else None}
-        outs[name] = (o, inf)
-    # accuracy against the oracle (its own theta-rule exp(A)) on a sample
-    idx = np.linspace(0, len(mats) - 1, args.check).astype(int)
-    errs = {name: [] for name in outs}
-    for i in idx:
-        A = mats[i].cpu().numpy()
-        ref, _ = O.expm(A)
-        for name in outs:
-            got = outs[name][0][i].cpu().numpy()
-            errs[name].append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
-    for name in outs:
-        res[name]["max_rel_err_vs_oracle"] = max(errs[name])
-    res["checked"] = len(idx)
-    res["count"] = len(mats)
-    print(json.dumps(res), flush=True)
-    h.close()
-    return res
-
-
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=("train", "evaluate"))
+    ap.add_argument("cmd", choices=("train",))
     ap.add_argument("--count", type=int, default=0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--lr", type=float, default=3e-3)
-    ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--check", type=int, default=24)
     ap.add_argument("--out", default=WEIGHTS)
-    ap.add_argument("--weights", default=WEIGHTS)
     a = ap.parse_args()
-    if a.cmd == "train":
-        a.count = a.count or 1_000_000
-        a.seed = a.seed or 11
-        train(a)
-    else:
-        a.count = a.count or 4096
-        a.seed = a.seed or 12
-        evaluate(a)
+    a.count = a.count or 1_000_000
+    a.seed = a.seed or 11
+    train(a)
 
 
 if __name__ == "__main__":

@@ -53,3 +53,38 @@ def test_traffic_record_follows_the_source(bench, monkeypatch):
     assert bench.ncu_traffic(src, 2048) is None          # another size: no record
     monkeypatch.setitem(bench.NCU_TRAFFIC, src, ("0" * 64, 4096, 1.0e9))
     assert bench.ncu_traffic(src, 4096) is None          # source changed since the capture
+
+
+def test_reference_arm_runs_the_oracle_alone_on_the_same_config(bench, monkeypatch):
+    """--impl reference times the oracle without loading the CUDA library, and
+    prints the same `config` the main arm prints for that workload (here the dense
+    workload's twelve matrices at N = 96, so that it runs in seconds)."""
+    import json
+    import subprocess
+    code = ("import runpy, sys\n"
+            "sys.argv = ['bench.py', '--impl', 'reference', '--n', '96', '--steps', '4']\n"
+            "runpy.run_path('bench.py', run_name='__main__')\n"
+            "maps = open('/proc/self/maps').read()\n"
+            "print('LOADED', 'libbbcexpm' in maps, 'paper_1710_10989_gb300.api' in sys.modules)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    lines = r.stdout.strip().splitlines()
+    line = json.loads(lines[0])
+    assert lines[-1] == "LOADED False False"
+    assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--n", "96"])
+    args = bench.parse()
+    mats = bench.dense_workload(96)
+    prods = bench.products_of(mats)            # the main arm's selection: the library's own
+    assert line["config"] == bench.dense_config(args, 96, mats, prods, 1)
+    assert line["config"]["products_per_step"] == 84
+
+
+def test_reference_cycle_samples_the_mix(bench):
+    """Every four consecutive reference steps hold the workload's mean product count."""
+    mats = bench.dense_workload(96)
+    from oracle import oracle as O
+    prods = bench.products_of(mats, select=lambda v, u: O.select(v, "new", u))
+    assert sorted(bench.DENSE_CYCLE) == list(range(12))
+    for k in range(0, 12, 4):
+        assert sum(prods[i] for i in bench.DENSE_CYCLE[k:k + 4]) == 4 * sum(prods) / len(prods)

@@ -188,3 +188,36 @@ def test_autotuner_choice_keeps_parity(api):
         want, _ = O.expm(A, "new")
         assert rel_fro(out.cpu().numpy(), want) < 1e-12
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split"])
+def test_batch_single_precision_thresholds(api, prec):
+    """Table 2's u = 2^-24 row through the batched call's tol: every matrix gets
+    the oracle's (m, s) at u = 2^-24 and its result equals the oracle's exp(A) at
+    that (m, s) within the batched workload's 1e-6 (binary32 storage)."""
+    import torch
+    hh = api.Handle(0)
+    flags = api.PREC_OZAKI if prec == "split" else api.PREC_FP64
+    hh.batch_reserve(256, flags)
+    ns, norms = W.batch_spec(count=40, seed=9)
+    ns[:5] = [1, 8, 65, 255, 256]
+    mats = [W.batch_matrix(i, int(n), float(v), seed=9) for i, (n, v) in enumerate(zip(ns, norms))]
+    ins = [torch.from_numpy(A.astype(np.float32)).cuda() for A in mats]
+    outs = [torch.full_like(a, float("nan")) for a in ins]
+    b = api.Batch(ins, outs)
+    hh.expm_batched(b, tol=api.U_SINGLE, flags=flags)
+    torch.cuda.synchronize()
+    fewer = 0
+    worst = 0.0
+    for A, o, inf in zip(mats, outs, b.infos()):
+        A = A.astype(np.float32).astype(np.float64)
+        want, oi = O.expm(A, "new", u=2.0 ** -24)
+        assert inf["status"] == 0, inf
+        assert (inf["m"], inf["s"], inf["products"]) == (oi.m, oi.s, oi.products), (inf, oi)
+        assert (oi.m, oi.s) == O.select(O.norm1(A), "new", 2.0 ** -24)
+        _, od = O.expm(A, "new")                       # u = 2^-53, for the product count only
+        fewer += od.products > oi.products
+        worst = max(worst, rel_fro(o.cpu().numpy().astype(np.float64), want))
+    assert worst < 1e-6, worst
+    assert fewer >= 10        # the single-precision thresholds save products on many matrices
+    hh.close()

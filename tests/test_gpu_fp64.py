@@ -176,19 +176,6 @@ def test_status_codes(h, api):
     assert (to_host(z) == np.eye(6)).all() and info.m == 1
 
 
-# ---- the 4096 x 4096 dense workload at full size -----------------------------------------------
-
-@pytest.mark.parametrize("idx,nonnormal", [(2, False), (5, False), (3, True)])
-def test_dense_4096_full_size(h, api, idx, nonnormal):
-    A = W.dense_case(idx, nonnormal=nonnormal)
-    out = empty_like_dev(A.shape[0])
-    info = h.expm(to_dev(A), out)
-    want, oi = O.expm_upper(A, "new") if nonnormal else O.expm(A, "new")
-    assert info.structure == (1 if nonnormal else 0)
-    assert (info.m, info.s) == (oi.m, oi.s)
-    assert rel_fro(to_host(out), want) < 1e-12
-
-
 # ---- upper triangular structure -----------------------------------------------------------------
 
 @pytest.mark.parametrize("n", [1, 5, 64, 130, 300, 1025])

@@ -127,18 +127,6 @@ def test_identity_dominated_operands(h, api):
         assert rel_fro(to_host(C), to_host(C64)) < 5e-15, k
 
 
-@pytest.mark.parametrize("idx,nonnormal", [(5, False), (5, True)])
-def test_dense_4096_split_full_size(h, api, idx, nonnormal):
-    """The dense 4096 workload at norm 100 (s = 7, the largest error amplification)."""
-    A = W.dense_case(idx, nonnormal=nonnormal)
-    out = empty_like_dev(A.shape[0])
-    info = h.expm(to_dev(A), out, 0.0, api.SCHEME_NEW | api.PREC_OZAKI)
-    want, oi = O.expm_upper(A, "new") if nonnormal else O.expm(A, "new")
-    assert info.structure == (1 if nonnormal else 0)
-    assert (info.m, info.s, info.products) == (oi.m, oi.s, oi.products)
-    assert rel_fro(to_host(out), want) < 1e-12
-
-
 def test_split_product_is_closer_to_exact_than_fp64(h, api):
     """Sampled entries of P Q computed exactly (rational arithmetic on the binary64
     inputs): the split product (exact slice sums) lands closer to them than the

@@ -209,3 +209,40 @@ def test_trained_network_gains_over_the_plain_rule(api):
             got = outs[name][i].cpu().numpy()
             assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
     hh.close()
+
+
+def test_training_labels_relabelled_by_the_oracle(api):
+    """The network's training labels come from the library's data mode (FP64
+    power norms on the GPU, then bbc_select_certified). A 1 % random sample of
+    10,240 matrices drawn as the training set is (N uniform on 16..512, seed 11)
+    is re-labelled by the oracle (its own products for ||A^k||_1 and its own
+    certified selection); the disagreement rate is reported and must stay at or
+    below one sample in a hundred (a disagreement needs a norm within rounding
+    of a threshold)."""
+    import torch
+    from oracle import oracle as O
+    from paper_1710_10989_gb300 import selector as SEL
+    h = api.Handle(0)
+    h.batch_reserve(512)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    rng = np.random.default_rng(11)
+    pick = np.random.default_rng(111)
+    total, sample = 0, []
+    while total < 10240:
+        n = int(rng.integers(16, 513))
+        A = SEL.gpu_matrices(torch, n, 256, gen)
+        _, nr = h.selector_data(api.Batch(list(A.unbind(0))))
+        lib_labels = SEL.labels_of(nr.cpu().numpy())
+        for j in np.nonzero(pick.random(256) < 0.01)[0]:
+            sample.append((A[j].cpu().numpy(), int(lib_labels[j])))
+        total += 256
+    h.close()
+    assert len(sample) >= 80
+    disagree = 0
+    for Ah, lab in sample:
+        m, s = O.select_certified(O.power_norms(Ah))
+        disagree += lab != SEL.DEGREES.index(m) * SEL.S_VALUES + min(s, SEL.S_VALUES - 1)
+    rate = disagree / len(sample)
+    print(f"oracle re-label of {len(sample)} of {total} training-style matrices: disagreement rate {rate:.4f}")
+    assert disagree <= max(1, len(sample) // 100), (disagree, len(sample))

@@ -1,6 +1,7 @@
 """Multi-rank logic of the batched path on the CPU (gloo, world size 2): every
-matrix lands on exactly one rank, the shards balance, and the max-over-ranks
-timing reduction the benchmark uses behaves."""
+matrix lands on exactly one rank, the shards balance on the cost N^3 (pi_m + s)
+(products of the theta rule's (m, s), Table 3), also for a norm-skewed batch,
+and the max-over-ranks timing reduction the benchmark uses behaves."""
 import os
 import socket
 
@@ -15,6 +16,30 @@ def _free_port():
     return p
 
 
+PI = {1: 0, 2: 1, 4: 2, 8: 3, 12: 4, 18: 5}   # Table 3: products of T_m in the paper's scheme
+
+
+def products_of(norms):
+    """pi_m + s of the theta rule's (m, s) for each norm (the oracle's selection)."""
+    from oracle import oracle as O
+    out = []
+    for v in norms:
+        m, s = O.select(float(v), "new")
+        out.append(PI[m] + s)
+    return out
+
+
+def skewed_spec(count=600):
+    """Sizes of the batched workload with 1-norms that grow with N: the largest
+    matrices also need the most products, the case an N^3-only cost misjudges."""
+    import numpy as np
+    from paper_1710_10989_gb300 import workloads as W
+    ns, _ = W.batch_spec(count=count)
+    rng = np.random.default_rng(3)
+    norms = np.where(rng.random(count) < 0.5, 1e-3, 1e2) * (ns / 256.0) ** 2
+    return ns, norms
+
+
 def _worker(rank, world, port, out):
     import torch
     import torch.distributed as dist
@@ -23,14 +48,17 @@ def _worker(rank, world, port, out):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    ns, _ = W.batch_spec(count=4000)
-    mine = sharding.shard_indices(ns, rank, world)
-    gathered = [None] * world
-    dist.all_gather_object(gathered, mine)
+    res = {}
+    for name, (ns, norms) in (("uniform", W.batch_spec(count=4000)), ("skewed", skewed_spec())):
+        prods = products_of(norms)
+        mine = sharding.shard_indices(ns, rank, world, prods)
+        gathered = [None] * world
+        dist.all_gather_object(gathered, mine)
+        res[name] = (gathered, [int(n) for n in ns], prods)
     t = torch.tensor([float(rank + 1)], dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     if rank == 0:
-        out.put((gathered, float(t.item()), [int(n) for n in ns]))
+        out.put((res, float(t.item())))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -43,16 +71,38 @@ def test_two_rank_shards_cover_the_batch_once():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    gathered, tmax, ns = q.get(timeout=120)
+    res, tmax = q.get(timeout=180)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
-    a, b = set(gathered[0]), set(gathered[1])
-    assert not (a & b) and (a | b) == set(range(len(ns)))
-    ca = sum(ns[i] ** 3 for i in a)
-    cb = sum(ns[i] ** 3 for i in b)
-    assert abs(ca - cb) / max(ca, cb) < 0.01
+    for name, (gathered, ns, prods) in res.items():
+        a, b = set(gathered[0]), set(gathered[1])
+        assert not (a & b) and (a | b) == set(range(len(ns))), name
+        ca = sum(ns[i] ** 3 * prods[i] for i in a)
+        cb = sum(ns[i] ** 3 * prods[i] for i in b)
+        assert abs(ca - cb) / max(ca, cb) < 0.01, name
     assert tmax == 2.0
+
+
+def test_product_count_matters_for_skewed_norms():
+    """On the norm-skewed batch, shards balanced on N^3 alone are off by more
+    than the (pi_m + s)-aware ones, measured in products x N^3."""
+    from paper_1710_10989_gb300 import sharding
+    ns, norms = skewed_spec()
+    prods = products_of(norms)
+    assert min(prods) <= 3 and max(prods) >= 12
+
+    def imbalance(assign_prods):
+        loads = []
+        for r in range(4):
+            idx = sharding.shard_indices(ns, r, 4, assign_prods)
+            loads.append(sum(int(ns[i]) ** 3 * prods[i] for i in idx))
+        return max(loads) / (sum(loads) / len(loads)) - 1.0
+
+    aware, blind = imbalance(prods), imbalance(None)
+    assert aware < 0.01
+    assert blind > 2 * aware
+    assert sum(sharding.shard_costs(ns, 4, prods)) == sum(int(n) ** 3 * p for n, p in zip(ns, prods))
 
 
 def test_shards_single_process():

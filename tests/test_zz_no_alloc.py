@@ -1,10 +1,11 @@
 """The allocation-free 1-norm entry point (bbc_norm1_noalloc), for callers that
-must not allocate device memory at call time, gives the same result as the
-handle-based bbc_norm1 -- on two calls in a row, which share the library's
-fixed scratch array -- and rejects sizes beyond its fixed capacity."""
+must not allocate device memory at call time, gives the oracle's ||A||_1 and the
+same result as the handle-based bbc_norm1 -- on two calls in a row, which share
+the library's fixed scratch array -- and rejects sizes beyond its fixed capacity."""
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_1710_10989_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -26,11 +27,14 @@ def test_noalloc_norm_matches_handle_norm_twice(api):
     # a larger matrix first, then a smaller one: the second call must not see
     # anything the first left in the shared scratch
     for n, seed in ((1500, 61), (257, 62)):
-        A = torch.from_numpy(W.gaussian(n, seed, None)).cuda()
+        Ah = W.gaussian(n, seed, None)
+        A = torch.from_numpy(Ah).cuda()
         api.norm1_noalloc(A, out)
         torch.cuda.synchronize()
-        want = h.norm1(A)
-        assert out.item() == pytest.approx(want, rel=1e-14)
+        got = out.item()
+        # the oracle's column sums (its own loop, independent of the slab kernels)
+        assert got == pytest.approx(O.norm1(Ah), rel=1e-14)
+        assert got == pytest.approx(h.norm1(A), rel=1e-14)
     h.close()
 
 
