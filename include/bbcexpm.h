@@ -47,8 +47,9 @@ typedef enum {
 #define BBC_SCHEME_NEW 0x0     /* reduced-product Taylor, degrees {1,2,4,8,12,18} (Section 3) */
 #define BBC_SCHEME_PS 0x1      /* Paterson-Stockmeyer Taylor, degrees {1,2,4,6,9,12,16} (eq. poli9) */
 #define BBC_SCHEME_PADE26 0x2  /* diagonal Pade r_26 (eq. pade26), the paper's comparator; its solve
-                                  beyond N = 1024 uses cuSOLVER, loaded at run time (BBC_UNSUPPORTED
-                                  where it is absent) */
+                                  (v - u) R = u + v is an LU with partial pivoting and both triangular
+                                  solves on the GPU (the library's own kernels; BBC_UNSUPPORTED beyond
+                                  the N whose panels fit a 16-CTA cluster's shared memory, about 13,000) */
 #define BBC_SCHEME_PADE 0x3    /* diagonal Pade r_10 (eq. pade10, 3 products) or r_26 (6), whichever costs
                                   fewer products + squarings (the solve is common to both), ties to
                                   the smaller s */
@@ -63,6 +64,15 @@ typedef enum {
                                   About 8k significant bits per product, no better than FP32 sums
                                   allow (~1e-7 relative); kept to report the plain split beside
                                   the exact one */
+#define BBC_PREC_SPLIT_BF16 BBC_PREC_SPLIT
+#define BBC_PREC_SPLIT_TF32 0x30  /* the literal split in TF32 terms (the precision config's 2-term TF32
+                                     form): each scaled operand written as k TF32 terms (10 explicit
+                                     mantissa bits each), the term products with p + q < k accumulated
+                                     in FP32 by tcgen05 kind::tf32 MMAs (bits 8-11 = k in 2..4, 0 -> 2).
+                                     About 22 significant bits per product at k = 2 */
+#define BBC_PREC_FP32 0x40     /* products at binary32 accuracy: three TF32 terms per operand with
+                                  FP32 accumulation on the tensor cores (as BBC_PREC_SPLIT_TF32 with
+                                  k = 3; the slice-count bits must be 0) */
 #define BBC_PREC_MASK 0xF0
 #define BBC_OZAKI_SLICES(k) (((k) & 0xF) << 8)
 /* bits 16-19: the last n squarings run on the FP64 pipe whatever the product precision
@@ -146,6 +156,19 @@ int bbc_norm1(bbc_handle h, const double* dA, int64_t N, void* stream, double* h
  * and must be serialised by the caller. Returns without waiting for the stream. */
 int bbc_norm1_noalloc(const double* dA, int64_t N, double* dNorm, void* stream);
 
+/* dB <- dM^-1 dB: the Pade comparator's linear solve (v - u) R = u + v (eq. pade26,
+ * Section 1: "4/3 of a product"), as bbc_expm runs it, exposed for testing and
+ * reuse. LU factorisation with partial pivoting (ties to the smaller row) of dM,
+ * forward substitution of the N right-hand sides, back substitution: for N <= 112
+ * in shared memory, one CTA per 4 right-hand sides; beyond, blocked (32-column
+ * panels factored by a thread-block cluster, FP64 rank-32 updates).
+ *  dM  device, N x N row-major binary64; overwritten by its LU factors
+ *  dB  device, N x N row-major binary64; overwritten by the solution
+ * Waits for the stream. BBC_OVERFLOW when dM is singular to working precision or
+ * the solution is not finite; BBC_UNSUPPORTED beyond the N the panel clusters hold
+ * (about 13,000 on a GPU with 227 KB of shared memory per CTA). */
+int bbc_solve(bbc_handle h, double* dM, double* dB, int64_t N, void* stream);
+
 /* dC = dP * dQ (one dense product) with the precision in `flags`. With
  * BBC_PREC_OZAKI the call waits for the stream and reports a non-finite
  * operand (BBC_OVERFLOW) or an expired device wait (BBC_TIMEOUT). */
@@ -190,8 +213,9 @@ int bbc_expm_complex(bbc_handle h, const double* dA, int64_t N, double* dOut, do
  * flags hold BBC_UPPER (the caller's guarantee). dStatus (device word, may be
  * NULL) receives, stream-ordered, bit 0 = a non-finite value in the result
  * (a non-finite input ends there too), bit 1 = a bounded device wait expired.
- * BBC_INVALID_ARG for a capture with too small a workspace; BBC_UNSUPPORTED for a
- * captured Pade comparator beyond N = 1024 (its solve allocates). */
+ * BBC_INVALID_ARG for a capture with too small a workspace, or for a captured
+ * Pade comparator (N > 112) on a device where no such solve has run outside a
+ * capture yet (its kernels' one-time set-up). */
 int bbc_expm_fixed_async(bbc_handle h, const double* dA, int64_t N, double* dOut, int m, int s, int flags,
                          void* stream, unsigned int* dStatus);
 

@@ -396,7 +396,7 @@ static int lu_solve(int64_t n, double* P, double* Q, double* R) {
   for (int64_t k = 0; k < n; ++k) {
     int64_t piv = k;
     double best = fabs(P[k * n + k]);
-    for (int64_t i = k + 1; i < n; ++i)
+    for (int64_t i = k + 1; i < n && g_mutation != 13; ++i)   /* planted (13): no row interchanges */
       if (fabs(P[i * n + k]) > best) { best = fabs(P[i * n + k]); piv = i; }
     if (best == 0.0) return 1;
     if (piv != k) {
@@ -427,6 +427,11 @@ static int lu_solve(int64_t n, double* P, double* Q, double* R) {
   }
   return 0;
 }
+
+/* The same solve as a public entry (the comparator's solve, tested on its own):
+ * R = P^-1 Q for n x n P and Q (both overwritten: P by its LU factors, Q by
+ * the eliminated right-hand sides). Returns 0, or 1 if P is singular. */
+int orc_solve(int64_t n, double* P, double* Q, double* R) { return lu_solve(n, P, Q, R); }
 
 /* R = r_2m(X) for 2m in {10, 26}. Returns the number of products, -1 for an
  * unsupported order, -2 if the denominator is singular. */

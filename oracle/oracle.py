@@ -45,6 +45,7 @@ def lib() -> ctypes.CDLL:
         L.orc_taylor_new.argtypes = [i64, dp, ctypes.c_int, dp]
         L.orc_taylor_ps.argtypes = [i64, dp, ctypes.c_int, dp]
         L.orc_pade.argtypes = [i64, dp, ctypes.c_int, dp]
+        L.orc_solve.argtypes = [i64, dp, dp, dp]
         L.orc_select.argtypes = [ctypes.c_double, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int)]
         L.orc_expm.argtypes = [i64, dp, dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
@@ -109,6 +110,19 @@ def pade(X, two_m: int) -> np.ndarray:
     rc = lib().orc_pade(X.shape[0], _p(X), two_m, _p(R))
     if rc < 0:
         raise ValueError(f"pade r_{two_m} failed ({rc})")
+    return R
+
+
+def solve(P, Q) -> np.ndarray:
+    """P^-1 Q by the comparator's Gaussian elimination with partial pivoting on
+    all right-hand sides at once, then back substitution (the solve of eq. pade26)."""
+    P = _sq(P).copy()
+    Q = _sq(Q).copy()
+    if P.shape != Q.shape:
+        raise ValueError("P and Q must have the same shape")
+    R = np.empty_like(P)
+    if lib().orc_solve(P.shape[0], _p(P), _p(Q), _p(R)):
+        raise ValueError("singular matrix")
     return R
 
 

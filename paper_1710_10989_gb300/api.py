@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libbbcexpm.so")
 
 OK, INVALID_ARG, NONFINITE_INPUT, OVERFLOW, CUDA_ERROR, TIMEOUT, UNSUPPORTED = range(7)
 SCHEME_NEW, SCHEME_PS, SCHEME_PADE26, SCHEME_PADE = 0x0, 0x1, 0x2, 0x3
-PREC_FP64, PREC_OZAKI, PREC_SPLIT = 0x00, 0x10, 0x20
+PREC_FP64, PREC_OZAKI, PREC_SPLIT, PREC_SPLIT_TF32, PREC_FP32 = 0x00, 0x10, 0x20, 0x30, 0x40
 SELECT_LEARNED, SELECT_ALPHA = 0x1000, 0x2000
 DENSE, UPPER = 0x4000, 0x8000
 DEGREES = (1, 2, 4, 8, 12, 18)
@@ -64,6 +64,7 @@ _SIGS = {
     "bbc_norm1": [_vp, _vp, _i64, _vp, _dp],
     "bbc_norm1_noalloc": [_vp, _i64, _vp, _vp],
     "bbc_gemm": [_vp, _vp, _vp, _i64, _vp, _int, _vp],
+    "bbc_solve": [_vp, _vp, _vp, _i64, _vp],
     "bbc_taylor": [_vp, _vp, _i64, _int, _int, _vp, _int, _vp, _ip],
     "bbc_expm": [_vp, _vp, _i64, _vp, _dbl, _int, _vp, ctypes.POINTER(Info)],
     "bbc_expm_fixed": [_vp, _vp, _i64, _vp, _int, _int, _int, _vp, ctypes.POINTER(Info)],
@@ -267,6 +268,12 @@ class Handle:
         pq, _ = _mat(Q, "Q")
         pc, _ = _mat(C, "C")
         _check(_lib.bbc_gemm(self._h, pp, pq, n, pc, flags, _stream(stream)))
+
+    def solve(self, M, B, stream=None) -> None:
+        """B <- M^-1 B in place (M is overwritten by its LU factors)."""
+        pm, n = _mat(M, "M")
+        pb, _ = _mat(B, "B")
+        _check(_lib.bbc_solve(self._h, pm, pb, n, _stream(stream)))
 
     def taylor(self, A, m: int, s: int, T, flags: int = 0, stream=None) -> int:
         pa, n = _mat(A, "A")

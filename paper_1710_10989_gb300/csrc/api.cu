@@ -59,16 +59,28 @@ namespace {
 
 thread_local std::string g_err;
 
-// Products rebuilt from BF16 slices on the tensor cores: the exact form
-// (BBC_PREC_OZAKI, default 7 slices) or the literal split (BBC_PREC_SPLIT,
-// default 3 terms).
+// Products rebuilt from slices on the tensor cores: the exact form (BBC_PREC_OZAKI,
+// default 7 BF16 slices) or the literal split in BF16 terms (BBC_PREC_SPLIT, default 3)
+// or TF32 terms (BBC_PREC_SPLIT_TF32, default 2; BBC_PREC_FP32 = 3 TF32 terms).
 bool split_prec(int flags) {
   const int prec = flags & BBC_PREC_MASK;
-  return prec == BBC_PREC_OZAKI || prec == BBC_PREC_SPLIT;
+  return prec == BBC_PREC_OZAKI || prec == BBC_PREC_SPLIT || prec == BBC_PREC_SPLIT_TF32 || prec == BBC_PREC_FP32;
+}
+int split_mode(int flags) {
+  const int prec = flags & BBC_PREC_MASK;
+  if (prec == BBC_PREC_SPLIT_TF32 || prec == BBC_PREC_FP32) return SPLIT_LITERAL_TF32;
+  return prec == BBC_PREC_SPLIT ? SPLIT_LITERAL_BF16 : SPLIT_EXACT;
 }
 int split_slices(int flags) {
+  const int prec = flags & BBC_PREC_MASK;
+  if (prec == BBC_PREC_FP32) return 3;
   const int k = (flags >> 8) & 0xF;
-  return k ? k : ((flags & BBC_PREC_MASK) == BBC_PREC_SPLIT ? 3 : 7);
+  if (k) return k;
+  return prec == BBC_PREC_SPLIT ? 3 : prec == BBC_PREC_SPLIT_TF32 ? 2 : 7;
+}
+// Workspace room in BF16 planes (a TF32 plane takes two).
+int split_planes(int flags) {
+  return split_slices(flags) * (split_mode(flags) == SPLIT_LITERAL_TF32 ? 2 : 1);
 }
 
 int fail(int code, const std::string& msg) {
@@ -278,7 +290,7 @@ int ensure_workspace(bbc_handle h, int64_t N, int flags) {
     h->slots_n = N;
   }
   if (split_prec(flags)) {
-    const size_t need = ozaki_workspace_bytes(N, split_slices(flags));
+    const size_t need = ozaki_workspace_bytes(N, split_planes(flags));
     if (need > h->ozaki_bytes) {
       if (h->ozaki) BBC_CUDA(cudaFree(h->ozaki));
       h->ozaki = nullptr;
@@ -336,14 +348,14 @@ int launch_product(bbc_handle h, const double* P, const double* Q, int64_t N, do
   h->flops[BBC_KERNEL_PRODUCT] += upper ? n * (n + 1) * (n + 2) / 3.0 : 2.0 * n * n * n;
   if (split_prec(flags)) {
     const int k = split_slices(flags);
-    const bool literal = (flags & BBC_PREC_MASK) == BBC_PREC_SPLIT;
+    const int mode = split_mode(flags);
     {
       LaunchScope scope(h, BBC_KERNEL_SPLIT, stream);
-      err = ozaki_split(P, Q, N, k, h->ozaki, h->dflag, stream, literal);
+      err = ozaki_split(P, Q, N, k, h->ozaki, h->dflag, stream, mode);
     }
     if (err != cudaSuccess) return cuda_fail(err, "split launch");
     LaunchScope scope(h, BBC_KERNEL_PRODUCT, stream);
-    err = ozaki_product(P, Q, N, alpha, e, k, h->ozaki, h->dflag, stream, upper, literal);
+    err = ozaki_product(P, Q, N, alpha, e, k, h->ozaki, h->dflag, stream, upper, mode);
   } else {
     LaunchScope scope(h, BBC_KERNEL_PRODUCT, stream);
     err = gemm_f64(P, Q, N, alpha, e, stream, upper);
@@ -393,7 +405,8 @@ int check_flags(int flags) {
   const int prec = flags & BBC_PREC_MASK;
   if (scheme != BBC_SCHEME_NEW && scheme != BBC_SCHEME_PS && scheme != BBC_SCHEME_PADE26 && scheme != BBC_SCHEME_PADE)
     return fail(BBC_INVALID_ARG, "unknown scheme");
-  if (prec != BBC_PREC_FP64 && prec != BBC_PREC_OZAKI && prec != BBC_PREC_SPLIT)
+  if (prec != BBC_PREC_FP64 && prec != BBC_PREC_OZAKI && prec != BBC_PREC_SPLIT && prec != BBC_PREC_SPLIT_TF32 &&
+      prec != BBC_PREC_FP32)
     return fail(BBC_INVALID_ARG, "unknown precision");
   if (flags & ~0xFFFFF) return fail(BBC_INVALID_ARG, "unknown flag bits");
   if ((flags & BBC_SELECT_MASK) == BBC_SELECT_MASK) return fail(BBC_INVALID_ARG, "two selectors requested");
@@ -401,6 +414,11 @@ int check_flags(int flags) {
     const int k = (flags >> 8) & 0xF;
     if (k != 0 && (k < 2 || k > 8)) return fail(BBC_INVALID_ARG, "slice count must be 2..8");
   }
+  if (prec == BBC_PREC_SPLIT_TF32) {
+    const int k = (flags >> 8) & 0xF;
+    if (k != 0 && (k < 2 || k > 4)) return fail(BBC_INVALID_ARG, "TF32 term count must be 2..4");
+  }
+  if (prec == BBC_PREC_FP32 && ((flags >> 8) & 0xF)) return fail(BBC_INVALID_ARG, "BBC_PREC_FP32 takes no term count");
   return BBC_OK;
 }
 
@@ -424,8 +442,8 @@ int run_expm(bbc_handle h, const double* A, int64_t N, double* Out, int m, int s
     return fail(BBC_INVALID_ARG, "degree not available in this scheme");
   if (s < 0 || s > 1100) return fail(BBC_INVALID_ARG, "squarings out of range");
   const bool pade = (flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE26 || (flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE;
-  if (pade && N > 1024 && !lu_solve_large_available())
-    return fail(BBC_UNSUPPORTED, "the Pade comparator beyond N = 1024 needs cuSOLVER, which is not available");
+  if (pade && N > 112 && N > lu_blocked_max_n())
+    return fail(BBC_UNSUPPORTED, "the Pade comparator's solve: N beyond what the panel clusters hold");
   if (pade) upper = false;
   auto exact = [&](double* T, int q) -> int {
     if (!upper) return BBC_OK;
@@ -478,7 +496,10 @@ int batch_flags_ok(int flags) {
     return fail(BBC_UNSUPPORTED, "batched path: schemes NEW, PADE and PADE26");
   if (scheme != BBC_SCHEME_NEW && (flags & BBC_SELECT_MASK))
     return fail(BBC_UNSUPPORTED, "batched path: the learned and alpha selections serve scheme NEW");
-  if ((flags & BBC_PREC_MASK) == BBC_PREC_OZAKI) {
+  const int prec = flags & BBC_PREC_MASK;
+  if (prec != BBC_PREC_FP64 && prec != BBC_PREC_OZAKI)
+    return fail(BBC_UNSUPPORTED, "batched path: FP64 products or BBC_PREC_OZAKI split products");
+  if (prec == BBC_PREC_OZAKI) {
     const int k = (flags >> 8) & 0xF;
     if (k != 0 && k != 4) return fail(BBC_UNSUPPORTED, "batched split products use 4 slices");
   }
@@ -577,7 +598,7 @@ int bbc_workspace_size(bbc_handle h, int64_t N, int dtype, int flags, size_t* by
   int rc = check_flags(flags);
   if (rc) return rc;
   size_t b = (size_t)NUM_WORK_SLOTS * N * N * sizeof(double) + norm1_partial_len(N) * sizeof(double);
-  if (split_prec(flags)) b += ozaki_workspace_bytes(N, split_slices(flags));
+  if (split_prec(flags)) b += ozaki_workspace_bytes(N, split_planes(flags));
   *bytes = b;
   return BBC_OK;
 }
@@ -669,6 +690,27 @@ int bbc_norm1_noalloc(const double* dA, int64_t N, double* dNorm, void* stream) 
   return BBC_OK;
 }
 
+int bbc_solve(bbc_handle h, double* dM, double* dB, int64_t N, void* stream) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!dM || !dB || N <= 0) return fail(BBC_INVALID_ARG, "bad solve arguments");
+  if (overlaps(dM, dB, N)) return fail(BBC_INVALID_ARG, "M and B overlap");
+  if (N > 112 && N > lu_blocked_max_n()) return fail(BBC_UNSUPPORTED, "N beyond what the panel clusters hold");
+  std::lock_guard<std::mutex> lk(h->mu);
+  if ((rc = ensure_workspace(h, N, BBC_PREC_FP64))) return rc;  // a work slot holds the pivot indices
+  cudaStream_t st = (cudaStream_t)stream;
+  BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
+  {
+    LaunchScope scope(h, BBC_KERNEL_LINCOMB, st);
+    const cudaError_t e = lu_solve_inplace(dM, dB, N, h->dflag, st, h->work);
+    if (e != cudaSuccess) return cuda_fail(e, "solve");
+  }
+  int status = BBC_OK;
+  if ((rc = finish_status(h, st, &status))) return rc;
+  if (status) return fail(status, "singular or non-finite system");
+  return BBC_OK;
+}
+
 int bbc_gemm(bbc_handle h, const double* dP, const double* dQ, int64_t N, double* dC, int flags,
              void* stream) {
   int rc = begin(h);
@@ -751,10 +793,11 @@ int bbc_expm_fixed_async(bbc_handle h, const double* dA, int64_t N, double* dOut
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   BBC_CUDA(cudaStreamIsCapturing(st, &cs));
   if (cs != cudaStreamCaptureStatusNone) {  // nothing may be allocated inside a capture
-    if (N > h->slots_n || (split_prec(flags) && ozaki_workspace_bytes(N, split_slices(flags)) > h->ozaki_bytes))
+    if (N > h->slots_n || (split_prec(flags) && ozaki_workspace_bytes(N, split_planes(flags)) > h->ozaki_bytes))
       return fail(BBC_INVALID_ARG, "workspace too small: run this N and precision once before the capture");
-    if (((flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE26 || (flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE) && N > 1024)
-      return fail(BBC_UNSUPPORTED, "the Pade comparator beyond N = 1024 cannot be captured");
+    if (((flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE26 || (flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE) && N > 112 &&
+        !lu_blocked_ready())
+      return fail(BBC_INVALID_ARG, "run the Pade comparator once (N > 112) before capturing it on this device");
   } else if ((rc = ensure_workspace(h, N, flags))) {
     return rc;
   }

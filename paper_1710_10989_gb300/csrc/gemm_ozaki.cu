@@ -50,7 +50,7 @@ namespace {
 using slices::OzLayout;
 using slices::layout;
 constexpr int TILE = slices::PAD;  // rows per CTA and columns of an output tile
-constexpr int KSTEP = 64;          // BF16 elements per 128-byte swizzle row
+constexpr int ROW_BYTES = 128;     // bytes of one swizzle row of a K step, either element type
 constexpr int CHUNK_STEPS = 16;    // 16 x 64 = 1024 K per exact FP32 chunk
 constexpr int G_EXACT = 5;         // groups 0..4 are summed exactly
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;  // 2 s per wait
@@ -133,16 +133,26 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // TMEM columns per CTA: [0,128) and [128,256) high buffers, [256,384) and [384,512)
 // low buffers.
 constexpr int P_STAGES = 8;
-constexpr int P_A_BYTES = TILE * KSTEP * 2;          // 128 rows of a P slice plane
-constexpr int P_B_BYTES = (TILE / 2) * KSTEP * 2;    // 64 rows of a Q^T slice plane
+constexpr int P_A_BYTES = TILE * ROW_BYTES;          // 128 rows of a P slice plane
+constexpr int P_B_BYTES = (TILE / 2) * ROW_BYTES;    // 64 rows of a Q^T slice plane
 constexpr int P_STAGE_BYTES = P_A_BYTES + P_B_BYTES;
 constexpr int P_THREADS = 320;
 constexpr int P_DRAIN_WARPS = 8;
 constexpr int P_GROUP_M = 8;                         // raster: 8 tile rows per column sweep
-// Instruction descriptor, kind::f16: D = F32 (bit 4), A = B = BF16 (bits 7, 10), both K-major,
-// N = 128 (bits 17-22: N / 8), M = 256 (bits 24-28: M / 16).
+// Instruction descriptor, kind::f16: D = F32 (bit 4), A = B = BF16 (bits 7-9, 10-12 = 1), both
+// K-major, N = 128 (bits 17-22: N / 8), M = 256 (bits 24-28: M / 16). kind::tf32 takes the same
+// layout with A = B = TF32 (format 2); its MMA covers K = 8 (32 bytes), as K = 16 does in BF16.
 constexpr uint32_t IDESC_PAIR = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TILE >> 3) << 17) |
                                 ((uint32_t)(2 * TILE >> 4) << 24);
+constexpr uint32_t IDESC_PAIR_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TILE >> 3) << 17) |
+                                     ((uint32_t)(2 * TILE >> 4) << 24);
+// Operand element type of a launch: BF16 slices (exact form and literal BF16 terms) or
+// TF32 terms (literal TF32 split). KS = elements per K step (one 128-byte swizzle row).
+template <bool TF32>
+struct OperandKind {
+  static constexpr int KS = TF32 ? 32 : 64;
+  static constexpr uint32_t IDESC = TF32 ? IDESC_PAIR_TF32 : IDESC_PAIR;
+};
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -242,13 +252,22 @@ __device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* m
       "l"(map), "r"(bar_cluster), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
+template <bool TF32>
 __device__ __forceinline__ void mma_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(a), "l"(b), "r"(IDESC_PAIR), "r"(accumulate)
-      : "memory");
+  if (TF32)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::
+            "r"(d_tmem),
+        "l"(a), "l"(b), "r"(IDESC_PAIR_TF32), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::
+            "r"(d_tmem),
+        "l"(a), "l"(b), "r"(IDESC_PAIR), "r"(accumulate)
+        : "memory");
 }
+// The exact form only (BF16): accumulate onto 2^-8 times the running sum.
 __device__ __forceinline__ void mma_pair_scaled(uint32_t d_tmem, uint64_t a, uint64_t b) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, 1, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p, 8;\n}\n" ::"r"(
@@ -306,7 +325,7 @@ struct TileWork {
   int c_lo, nch;       // first chunk, number of chunks
 };
 __device__ __forceinline__ TileWork tile_work(int t, const uint32_t* __restrict__ list, int tiles_m, int tiles_n,
-                                              int nksteps, int upper) {
+                                              int nksteps, int upper, int ks) {
   TileWork w;
   if (list) {
     const uint32_t code = __ldg(list + t);
@@ -315,8 +334,8 @@ __device__ __forceinline__ TileWork tile_work(int t, const uint32_t* __restrict_
   } else {
     pair_tile(t, tiles_m, tiles_n, &w.mp, &w.nt);
   }
-  w.ks_lo = upper ? min(nksteps, w.mp * (2 * TILE / KSTEP)) : 0;
-  w.ks_hi = upper ? min(nksteps, (w.nt + 1) * (TILE / KSTEP)) : nksteps;
+  w.ks_lo = upper ? min(nksteps, w.mp * (2 * TILE / ks)) : 0;
+  w.ks_hi = upper ? min(nksteps, (w.nt + 1) * (TILE / ks)) : nksteps;
   if (w.ks_hi <= w.ks_lo) {
     w.c_lo = 0;
     w.nch = 0;
@@ -354,6 +373,7 @@ struct ItemCursor {
   }
 };
 
+template <bool TF32>
 __global__ void __launch_bounds__(P_THREADS, 1)
 k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const int* __restrict__ erow, const int* __restrict__ fcol, const double* __restrict__ P,
@@ -367,6 +387,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   PairShared* sh = reinterpret_cast<PairShared*>(smem + P_STAGES * P_STAGE_BYTES);
   volatile int* cta_err = &sh->err;
 
+  constexpr int KS = OperandKind<TF32>::KS;  // elements per K step
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
   const int cid = cluster_index(), ncl = cluster_count();
@@ -411,7 +432,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     uint32_t ph = 0;
     bool ok = true;
     for (int t = cid; t < ntiles && ok; t += ncl) {
-      const TileWork w = tile_work(t, tile_list, tiles_m, tiles_n, nksteps, upper);
+      const TileWork w = tile_work(t, tile_list, tiles_m, tiles_n, nksteps, upper, KS);
       const int arow = w.mp * 2 * TILE + (int)rank * TILE;
       const int brow = w.nt * TILE + (int)rank * (TILE / 2);
       const int nunits = (pairs_h + pairs_l) * w.nch;
@@ -424,8 +445,8 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           if (leader_lane) {
             if (rank == 0) mbar_arrive_expect_tx(&sh->full[s], 2 * P_STAGE_BYTES);
             const uint32_t fb = peer_addr(&sh->full[s], 0);
-            tma_load_3d_pair(smA + s * P_A_BYTES, &tmA, fb, ks * KSTEP, arow, cur.p);
-            tma_load_3d_pair(smB + s * P_B_BYTES, &tmB, fb, ks * KSTEP, brow, cur.g - cur.p);
+            tma_load_3d_pair(smA + s * P_A_BYTES, &tmA, fb, ks * KS, arow, cur.p);
+            tma_load_3d_pair(smB + s * P_B_BYTES, &tmB, fb, ks * KS, brow, cur.g - cur.p);
           }
           __syncwarp();
           if (++s == P_STAGES) { s = 0; ph ^= 1u; }
@@ -450,7 +471,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       int hc = 0, ln = 0;  // high items and low-buffer uses so far (the drains count alike)
       bool ok = true;
       for (int t = cid; t < ntiles && ok; t += ncl) {
-        const TileWork w = tile_work(t, tile_list, tiles_m, tiles_n, nksteps, upper);
+        const TileWork w = tile_work(t, tile_list, tiles_m, tiles_n, nksteps, upper, KS);
         const int nL = pairs_l * w.nch, nunits = (pairs_h + pairs_l) * w.nch;
         const int lb = ln & 1;
         if (nL > 0) {
@@ -476,11 +497,11 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           if (!mbar_wait_warp_cl(&sh->full[s], ph, cta_err)) { ok = false; break; }
           if (issuer) {
             const uint64_t da = dA0 + (uint64_t)(s * (P_A_BYTES >> 4)), db = dB0 + (uint64_t)(s * (P_B_BYTES >> 4));
-            if (kind0 == 2) mma_pair_scaled(d_tmem, da, db);
-            else mma_pair(d_tmem, da, db, (uint32_t)kind0);
-            mma_pair(d_tmem, da + 2, db + 2, 1u);  // +32 bytes per K = 16 inside the swizzle row
-            mma_pair(d_tmem, da + 4, db + 4, 1u);
-            mma_pair(d_tmem, da + 6, db + 6, 1u);
+            if (!TF32 && kind0 == 2) mma_pair_scaled(d_tmem, da, db);
+            else mma_pair<TF32>(d_tmem, da, db, (uint32_t)(kind0 != 0));
+            mma_pair<TF32>(d_tmem, da + 2, db + 2, 1u);  // +32 bytes per MMA (K = 16 BF16, 8 TF32)
+            mma_pair<TF32>(d_tmem, da + 4, db + 4, 1u);
+            mma_pair<TF32>(d_tmem, da + 6, db + 6, 1u);
             commit_pair(&sh->empty[s]);
           }
           __syncwarp();
@@ -489,10 +510,10 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             if (!mbar_wait_warp_cl(&sh->full[s], ph, cta_err)) { ok = false; break; }
             if (issuer) {
               const uint64_t da = dA0 + (uint64_t)(s * (P_A_BYTES >> 4)), db = dB0 + (uint64_t)(s * (P_B_BYTES >> 4));
-              mma_pair(d_tmem, da, db, 1u);
-              mma_pair(d_tmem, da + 2, db + 2, 1u);
-              mma_pair(d_tmem, da + 4, db + 4, 1u);
-              mma_pair(d_tmem, da + 6, db + 6, 1u);
+              mma_pair<TF32>(d_tmem, da, db, 1u);
+              mma_pair<TF32>(d_tmem, da + 2, db + 2, 1u);
+              mma_pair<TF32>(d_tmem, da + 4, db + 4, 1u);
+              mma_pair<TF32>(d_tmem, da + 6, db + 6, 1u);
               commit_pair(&sh->empty[s]);
             }
             __syncwarp();
@@ -526,7 +547,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     int hc = 0, ln = 0;
     bool ok = true;
     for (int t = cid; t < ntiles && ok; t += ncl) {
-      const TileWork w = tile_work(t, tile_list, tiles_m, tiles_n, nksteps, upper);
+      const TileWork w = tile_work(t, tile_list, tiles_m, tiles_n, nksteps, upper, KS);
       const int nL = pairs_l * w.nch;
       long long R[64];
 #pragma unroll
@@ -658,14 +679,18 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, void* base, int64_t Rp, int64_t Kp, int k, int box_rows) {
+// k planes [k][Rp][Kp] of BF16 (or, tf32, of 32-bit TF32 words); boxes of one
+// 128-byte swizzle row (64 or 32 elements) by box_rows rows.
+bool make_map(CUtensorMap* m, void* base, int64_t Rp, int64_t Kp, int k, int box_rows, bool tf32) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
+  const cuuint64_t esz = tf32 ? 4 : 2;
   const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)Rp, (cuuint64_t)k};
-  const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)(Rp * Kp * 2)};
-  const cuuint32_t box[3] = {KSTEP, (cuuint32_t)box_rows, 1};
+  const cuuint64_t strides[2] = {(cuuint64_t)Kp * esz, (cuuint64_t)(Rp * Kp * esz)};
+  const cuuint32_t box[3] = {(cuuint32_t)(ROW_BYTES / esz), (cuuint32_t)box_rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  return fn(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -673,14 +698,17 @@ bool make_map(CUtensorMap* m, void* base, int64_t Rp, int64_t Kp, int k, int box
 }  // namespace
 
 namespace {
-// Clusters of two k_ozaki_pair CTAs that fit on the device at once (cached per device).
+// Clusters of two k_ozaki_pair CTAs that fit on the device at once (cached per device;
+// both operand kinds use the same resources).
 int pair_clusters() {
   static int cached[64] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   if (cached[dev] > 0) return cached[dev];
-  if (cudaFuncSetAttribute(k_ozaki_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PAIR_SMEM_BYTES) !=
-      cudaSuccess)
+  if (cudaFuncSetAttribute(k_ozaki_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PAIR_SMEM_BYTES) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_ozaki_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PAIR_SMEM_BYTES) !=
+          cudaSuccess)
     return 0;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -694,7 +722,7 @@ int pair_clusters() {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_ozaki_pair, &cfg) != cudaSuccess || n <= 0) {
+  if (cudaOccupancyMaxActiveClusters(&n, k_ozaki_pair<false>, &cfg) != cudaSuccess || n <= 0) {
     // clusters are independent: any count is correct, the SM count / 2 is the natural one
     cudaGetLastError();
     int sms = 0;
@@ -711,7 +739,7 @@ int pair_clusters() {
 // mapped pinned host memory that the kernel reads directly (each CTA reads a few
 // entries), so no copy is queued before a launch. Null when that memory is
 // unavailable.
-const uint32_t* upper_tile_order(int tiles_m, int tiles_n, int nksteps, int ncl) {
+const uint32_t* upper_tile_order(int tiles_m, int tiles_n, int nksteps, int ncl, int ks) {
   static std::mutex mu;
   static std::map<std::tuple<int, int, int, int>, const uint32_t*> cache;
   std::lock_guard<std::mutex> lk(mu);
@@ -722,7 +750,7 @@ const uint32_t* upper_tile_order(int tiles_m, int tiles_n, int nksteps, int ncl)
   std::vector<T> v;
   for (int mp = 0; mp < tiles_m; ++mp)
     for (int nt = 0; nt < tiles_n; ++nt) {
-      const int lo = std::min(nksteps, mp * (2 * TILE / KSTEP)), hi = std::min(nksteps, (nt + 1) * (TILE / KSTEP));
+      const int lo = std::min(nksteps, mp * (2 * TILE / ks)), hi = std::min(nksteps, (nt + 1) * (TILE / ks));
       v.push_back({std::max(0, hi - lo), ((uint32_t)mp << 16) | (uint32_t)nt});
     }
   std::stable_sort(v.begin(), v.end(), [](const T& a, const T& b) { return a.cost > b.cost; });
@@ -747,11 +775,13 @@ const uint32_t* upper_tile_order(int tiles_m, int tiles_n, int nksteps, int ncl)
   return dev;
 }
 
+template <bool TF32>
 cudaError_t launch_pair(const OzLayout& L, const double* P, const double* Q, int64_t N, double alpha,
                         const Epilogue& e, int slices, unsigned int* flag, cudaStream_t st, bool upper,
                         bool literal) {
+  constexpr int KS = OperandKind<TF32>::KS;
   CUtensorMap ta, tb;
-  if (!make_map(&ta, L.Ps, L.Rp, L.Rp, slices, TILE) || !make_map(&tb, L.Qs, L.Rp, L.Rp, slices, TILE / 2))
+  if (!make_map(&ta, L.Ps, L.Rp, L.Rp, slices, TILE, TF32) || !make_map(&tb, L.Qs, L.Rp, L.Rp, slices, TILE / 2, TF32))
     return cudaErrorNotSupported;
   const int ncl_max = pair_clusters();
   if (ncl_max <= 0) return cudaErrorNotSupported;
@@ -759,7 +789,7 @@ cudaError_t launch_pair(const OzLayout& L, const double* P, const double* Q, int
   const int tiles_n = (int)(L.Rp / TILE);
   const int ncl = std::min(ncl_max, tiles_m * tiles_n);
   // triangular products: the balanced tile order (without it, the plain raster order, equally correct)
-  const uint32_t* list = upper ? upper_tile_order(tiles_m, tiles_n, (int)(L.Rp / KSTEP), ncl) : nullptr;
+  const uint32_t* list = upper ? upper_tile_order(tiles_m, tiles_n, (int)(L.Rp / KS), ncl, KS) : nullptr;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -772,16 +802,21 @@ cudaError_t launch_pair(const OzLayout& L, const double* P, const double* Q, int
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_ozaki_pair, ta, tb, (const int*)L.erow, (const int*)L.fcol, P, Q,
-                            (const double*)L.pdiag, (const double*)L.qdiag, N, alpha, slices, (int)(L.Rp / KSTEP),
+  return cudaLaunchKernelEx(&cfg, k_ozaki_pair<TF32>, ta, tb, (const int*)L.erow, (const int*)L.fcol, P, Q,
+                            (const double*)L.pdiag, (const double*)L.qdiag, N, alpha, slices, (int)(L.Rp / KS),
                             tiles_m, tiles_n, e, flag, list, upper ? 1 : 0, literal ? 1 : 0);
 }
 }  // namespace
 
 cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e, int slices,
-                          void* work, unsigned int* flag, cudaStream_t st, bool upper, bool literal) {
-  if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
-  return launch_pair(layout(work, N, slices), P, Q, N, alpha, e, slices, flag, st, upper, literal);
+                          void* work, unsigned int* flag, cudaStream_t st, bool upper, int mode) {
+  const int kmax = (mode == SPLIT_LITERAL_TF32) ? 4 : 8;
+  if (!ozaki_supported(N) || slices < 2 || slices > kmax || !work || !flag || mode < 0 || mode > 2)
+    return cudaErrorInvalidValue;
+  if (mode == SPLIT_LITERAL_TF32)  // TF32 planes take the room of two BF16 planes each
+    return launch_pair<true>(layout(work, N, 2 * slices), P, Q, N, alpha, e, slices, flag, st, upper, true);
+  return launch_pair<false>(layout(work, N, slices), P, Q, N, alpha, e, slices, flag, st, upper,
+                            mode == SPLIT_LITERAL_BF16);
 }
 
 cudaError_t wait_selftest(unsigned int* status, cudaStream_t st) {

@@ -93,14 +93,17 @@ cudaError_t norm1_noalloc(const double* A, int64_t N, double* dNorm, cudaStream_
 // ozaki_split writes the slice planes and scales of P (rows) and Q (columns)
 // into `work`; ozaki_product then forms alpha * (P Q) from them with the
 // fused epilogue.
+// `slices` counts BF16 planes; a TF32 plane takes the room of two.
 size_t ozaki_workspace_bytes(int64_t N, int slices);
-// literal: the plain floating-point split of BBC_PREC_SPLIT (each term the BF16
-// rounding of the remainder) with every term product accumulated in FP32.
+// Split modes: the exact BF16 digits, or the plain floating-point split (each term
+// the rounding of the remainder: BF16 for BBC_PREC_SPLIT, TF32 for
+// BBC_PREC_SPLIT_TF32 and BBC_PREC_FP32) with every term product accumulated in FP32.
+enum SplitMode { SPLIT_EXACT = 0, SPLIT_LITERAL_BF16 = 1, SPLIT_LITERAL_TF32 = 2 };
 cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices, void* work,
-                        unsigned int* flag, cudaStream_t st, bool literal = false);
+                        unsigned int* flag, cudaStream_t st, int mode = SPLIT_EXACT);
 cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
                           int slices, void* work, unsigned int* flag, cudaStream_t st, bool upper = false,
-                          bool literal = false);
+                          int mode = SPLIT_EXACT);
 bool ozaki_supported(int64_t N);
 // One warp waits, with the product kernel's bounded wait, on an mbarrier that
 // nothing arrives at; about 2 s later bit 1 (timeout) of *status is set.
@@ -114,11 +117,18 @@ cudaError_t complex_norm1(const double* A, int64_t N, double* partial, double* d
 cudaError_t complex_embed(const double* A, int64_t N, double* E, cudaStream_t st);
 cudaError_t complex_extract(const double* E, int64_t N, double* out, unsigned int* flag, cudaStream_t st);
 
-// Solve M X = B in place (X overwrites B, M is destroyed) (pade.cu). N > 1024 goes
-// through cuSOLVER (loaded at run time) and needs an N x N scratch matrix.
+// Solve M X = B in place (X overwrites B, M is destroyed) (pade.cu). N > 112 runs
+// the blocked LU (lu_blocked.cu), which keeps its N pivot indices in `scratch`
+// (at least N ints; an N x N matrix of the workspace serves). No allocation.
 cudaError_t lu_solve_inplace(double* M, double* B, int64_t N, unsigned int* flag, cudaStream_t st,
                              double* scratch = nullptr);
-bool lu_solve_large_available();
+// The blocked LU with partial pivoting and both triangular solves (lu_blocked.cu);
+// lu_blocked_max_n: the largest N its cluster-resident panels allow on this device.
+cudaError_t lu_blocked_solve(double* M, double* B, int64_t N, unsigned int* flag, cudaStream_t st, void* scratch);
+int64_t lu_blocked_max_n();
+// Whether the blocked LU's one-time device set-up (kernel attributes, cluster
+// occupancy) has run on the current device; it must run outside any stream capture.
+bool lu_blocked_ready();
 
 // The (m, s)-proposing MLP (mlp.cu).
 int64_t mlp_param_count(int n_in, int hid, int n_out);

@@ -16,8 +16,10 @@
 // epilogue: P Q = P'Q' + D_P Q + P D_Q - D_P D_Q (elementwise: P_ii Q_ij +
 // P_ij Q_jj - [i = j] P_ii Q_jj).
 //
-// The literal split (BBC_PREC_SPLIT) writes, instead of digits, K BF16 terms of the
-// scaled value, each the rounding of what the earlier ones left.
+// The literal split writes, instead of digits, K terms of the scaled value, each
+// the rounding of what the earlier ones left: BF16 terms (BBC_PREC_SPLIT) or TF32
+// terms (BBC_PREC_SPLIT_TF32, BBC_PREC_FP32), the latter as 32-bit words whose low
+// 13 mantissa bits are zero, which the kind::tf32 MMAs read unchanged.
 //
 // HBM-bound kernels: per product they read the two FP64 operands (twice each:
 // once for the scale exponents) and write 2 k BF16 planes.
@@ -25,6 +27,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 #include "slices.h"
@@ -90,15 +93,37 @@ __device__ __forceinline__ void float_terms(double x, int Emax, uint32_t (&out)[
     r -= (double)__bfloat162float(b);
   }
 }
-template <int K, bool FLT>
+// TF32 rounding (to nearest, ties away from zero) of a binary32 value: the
+// 32-bit word with the low 13 mantissa bits cleared.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// The literal split in TF32 terms: as float_terms, each term the TF32 rounding of
+// (the binary32 rounding of) what the earlier terms left.
+template <int K>
+__device__ __forceinline__ void tf32_terms(double x, int Emax, uint32_t (&out)[K]) {
+  double r = ldexp(x, -(Emax - 1021));
+#pragma unroll
+  for (int p = 0; p < K; ++p) {
+    const uint32_t t = tf32_rna((float)r);
+    out[p] = t;
+    r -= (double)__uint_as_float(t);
+  }
+}
+// MODE: 0 exact digits (BF16), 1 literal BF16 terms, 2 literal TF32 terms.
+template <int K, int MODE>
 __device__ __forceinline__ void terms(double x, int Emax, uint32_t (&out)[K]) {
-  if (FLT) float_terms<K>(x, Emax, out);
+  if (MODE == 2) tf32_terms<K>(x, Emax, out);
+  else if (MODE == 1) float_terms<K>(x, Emax, out);
   else digits<K>(fixed_point(x, Emax, K), out);
 }
 
-// P (N x N, row-major FP64) -> K slice planes [K][Rp][Kp] of BF16 digits with
-// row exponents. One warp per row; padding rows/columns are written as zeros.
-template <int K, bool FLT>
+// P (N x N, row-major FP64) -> K slice planes [K][Rp][Kp] of BF16 digits (or
+// literal terms: BF16, or TF32 in 32-bit words) with row exponents. One warp per
+// row; padding rows/columns are written as zeros.
+template <int K, int MODE>
 __global__ void __launch_bounds__(256)
 k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, uint16_t* __restrict__ planes,
              int* __restrict__ erow, double* __restrict__ pdiag, unsigned int* __restrict__ status) {
@@ -147,16 +172,23 @@ k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, ui
     const double x0 = elem(j), x1 = elem(j + 1);
     const double x2 = (j2 < Kp) ? elem(j2) : 0.0, x3 = (j2 < Kp) ? elem(j2 + 1) : 0.0;
     uint32_t d0[K], d1[K];
-    terms<K, FLT>(x0, Emax, d0);
-    terms<K, FLT>(x1, Emax, d1);
-    const size_t idx = ((size_t)row * Kp + j) >> 1;
+    terms<K, MODE>(x0, Emax, d0);
+    terms<K, MODE>(x1, Emax, d1);
+    const size_t idx = ((size_t)row * Kp + j) >> 1;  // element pair (j, j + 1)
+    uint2* out2 = reinterpret_cast<uint2*>(planes);    // TF32: one 32-bit word per element
 #pragma unroll
-    for (int p = 0; p < K; ++p) out[p * (plane >> 1) + idx] = d0[p] | (d1[p] << 16);
+    for (int p = 0; p < K; ++p) {
+      if (MODE == 2) out2[p * (plane >> 1) + idx] = make_uint2(d0[p], d1[p]);
+      else out[p * (plane >> 1) + idx] = d0[p] | (d1[p] << 16);
+    }
     if (j2 < Kp) {
-      terms<K, FLT>(x2, Emax, d0);
-      terms<K, FLT>(x3, Emax, d1);
+      terms<K, MODE>(x2, Emax, d0);
+      terms<K, MODE>(x3, Emax, d1);
 #pragma unroll
-      for (int p = 0; p < K; ++p) out[p * (plane >> 1) + idx + 32] = d0[p] | (d1[p] << 16);
+      for (int p = 0; p < K; ++p) {
+        if (MODE == 2) out2[p * (plane >> 1) + idx + 32] = make_uint2(d0[p], d1[p]);
+        else out[p * (plane >> 1) + idx + 32] = d0[p] | (d1[p] << 16);
+      }
     }
   }
 }
@@ -180,12 +212,14 @@ k_col_maxexp(const double* __restrict__ Q, int64_t N, int64_t rows_per, int* __r
 // Q) with column exponents fcol. 64 x 32 tiles (rows x columns of Q) transposed
 // through shared memory: each thread keeps eight loads in flight, and each warp
 // writes a plane row's 64 digits as one 128-byte line.
-template <int K, bool FLT>
+template <int K, int MODE>
 __global__ void __launch_bounds__(256)
 k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, const int* __restrict__ fexp,
              uint16_t* __restrict__ planes, int* __restrict__ fcol, double* __restrict__ qdiag,
              unsigned int* __restrict__ status) {
-  __shared__ __align__(16) uint16_t tile[K][32][66];  // [plane][column of Q][row of Q], rows padded
+  // [plane][column of Q][row of Q], rows padded; TF32 terms take a 32-bit word each
+  using Elem = typename std::conditional<MODE == 2, uint32_t, uint16_t>::type;
+  __shared__ __align__(16) Elem tile[K][32][MODE == 2 ? 65 : 66];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t i0 = (int64_t)blockIdx.x * 64;  // rows of Q (the K dimension)
   const int64_t j0 = (int64_t)blockIdx.y * 32;  // columns of Q
@@ -207,30 +241,36 @@ k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, co
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     uint32_t d[K];
-    terms<K, FLT>(x[r], Emax, d);
+    terms<K, MODE>(x[r], Emax, d);
 #pragma unroll
-    for (int p = 0; p < K; ++p) tile[p][tx][ty + 8 * r] = (uint16_t)d[p];
+    for (int p = 0; p < K; ++p) tile[p][tx][ty + 8 * r] = (Elem)d[p];
   }
   __syncthreads();
   const size_t plane = (size_t)Rp * Kp;
   uint32_t* out = reinterpret_cast<uint32_t*>(planes);
+  uint2* out2 = reinterpret_cast<uint2*>(planes);
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int jl = ty + 8 * r;
     const int64_t jj = j0 + jl, ii = i0 + 2 * tx;
     if (jj < Rp && ii < Kp) {
 #pragma unroll
-      for (int p = 0; p < K; ++p)
-        out[(p * plane + (size_t)jj * Kp + ii) >> 1] = *reinterpret_cast<const uint32_t*>(&tile[p][jl][2 * tx]);
+      for (int p = 0; p < K; ++p) {
+        if (MODE == 2)
+          out2[(p * plane + (size_t)jj * Kp + ii) >> 1] =
+              make_uint2((uint32_t)tile[p][jl][2 * tx], (uint32_t)tile[p][jl][2 * tx + 1]);
+        else
+          out[(p * plane + (size_t)jj * Kp + ii) >> 1] = *reinterpret_cast<const uint32_t*>(&tile[p][jl][2 * tx]);
+      }
     }
   }
 }
 
-template <int K, bool FLT>
+template <int K, int MODE>
 cudaError_t split_both(const double* P, const double* Q, int64_t N, int64_t Rp, uint16_t* Ps, uint16_t* Qs,
                        int* erow, int* fcol, int* fexp, double* pdiag, double* qdiag, unsigned int* status,
                        cudaStream_t st) {
-  k_split_rows<K, FLT><<<(unsigned)((Rp + 7) / 8), 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
+  k_split_rows<K, MODE><<<(unsigned)((Rp + 7) / 8), 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
   cudaError_t err = cudaMemsetAsync(fexp, 0, (size_t)N * sizeof(int), st);
   if (err != cudaSuccess) return err;
   const int64_t colblocks = (N + 255) / 256;
@@ -238,7 +278,7 @@ cudaError_t split_both(const double* P, const double* Q, int64_t N, int64_t Rp, 
   slabs = std::min<int64_t>(slabs, (N + 63) / 64);
   const int64_t rows_per = (N + slabs - 1) / slabs;
   k_col_maxexp<<<dim3((unsigned)colblocks, (unsigned)slabs), 256, 0, st>>>(Q, N, rows_per, fexp);
-  k_split_cols<K, FLT><<<dim3((unsigned)(Rp / 64), (unsigned)(Rp / 32)), 256, 0, st>>>(Q, N, Rp, Rp, fexp, Qs, fcol,
+  k_split_cols<K, MODE><<<dim3((unsigned)(Rp / 64), (unsigned)(Rp / 32)), 256, 0, st>>>(Q, N, Rp, Rp, fexp, Qs, fcol,
                                                                                    qdiag, status);
   return cudaGetLastError();
 }
@@ -255,25 +295,41 @@ size_t ozaki_workspace_bytes(int64_t N, int slices) {
 }
 
 
-template <bool FLT>
+template <int MODE>
 cudaError_t split_k(const double* P, const double* Q, int64_t N, int slices, const OzLayout& L, unsigned int* flag,
                     cudaStream_t st) {
-  switch (slices) {
-    case 2: return split_both<2, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 3: return split_both<3, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 4: return split_both<4, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 5: return split_both<5, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 6: return split_both<6, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    case 7: return split_both<7, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
-    default: return split_both<8, FLT>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+#define BBC_SPLIT_CASE(k) \
+  case k: return split_both<k, MODE>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+  if (MODE == 2) {  // TF32 terms: 2..4
+    switch (slices) {
+      BBC_SPLIT_CASE(2)
+      BBC_SPLIT_CASE(3)
+      default: return split_both<4, MODE>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag,
+                                          flag, st);
+    }
   }
+  switch (slices) {
+    BBC_SPLIT_CASE(2)
+    BBC_SPLIT_CASE(3)
+    BBC_SPLIT_CASE(4)
+    BBC_SPLIT_CASE(5)
+    BBC_SPLIT_CASE(6)
+    BBC_SPLIT_CASE(7)
+    default: return split_both<8, MODE>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+  }
+#undef BBC_SPLIT_CASE
 }
 
+// mode: 0 exact BF16 digits, 1 literal BF16 terms, 2 literal TF32 terms (whose planes
+// take two BF16 planes' room each: the layout is that of 2 x slices BF16 planes).
 cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices, void* work, unsigned int* flag,
-                        cudaStream_t st, bool literal) {
-  if (!ozaki_supported(N) || slices < 2 || slices > 8 || !work || !flag) return cudaErrorInvalidValue;
-  const OzLayout L = layout(work, N, slices);
-  return literal ? split_k<true>(P, Q, N, slices, L, flag, st) : split_k<false>(P, Q, N, slices, L, flag, st);
+                        cudaStream_t st, int mode) {
+  const int kmax = (mode == 2) ? 4 : 8;
+  if (!ozaki_supported(N) || slices < 2 || slices > kmax || !work || !flag || mode < 0 || mode > 2)
+    return cudaErrorInvalidValue;
+  const OzLayout L = layout(work, N, mode == 2 ? 2 * slices : slices);
+  if (mode == 2) return split_k<2>(P, Q, N, slices, L, flag, st);
+  return mode == 1 ? split_k<1>(P, Q, N, slices, L, flag, st) : split_k<0>(P, Q, N, slices, L, flag, st);
 }
 
 }  // namespace bbc

@@ -250,10 +250,10 @@ def test_small_workload_pade26(h, api):
 
 
 # N <= 112: the shared-memory solve (one CTA per 4 right-hand sides, each factoring M);
-# 113..1024: the one-CTA global-memory solve
+# beyond: the blocked LU (cluster-factored panels, rank-32 updates)
 @pytest.mark.parametrize("n,norm,nonnormal", [(1, 0.5, False), (7, 3.0, False), (96, 20.0, False),
                                               (112, 40.0, False), (113, 5.0, True), (300, 100.0, True),
-                                              (257, 0.3, False)])
+                                              (257, 0.3, False), (1025, 2.0, False)])
 def test_pade26_matches_oracle(h, api, n, norm, nonnormal):
     A = W.nonnormal_upper(n, 7, norm) if nonnormal else W.gaussian(n, 8, norm)
     out = empty_like_dev(n)
@@ -276,19 +276,54 @@ def test_pade_scheme_selects_r10_or_r26(h, api, norm, want):
     assert rel_fro(to_host(out), ref) < 1e-12
 
 
-def test_pade26_beyond_single_cta_solve(h, api):
-    """N > 1024: the comparator's solve goes through the blocked library LU."""
-    A = W.gaussian(1500, 11, 8.0)
-    out = empty_like_dev(1500)
-    try:
-        info = h.expm(to_dev(A), out, 0.0, api.SCHEME_PADE26)
-    except api.BBCError as e:
-        if e.code == api.UNSUPPORTED:
-            pytest.skip("no cuSOLVER on this machine")
-        raise
+@pytest.mark.parametrize("n,idx", [(1500, None), (4096, 4)])
+def test_pade26_blocked_solve_large(h, api, n, idx):
+    """The comparator at N = 1500 and at the dense workload's 4096 (norm 20: r_26
+    with s = 2): products, the blocked LU solve and squarings against the oracle."""
+    A = W.gaussian(1500, 11, 8.0) if idx is None else W.dense_case(idx)
+    out = empty_like_dev(n)
+    info = h.expm(to_dev(A), out, 0.0, api.SCHEME_PADE26)
     want, oi = O.expm(A, "pade26")
     assert (info.m, info.s, info.products) == (oi.m, oi.s, oi.products)
     assert rel_fro(to_host(out), want) < 1e-12
+
+
+# ---- the comparator's solve on its own (bbc_solve): row interchanges exercised --------------------
+
+@pytest.mark.parametrize("n", [1, 5, 64, 112, 113, 130, 500, 1025, 2000])
+def test_solve_matches_oracle(h, api, n):
+    """Gaussian matrices need row interchanges all the way down (the Pade denominators
+    rarely do): the GPU solve against the oracle's elimination, same partial pivoting."""
+    rng = np.random.default_rng(500 + n)
+    M = rng.standard_normal((n, n))
+    B = rng.standard_normal((n, n))
+    dM, dB = to_dev(M), to_dev(B)
+    h.solve(dM, dB)
+    want = O.solve(M, B)
+    cond = np.linalg.cond(M)
+    assert rel_fro(to_host(dB), want) < 1e-15 * max(10.0, cond) * np.sqrt(n), (n, rel_fro(to_host(dB), want))
+
+
+def test_solve_forced_pivots_and_singular(h, api):
+    """A permuted, scaled identity plus noise: every pivot is forced and the result
+    is known; a rank-deficient M reports BBC_OVERFLOW."""
+    n = 300
+    rng = np.random.default_rng(7)
+    perm = rng.permutation(n)
+    M = np.zeros((n, n))
+    M[np.arange(n), perm] = rng.uniform(1.0, 2.0, n) * rng.choice([-1.0, 1.0], n)
+    M += 1e-3 * rng.standard_normal((n, n))
+    X = rng.standard_normal((n, n))
+    B = M @ X
+    dM, dB = to_dev(M), to_dev(B)
+    h.solve(dM, dB)
+    assert rel_fro(to_host(dB), X) < 1e-12
+    assert rel_fro(to_host(dB), O.solve(M, B)) < 1e-13
+    S = rng.standard_normal((n, n))
+    S[:, 5] = 0.0                             # a zero column stays exactly zero under elimination
+    with pytest.raises(api.BBCError) as e:
+        h.solve(to_dev(S), to_dev(np.eye(n)))
+    assert e.value.code == api.OVERFLOW
 
 
 def test_pade26_split_products(h, api):

@@ -186,3 +186,72 @@ def test_literal_split_expm_and_fp64_last_squarings(h, api):
     assert 1e-10 < e_lit < 1e-4
     assert e_last < e_lit            # FP64 squarings stop the 2^s amplification
     assert e_fp64 < 1e-12            # an all-FP64 run is unchanged by the flag
+
+
+# ---- the literal split in TF32 terms (BBC_PREC_SPLIT_TF32, BBC_PREC_FP32; kind::tf32 MMAs) ------------
+
+@pytest.mark.parametrize("n", [1, 7, 64, 200, 256, 300])
+@pytest.mark.parametrize("upper", [False, True])
+def test_tf32_terms_exact_on_small_integers(h, api, n, upper):
+    """Entries of at most 7 significant bits (integers up to 127 times a power of two
+    per row / column) are one TF32 term each, and every partial sum of their products
+    stays below 300 x 127^2 < 2^24, so the FP32 accumulation is exact: the TF32 path
+    must give the exact product. Pins the kind::tf32 descriptor, the 32-bit TMA layout
+    and the K steps of 32 elements, also on triangles (K ranges per tile)."""
+    rng = np.random.default_rng(1000 + n)
+    P = rng.integers(-127, 128, size=(n, n)).astype(np.float64) * np.ldexp(1.0, rng.integers(-6, 6, size=(n, 1)))
+    Q = rng.integers(-127, 128, size=(n, n)).astype(np.float64) * np.ldexp(1.0, rng.integers(-6, 6, size=(1, n)))
+    flags = api.PREC_SPLIT_TF32 | api.ozaki_slices(2)
+    if upper:
+        P, Q = np.triu(P), np.triu(Q)
+        flags |= api.UPPER
+    C = empty_like_dev(n)
+    h.gemm(to_dev(P), to_dev(Q), C, flags)
+    assert np.array_equal(to_host(C), O.gemm(P, Q))
+
+
+def test_tf32_literal_split_products(h, api):
+    """Two TF32 terms per operand (about 22 significant bits) with FP32 sums: the
+    error sits at the FP32 accumulation floor (as the 3-term BF16 split's does), so
+    a third term (BBC_PREC_FP32) is no worse and no better than that floor; all far
+    from the exact form."""
+    n = 512
+    P = W.gaussian(n, 71, None)
+    Q = W.gaussian(n, 72, None)
+    ref = O.gemm(P, Q)
+    err = {}
+    for name, fl in (("tf32x2", api.PREC_SPLIT_TF32), ("tf32x3", api.PREC_SPLIT_TF32 | api.ozaki_slices(3)),
+                     ("fp32", api.PREC_FP32), ("bf16x3", api.PREC_SPLIT)):
+        C = empty_like_dev(n)
+        h.gemm(to_dev(P), to_dev(Q), C, fl)
+        err[name] = rel_fro(to_host(C), ref)
+    print("literal split product errors (N = 512):", {k: f"{v:.2e}" for k, v in err.items()})
+    assert 1e-8 < err["tf32x2"] < 1e-5, err
+    assert err["tf32x3"] <= 1.5 * err["tf32x2"], err
+    assert err["fp32"] == err["tf32x3"], err          # BBC_PREC_FP32 is the 3-term TF32 split
+    assert 0.2 < err["tf32x2"] / err["bf16x3"] < 5, err
+
+
+def test_tf32_flag_checks(h, api):
+    P = to_dev(np.eye(8))
+    with pytest.raises(api.BBCError) as e:
+        h.gemm(P, P, empty_like_dev(8), api.PREC_SPLIT_TF32 | api.ozaki_slices(5))
+    assert e.value.code == api.INVALID_ARG
+    with pytest.raises(api.BBCError) as e:
+        h.gemm(P, P, empty_like_dev(8), api.PREC_FP32 | api.ozaki_slices(2))
+    assert e.value.code == api.INVALID_ARG
+
+
+def test_tf32_literal_expm(h, api):
+    A = W.gaussian(300, 73, 20.0)      # s = 5
+    want, oi = O.expm(A, "new")
+    out = empty_like_dev(300)
+    errs = {}
+    for name, fl in (("tf32x2", api.PREC_SPLIT_TF32), ("tf32x2+fp64 last", api.PREC_SPLIT_TF32 |
+                                                        api.square_fp64_last(oi.s)), ("fp32", api.PREC_FP32)):
+        info = h.expm(to_dev(A), out, 0.0, fl)
+        assert (info.m, info.s, info.products) == (oi.m, oi.s, oi.products)
+        errs[name] = rel_fro(to_host(out), want)
+    assert 1e-9 < errs["tf32x2"] < 1e-3, errs
+    assert errs["tf32x2+fp64 last"] < errs["tf32x2"], errs
+    assert errs["fp32"] <= 1.5 * errs["tf32x2"], errs

@@ -67,9 +67,21 @@ def _triangular_pins() -> bool:
     return all(E[i, i] == math.exp(A[i, i]) for i in range(12))
 
 
+def _solve_pins() -> bool:
+    from test_oracle_solve import exact_solve
+    P = np.array([[0.0, 2.0, 1.0, 0.0], [1.0, 0.0, 0.0, 3.0], [0.0, 1.0, 0.0, 0.0], [2.0, 0.0, 1.0, 1.0]])
+    Q = np.arange(16.0).reshape(4, 4) - 5.0
+    try:
+        got = O.solve(P, Q)
+    except ValueError:
+        return False
+    want = exact_solve(P, Q)
+    return bool(np.all(np.isfinite(got))) and np.abs(got - want).max() <= 1e-14 * np.abs(want).max()
+
+
 def all_pins_pass() -> bool:
     return (_taylor_pins() and _closed_form_pins() and _norm_and_selection_pins()
-            and _coefficient_pins() and _triangular_pins())
+            and _coefficient_pins() and _triangular_pins() and _solve_pins())
 
 
 MUTATIONS = {
@@ -85,6 +97,7 @@ MUTATIONS = {
     10: "triangular path: superdiagonal without the divided difference of exp",
     11: "triangular path: exact diagonals not put back after the last squaring",
     12: "Pade scheme: r_10 charged 6 products, as r_26",
+    13: "comparator's solve without row interchanges",
 }
 
 
