@@ -432,11 +432,12 @@ def run_dense(args, torch, dist, api, rank, world, local):
                 "flops_per_launch": pairs * flops_per_product, "avg_launch_ms": avg_ms,
                 "launches": prod_launches, "logical_fp64_tflops": logical,
                 "split_ms_per_product": split_ms / max(1, split_launches / 3)}
-    # the CPU-baseline leg: the oracle timed on a sample of the workload; its outputs are
-    # also the reference the timed form's results are checked against (same (m, s))
-    cpu, oracle_check = None, None
+    # the CPU-baseline leg: the oracle timed on a sample of the workload (the whole
+    # workload for the 8192 one); its outputs are also the reference the timed form's
+    # results (and, at 8192, every precision form's) are checked against (same (m, s))
+    cpu, oracle_check, forms = None, None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        idx = DENSE_CPU_SAMPLE if len(mats) == 12 else (0,)
+        idx = DENSE_CPU_SAMPLE if len(mats) == 12 else tuple(range(len(mats)))
         cpu, outs = cpu_dense_sample(mats, prods, idx)
         tol = 1e-12 if args.workload == "dense4096" else 1e-10
         errs = []
@@ -445,6 +446,8 @@ def run_dense(args, torch, dist, api, rank, world, local):
             errs.append(float(np.linalg.norm(got - outs[i]) / np.linalg.norm(outs[i])))
         oracle_check = {"matrices": list(idx), "rel_fro_vs_oracle": errs, "tolerance": tol,
                         "tolerance_met": max(errs) <= tol}
+        if args.workload == "large":
+            forms = large_forms(torch, api, h, stream, dA, outs, prods)
         del outs
     h.close()
     line = {
@@ -459,13 +462,48 @@ def run_dense(args, torch, dist, api, rank, world, local):
                  "structure": "upper triangular inputs (the non-normal six) are detected in the 1-norm pass and "
                               "run on the triangles, with the exact diagonal and superdiagonal put back "
                               "(Section 5); the flop figures count the triangle products' own work"},
-        "oracle_check": oracle_check,
+        "oracle_check": oracle_check, "precision_forms": forms,
         "tflops_logical": prod_flops * world / (ms / 1e3) / 1e12,
         "time_share": {"product_ms": prod_ms, "split_ms": split_ms, "norm_ms": norm_ms, "timed_ms": ms},
         "roofline": roof, "plain_fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,
     }
     return line
+
+
+def large_forms(torch, api, h, stream, dA, outs, prods):
+    """The precision config's forms on the 8192 matrices, one pass each (event-timed,
+    after one untimed pass), with every run's relative Frobenius error against the
+    oracle's result at the same (m, s): the exact slices, the stated literal splits
+    (3 BF16 terms, 2 TF32 terms) with and without the squarings on the FP64 pipe,
+    FP32-accurate products (3 TF32 terms), and all-FP64 products."""
+    res = {}
+    for name, fl in (("exact 6 BF16 slices", api.PREC_OZAKI | api.ozaki_slices(6)),
+                     ("exact 7 BF16 slices", api.PREC_OZAKI),
+                     ("literal 3 BF16 terms", api.PREC_SPLIT | api.ozaki_slices(3)),
+                     ("literal 3 BF16 terms, FP64 squarings", api.PREC_SPLIT | api.ozaki_slices(3)
+                      | api.square_fp64_last(15)),
+                     ("literal 2 TF32 terms", api.PREC_SPLIT_TF32 | api.ozaki_slices(2)),
+                     ("literal 2 TF32 terms, FP64 squarings", api.PREC_SPLIT_TF32 | api.ozaki_slices(2)
+                      | api.square_fp64_last(15)),
+                     ("FP32 products (3 TF32 terms)", api.PREC_FP32),
+                     ("FP64 products", api.PREC_FP64)):
+        out = torch.empty_like(dA[0])
+        runs = []
+        for i, a in enumerate(dA):
+            h.expm(a, out, 0.0, api.SCHEME_NEW | fl, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = h.expm(a, out, 0.0, api.SCHEME_NEW | fl, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            runs.append({"m": info.m, "s": info.s, "ms": e0.elapsed_time(e1),
+                         "rel_fro_vs_oracle": float(np.linalg.norm(got - outs[i]) / np.linalg.norm(outs[i]))})
+        res[name] = {"expm_per_s": len(dA) / (sum(r["ms"] for r in runs) / 1e3), "runs": runs,
+                     "meets_1e-10": all(r["rel_fro_vs_oracle"] <= 1e-10 for r in runs)}
+        del out
+    return res
 
 
 def run_batch(args, torch, dist, api, rank, world, local, mats):

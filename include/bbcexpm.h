@@ -78,7 +78,13 @@ typedef enum {
 /* bits 16-19: the last n squarings run on the FP64 pipe whatever the product precision
  * (the squarings amplify a product's error 2^s-fold) */
 #define BBC_SQUARE_FP64_LAST(n) (((n) & 0xF) << 16)
-/* selection of (m, s) in bbc_expm_batched (bits 12-13; default: the paper's rule) */
+/* selection of (m, s) (bits 12-13; default: the paper's rule) in bbc_expm_batched and in
+ * bbc_expm. bbc_expm runs such a call as a batch of one through the persistent batched
+ * kernel (which computes the power-norm estimates, the network and the certificate):
+ * it needs bbc_batch_reserve(max_n >= N) (N <= 512), scheme NEW and FP64 products
+ * (BBC_UNSUPPORTED otherwise), and for BBC_SELECT_LEARNED an installed network;
+ * bbc_info.selector then reports 2 certified by ||A||_1, 3 by alpha_2, 4 fallback to
+ * the paper's rule, 5 the alpha rule; no triangular structure is detected there. */
 #define BBC_SELECT_LEARNED 0x1000  /* network proposal, certified, else the paper's rule */
 #define BBC_SELECT_ALPHA 0x2000    /* cheapest (m, s) certified by ||A|| or alpha_2 (computes A^2, A^3) */
 #define BBC_SELECT_MASK 0x3000
@@ -181,7 +187,8 @@ int bbc_taylor(bbc_handle h, const double* dA, int64_t N, int m, int s, double* 
                void* stream, int* products);
 
 /* dOut = exp(dA). tol is the backward-error target u (eq. theta);
- * tol <= 0 selects u = 2^-53. info (may be NULL) receives the outcome. */
+ * tol <= 0 selects u = 2^-53. info (may be NULL) receives the outcome.
+ * With BBC_SELECT_LEARNED or BBC_SELECT_ALPHA see the selection flags above. */
 int bbc_expm(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol, int flags,
              void* stream, bbc_info* info);
 

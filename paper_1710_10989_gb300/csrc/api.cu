@@ -2,6 +2,7 @@
 // workspace, backward-error thresholds, (m, s) selection, program execution and
 // the squaring chain of scaling and squaring (eq. eses).
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -26,7 +27,8 @@ struct bbc_handle_s {
   double* dnorm = nullptr;        // device ||A||_1
   unsigned int* dflag = nullptr;  // device non-finite flag
   unsigned int* dlower = nullptr; // device: A has a nonzero below its diagonal
-  void* hstage = nullptr;         // pinned host staging: [0] norm, [1] flag
+  void* hstage = nullptr;         // mapped pinned host staging: [0] norm, [1] flag, [2] lower flag
+  void* hstage_dev = nullptr;     // its device address (null: not mapped, copies go through memcpy)
   void* ozaki = nullptr;          // Ozaki slice workspace
   size_t ozaki_bytes = 0;
   // profiling: launch counters per kernel class and, when enabled, event pairs
@@ -46,6 +48,10 @@ struct bbc_handle_s {
   double* cplx = nullptr;         // complex calls: two (2N)^2 real forms and the norm partials
   int64_t cplx_n = 0;
   void* batch_work = nullptr;
+  // bbc_expm with a certified selection runs as a batch of one: its device descriptor
+  // (pointers, size, bbc_info) and the pinned host copy it is filled from
+  void* one_dev = nullptr;
+  void* one_host = nullptr;
   int64_t io_n = 0;               // N the host-call staging buffers are sized for
   double* io = nullptr;           // 4 * N * N doubles: device copies of two inputs and two outputs
   cudaStream_t copy_in = nullptr;   // host-call pipeline: host -> device copies
@@ -58,6 +64,18 @@ struct bbc_handle_s {
 namespace {
 
 thread_local std::string g_err;
+
+// Descriptor of a batch of one (bbc_expm with a certified selection).
+struct OneDesc {
+  const void* a;
+  void* out;
+  int64_t n;
+  bbc_info info;
+};
+constexpr size_t ONE_DESC_BYTES = 256;
+static_assert(sizeof(OneDesc) <= ONE_DESC_BYTES, "descriptor room");
+int batched_locked(bbc_handle h, const void* const* dA, const void* const* dB, const int64_t* dNs, int64_t count,
+                   void* const* dOut, int dtype, double u, int flags, cudaStream_t st, bbc_info* dInfo);
 
 // Products rebuilt from slices on the tensor cores: the exact form (BBC_PREC_OZAKI,
 // default 7 BF16 slices) or the literal split in BF16 terms (BBC_PREC_SPLIT, default 3)
@@ -513,6 +531,18 @@ int begin(bbc_handle h) {
   return BBC_OK;
 }
 
+// A few bytes of device state into the handle's host staging `dst` (inside hstage):
+// written by a kernel through the mapped address, so that no copy engine is involved
+// (a large device-to-host copy in flight on another stream would hold it up), or by
+// cudaMemcpyAsync where the staging is not mapped.
+cudaError_t to_host(bbc_handle h, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (h->hstage_dev) {
+    char* d = static_cast<char*>(h->hstage_dev) + (static_cast<char*>(dst) - static_cast<char*>(h->hstage));
+    return copy_to_mapped(d, src, bytes, st);
+  }
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+}
+
 // ||A||_1 to the host; with `upper` non-null also whether A is upper triangular
 // (found in the same pass over A).
 int read_norm(bbc_handle h, const double* A, int64_t N, cudaStream_t st, double* norm, bool* upper = nullptr) {
@@ -524,8 +554,8 @@ int read_norm(bbc_handle h, const double* A, int64_t N, cudaStream_t st, double*
   if (e != cudaSuccess) return cuda_fail(e, "norm1");
   double* hs = (double*)h->hstage;
   unsigned int* hl = (unsigned int*)(hs + 2);
-  BBC_CUDA(cudaMemcpyAsync(hs, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
-  if (upper) BBC_CUDA(cudaMemcpyAsync(hl, h->dlower, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  BBC_CUDA(to_host(h, hs, h->dnorm, sizeof(double), st));
+  if (upper) BBC_CUDA(to_host(h, hl, h->dlower, sizeof(unsigned int), st));
   BBC_CUDA(cudaStreamSynchronize(st));
   *norm = hs[0];
   if (upper) *upper = (*hl == 0) && N > 1;
@@ -534,7 +564,7 @@ int read_norm(bbc_handle h, const double* A, int64_t N, cudaStream_t st, double*
 
 int finish_status(bbc_handle h, cudaStream_t st, int* status) {
   unsigned int* hf = (unsigned int*)((double*)h->hstage + 1);
-  BBC_CUDA(cudaMemcpyAsync(hf, h->dflag, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  BBC_CUDA(to_host(h, hf, h->dflag, sizeof(unsigned int), st));
   BBC_CUDA(cudaStreamSynchronize(st));
   *status = (*hf & 2u) ? BBC_TIMEOUT : (*hf != 0) ? BBC_OVERFLOW : BBC_OK;
   return BBC_OK;
@@ -558,7 +588,11 @@ int bbc_create(bbc_handle* out, int device) {
   cudaError_t e = cudaMalloc(&h->dnorm, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->dflag, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&h->dlower, sizeof(unsigned int));
-  if (e == cudaSuccess) e = cudaMallocHost(&h->hstage, 64);
+  if (e == cudaSuccess) e = cudaHostAlloc(&h->hstage, 64, cudaHostAllocMapped | cudaHostAllocPortable);
+  if (e == cudaSuccess && cudaHostGetDevicePointer(&h->hstage_dev, h->hstage, 0) != cudaSuccess) {
+    cudaGetLastError();
+    h->hstage_dev = nullptr;
+  }
   if (e != cudaSuccess) {
     bbc_destroy(h);
     return cuda_fail(e, "bbc_create");
@@ -578,6 +612,8 @@ int bbc_destroy(bbc_handle h) {
   cudaFree(h->ozaki);
   cudaFree(h->io);
   cudaFree(h->batch_work);
+  cudaFree(h->one_dev);
+  if (h->one_host) cudaFreeHost(h->one_host);
   cudaFree(h->cplx);
   if (h->copy_in) cudaStreamDestroy(h->copy_in);
   if (h->copy_out) cudaStreamDestroy(h->copy_out);
@@ -858,7 +894,7 @@ int bbc_expm_complex(bbc_handle h, const double* dA, int64_t N, double* dOut, do
     if (e != cudaSuccess) return cuda_fail(e, "complex norm1");
   }
   double* hs = (double*)h->hstage;
-  BBC_CUDA(cudaMemcpyAsync(hs, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st));
+  BBC_CUDA(to_host(h, hs, h->dnorm, sizeof(double), st));
   BBC_CUDA(cudaStreamSynchronize(st));
   inf->norm1 = hs[0];
   if (!std::isfinite(inf->norm1)) {
@@ -893,6 +929,30 @@ int bbc_expm(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol
   const double u = tol > 0 ? tol : std::ldexp(1.0, -53);
   if (!valid_u(u)) return fail(BBC_INVALID_ARG, "tol out of range [2^-60, 2^-5]");
   if ((rc = check_flags(flags))) return rc;
+  if (flags & BBC_SELECT_MASK) {
+    // A certified (m, s) proposal (learned network, or the alpha_2 bound) needs the
+    // power-norm estimates and the network the persistent batched kernel carries:
+    // the matrix runs there as a batch of one.
+    if ((flags & BBC_SCHEME_MASK) != BBC_SCHEME_NEW || (flags & BBC_PREC_MASK) != BBC_PREC_FP64)
+      return fail(BBC_UNSUPPORTED, "bbc_expm: the learned and alpha selections run scheme NEW with FP64 products");
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (!h->batch_work || !h->one_dev || N > h->batch_nmax)
+      return fail(BBC_INVALID_ARG, "bbc_expm with a certified selection: call bbc_batch_reserve(max_n >= N) first");
+    cudaStream_t st = (cudaStream_t)stream;
+    OneDesc* host = static_cast<OneDesc*>(h->one_host);
+    OneDesc* dev = static_cast<OneDesc*>(h->one_dev);
+    host->a = dA;
+    host->out = dOut;
+    host->n = N;
+    BBC_CUDA(cudaMemcpyAsync(dev, host, offsetof(OneDesc, info), cudaMemcpyHostToDevice, st));
+    if ((rc = batched_locked(h, &dev->a, nullptr, &dev->n, 1, &dev->out, BBC_DTYPE_F64, u, flags, st, &dev->info)))
+      return rc;
+    BBC_CUDA(cudaMemcpyAsync(&host->info, &dev->info, sizeof(bbc_info), cudaMemcpyDeviceToHost, st));
+    BBC_CUDA(cudaStreamSynchronize(st));
+    if (info) *info = host->info;
+    if (host->info.status) return fail(host->info.status, "certified-selection exp(A) failed");
+    return BBC_OK;
+  }
   std::lock_guard<std::mutex> lk(h->mu);
   if ((rc = ensure_workspace(h, N, flags))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1217,6 +1277,8 @@ int bbc_batch_reserve(bbc_handle h, int64_t max_n, int flags) {
     h->batch_nmax = nmax;
     h->batch_split = want_split;
   }
+  if (!h->one_dev) BBC_CUDA(cudaMalloc(&h->one_dev, ONE_DESC_BYTES));
+  if (!h->one_host) BBC_CUDA(cudaMallocHost(&h->one_host, ONE_DESC_BYTES));
   return BBC_OK;
 }
 
@@ -1291,6 +1353,8 @@ int bbc_batch_order(const int64_t* hNs, int64_t count, int64_t* hOrder) {
   return BBC_OK;
 }
 
+}  // extern "C"
+
 namespace {
 int expm_batched_impl(bbc_handle h, const void* const* dA, const void* const* dB, const int64_t* dNs, int64_t count,
                       void* const* dOut, int dtype, double tol, int flags, void* stream, bbc_info* dInfo) {
@@ -1302,9 +1366,16 @@ int expm_batched_impl(bbc_handle h, const void* const* dA, const void* const* dB
   if (!valid_u(u)) return fail(BBC_INVALID_ARG, "tol out of range [2^-60, 2^-5]");
   if ((rc = check_flags(flags))) return rc;
   if ((rc = batch_flags_ok(flags))) return rc;
-  const bool split = (flags & BBC_PREC_MASK) == BBC_PREC_OZAKI;
   if (count == 0) return BBC_OK;
   std::lock_guard<std::mutex> lk(h->mu);
+  return batched_locked(h, dA, dB, dNs, count, dOut, dtype, u, flags, (cudaStream_t)stream, dInfo);
+}
+
+// The launch of bbc_expm_batched / bbc_expm_apply_batched once the arguments are
+// checked; the caller holds h->mu.
+int batched_locked(bbc_handle h, const void* const* dA, const void* const* dB, const int64_t* dNs, int64_t count,
+                   void* const* dOut, int dtype, double u, int flags, cudaStream_t st, bbc_info* dInfo) {
+  const bool split = (flags & BBC_PREC_MASK) == BBC_PREC_OZAKI;
   if (!h->batch_work) return fail(BBC_INVALID_ARG, "call bbc_batch_reserve first");
   if (split && !h->batch_split) return fail(BBC_INVALID_ARG, "reserve with BBC_PREC_OZAKI first");
   static const int deg[6] = {1, 2, 4, 8, 12, 18};
@@ -1320,7 +1391,6 @@ int expm_batched_impl(bbc_handle h, const void* const* dA, const void* const* dB
     sel.mode = 2;
     psel = &sel;
   }
-  cudaStream_t st = (cudaStream_t)stream;
   LaunchScope scope(h, BBC_KERNEL_BATCHED, st);
   const int ctas = (h->batch_grid > 0 && h->batch_grid <= h->batch_ctas) ? h->batch_grid : h->batch_ctas;
   const int scheme = flags & BBC_SCHEME_MASK;
@@ -1333,6 +1403,8 @@ int expm_batched_impl(bbc_handle h, const void* const* dA, const void* const* dB
   return BBC_OK;
 }
 }  // namespace
+
+extern "C" {
 
 int bbc_expm_batched(bbc_handle h, const void* const* dA, const int64_t* dNs, int64_t count, void* const* dOut,
                      int dtype, double tol, int flags, void* stream, bbc_info* dInfo) {

@@ -131,6 +131,21 @@ cudaError_t exact_diagonals(const double* A, int64_t N, int q, double* T, cudaSt
   return cudaGetLastError();
 }
 
+// A few words from device memory into host memory the device can write directly
+// (mapped pinned memory): the host reads a norm or a status word after a stream
+// synchronisation without a copy-engine transfer, which would queue behind any
+// large device-to-host copy in flight on another stream.
+__global__ void k_words_to_host(const uint32_t* __restrict__ src, uint32_t* dst, int words) {
+  if ((int)threadIdx.x < words) dst[threadIdx.x] = src[threadIdx.x];
+}
+
+cudaError_t copy_to_mapped(void* dst_dev, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0 || bytes % 4 != 0 || bytes > 128) return cudaErrorInvalidValue;
+  k_words_to_host<<<1, 32, 0, st>>>(static_cast<const uint32_t*>(src), static_cast<uint32_t*>(dst_dev),
+                                    (int)(bytes / 4));
+  return cudaGetLastError();
+}
+
 }  // namespace bbc
 
 // ---------------------------------------------------------------------------

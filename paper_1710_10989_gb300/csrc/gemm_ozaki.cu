@@ -586,8 +586,14 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       const int64_t row = (int64_t)w.mp * 2 * TILE + (int64_t)rank * TILE + row_in_tile;
       const int64_t col0 = (int64_t)w.nt * TILE + half * 64;
       if (upper && w.nt * TILE + TILE <= w.mp * 2 * TILE) {  // strictly below the diagonal: zeros
-        if (row < N)
-          for (int64_t col = col0; col < min(N, col0 + 64); ++col) zero_epilogue(e, N, row, col);
+        // the warp's 32 rows one after another, its lanes across the 64 columns: each
+        // store instruction writes whole row segments
+        for (int rl = 0; rl < 32; ++rl) {
+          const int64_t r = row - lane + rl;
+          if (r >= N) break;
+          for (int cc = lane; cc < 64; cc += 32)
+            if (col0 + cc < N) zero_epilogue(e, N, r, col0 + cc);
+        }
         continue;
       }
       // Each pass takes 8 columns: the warp's 32 threads (one row each) rebuild the

@@ -78,6 +78,10 @@ int64_t norm1_partial_len(int64_t N);
 cudaError_t norm1(const double* A, int64_t N, double* partial, double* dNorm, cudaStream_t st,
                   unsigned int* lower_nz = nullptr);
 
+// `bytes` (a multiple of 4, at most 128) from device memory `src` to `dst_dev`, the
+// device address of mapped pinned host memory, by a one-warp kernel on `st`.
+cudaError_t copy_to_mapped(void* dst_dev, const void* src, size_t bytes, cudaStream_t st);
+
 // Upper triangular A: overwrite the diagonal and first superdiagonal of T with
 // those of exp(2^-q A), known in closed form (Section 5, concluding remarks).
 cudaError_t exact_diagonals(const double* A, int64_t N, int q, double* T, cudaStream_t st);

@@ -246,3 +246,42 @@ def test_training_labels_relabelled_by_the_oracle(api):
     rate = disagree / len(sample)
     print(f"oracle re-label of {len(sample)} of {total} training-style matrices: disagreement rate {rate:.4f}")
     assert disagree <= max(1, len(sample) // 100), (disagree, len(sample))
+
+
+def test_single_matrix_call_with_certified_selection(api):
+    """bbc_expm with BBC_SELECT_LEARNED / BBC_SELECT_ALPHA (a batch of one through the
+    persistent kernel): the same (m, s), products and result as the batched call, and
+    the oracle's exp(A) at that (m, s); the alpha rule's (m, s) is the oracle's
+    certified choice."""
+    import torch
+    from oracle import oracle as O
+    from paper_1710_10989_gb300 import selector as SEL, workloads as W
+    h = api.Handle(0)
+    h.batch_reserve(512)
+    SEL.install(h)
+    for n, norm, seed in ((200, 3.0, 1), (64, 0.05, 2), (512, 40.0, 3)):
+        A = W.batch_matrix(seed, n, norm, seed=41)
+        dA = torch.from_numpy(A).cuda()
+        for flag in (api.SELECT_LEARNED, api.SELECT_ALPHA):
+            out = torch.empty_like(dA)
+            info = h.expm(dA, out, 0.0, flag)
+            ref = torch.empty_like(dA)
+            b = api.Batch([dA], [ref])
+            h.expm_batched(b, flags=flag)
+            torch.cuda.synchronize()
+            bi = b.infos()[0]
+            assert (info.m, info.s, info.products, info.selector) == (bi["m"], bi["s"], bi["products"],
+                                                                     bi["selector"])
+            assert torch.equal(out, ref)
+            want, _ = O.expm(A, m=info.m, s=info.s)
+            assert np.linalg.norm(out.cpu().numpy() - want) / np.linalg.norm(want) < 1e-12
+            if flag == api.SELECT_ALPHA:
+                assert (info.m, info.s) == O.select_certified(O.power_norms(A))
+    with pytest.raises(api.BBCError) as e:                  # beyond the reservation
+        big = torch.zeros((600, 600), dtype=torch.float64, device="cuda")
+        h.expm(big, torch.empty_like(big), 0.0, api.SELECT_ALPHA)
+    assert e.value.code == api.INVALID_ARG
+    with pytest.raises(api.BBCError) as e:                  # FP64 products only
+        h.expm(dA, torch.empty_like(dA), 0.0, api.SELECT_ALPHA | api.PREC_OZAKI)
+    assert e.value.code == api.UNSUPPORTED
+    h.close()
