@@ -305,19 +305,35 @@ int bbc_expm_apply_batched(bbc_handle h, const void* const* dA, const void* cons
 /* Autotuner of bbc_expm_batched (needs bbc_batch_reserve with BBC_PREC_OZAKI).
  * Times, on this GPU, calibration batches the library generates itself (entries
  * uniform on [-1, 1), 1-norm about 5, two matrices per resident CTA per size):
- *  1. for every size bucket ((N - 1) / 8 for N <= min(max_n, 256)) whether split
- *     products or FP64 products are faster, and
+ *  1. for every size bucket ((N - 1) / 8 for N <= min(max_n, 256)) the fastest of
+ *     split products (32 x 16 or 16 x 16 warp tasks) and FP64 products (64 x 64,
+ *     32 x 32 or 16 x 16 output tiles), and
  *  2. the persistent grid, one or two CTAs per SM, on a largest-first mix of all
  *     buckets (eight matrices per resident CTA) with the choices of 1.
  * Keeps the result in the handle for later split-precision batched calls and
- * returns it (split_mask: bit b set = bucket b uses split products; ctas: CTA
- * count), so that callers can cache it and restore it with bbc_batch_set_tuning.
+ * returns the product family and grid (split_mask: bit b set = bucket b uses split
+ * products; ctas: CTA count; the shapes through bbc_batch_get_shapes), so that
+ * callers can cache them and restore them with bbc_batch_set_tuning and
+ * bbc_batch_set_shapes.
  * Allocates and frees temporary device memory (about 1 GB for max_n = 256 on a
  * 152-SM GPU) and waits for the stream; takes seconds. */
 int bbc_batch_tune(bbc_handle h, int64_t max_n, double tol, void* stream, uint32_t* split_mask, int* ctas);
 
 /* Install a tuning (from bbc_batch_tune, possibly cached): ctas 0 = the reserved count. */
 int bbc_batch_set_tuning(bbc_handle h, uint32_t split_mask, int ctas);
+
+/* Product shapes of the batched kernel per size bucket b = (N - 1) / 8 (bit b of each
+ * mask), as bbc_batch_tune chose them alongside the split mask: for every bucket it
+ * times split products in 32 x 16 and 16 x 16 warp tasks and FP64 products in
+ * 64 x 64, 32 x 32 and 16 x 16 output tiles and keeps the fastest.
+ *  masks[0]  FP64 products in 16 x 16 output tiles
+ *  masks[1]  FP64 products in 32 x 32 output tiles (where masks[0] is clear)
+ *  masks[2]  split products in 16 x 16 warp tasks (default 32 x 16)
+ * All zero: the defaults (the largest tile that gives every CTA sharing a matrix a
+ * tile). Results are bit-identical whatever the shapes. host arrays of 3 words; set
+ * with NULL restores the defaults. */
+int bbc_batch_get_shapes(bbc_handle h, uint32_t* masks);
+int bbc_batch_set_shapes(bbc_handle h, const uint32_t* masks);
 
 /* How bbc_expm_batched would launch a batch of `count` matrices (host query, no
  * GPU work): *csize = CTAs sharing each matrix (1, or a thread-block cluster of

@@ -91,6 +91,8 @@ _SIGS = {
     "bbc_profile_flops": [_vp, _int, _dp],
     "bbc_batch_tune": [_vp, _i64, _dbl, _vp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int)],
     "bbc_batch_set_tuning": [_vp, ctypes.c_uint32, _int],
+    "bbc_batch_get_shapes": [_vp, ctypes.POINTER(ctypes.c_uint32)],
+    "bbc_batch_set_shapes": [_vp, ctypes.POINTER(ctypes.c_uint32)],
     "bbc_batch_launch_shape": [_vp, ctypes.c_int64, ctypes.POINTER(_int), ctypes.POINTER(_int)],
 }
 KERNEL_PRODUCT, KERNEL_NORM, KERNEL_LINCOMB, KERNEL_SPLIT, KERNEL_BATCHED, KERNEL_ALL = 0, 1, 2, 3, 4, -1
@@ -206,6 +208,19 @@ class Handle:
 
     def batch_set_tuning(self, split_mask: int, ctas: int) -> None:
         _check(_lib.bbc_batch_set_tuning(self._h, split_mask & 0xFFFFFFFF, ctas))
+
+    def batch_get_shapes(self) -> tuple[int, int, int]:
+        """(FP64 16 x 16 tile mask, FP64 32 x 32 tile mask, split 16 x 16 task mask) per size bucket."""
+        m = (ctypes.c_uint32 * 3)()
+        _check(_lib.bbc_batch_get_shapes(self._h, m))
+        return int(m[0]), int(m[1]), int(m[2])
+
+    def batch_set_shapes(self, masks=None) -> None:
+        if masks is None:
+            _check(_lib.bbc_batch_set_shapes(self._h, None))
+            return
+        m = (ctypes.c_uint32 * 3)(*[int(x) & 0xFFFFFFFF for x in masks])
+        _check(_lib.bbc_batch_set_shapes(self._h, m))
 
     def batch_launch_shape(self, count: int) -> tuple:
         """(CTAs per matrix, CTAs launched) of a batch of `count` matrices."""

@@ -44,6 +44,7 @@ struct bbc_handle_s {
   bool batch_split = false;       // reservation includes the split-precision scratch
   uint32_t batch_split_mask = 0xFFFFFFFFu;  // tuned: size buckets ((N-1)/8) that use split products
   int batch_grid = 0;                       // tuned persistent CTA count (0: the reserved count)
+  BatchShapes batch_shapes;                 // tuned product shapes per size bucket
   BatchClusters batch_cl;                   // cluster shapes for small batches
   double* cplx = nullptr;         // complex calls: two (2N)^2 real forms and the norm partials
   int64_t cplx_n = 0;
@@ -369,7 +370,7 @@ int launch_product(bbc_handle h, const double* P, const double* Q, int64_t N, do
     const int mode = split_mode(flags);
     {
       LaunchScope scope(h, BBC_KERNEL_SPLIT, stream);
-      err = ozaki_split(P, Q, N, k, h->ozaki, h->dflag, stream, mode);
+      err = ozaki_split(P, Q, N, k, h->ozaki, h->dflag, stream, mode, upper);
     }
     if (err != cudaSuccess) return cuda_fail(err, "split launch");
     LaunchScope scope(h, BBC_KERNEL_PRODUCT, stream);
@@ -1076,7 +1077,8 @@ struct DevBuf {
 
 // Best of `reps` event-timed launches (after one warm-up) of the batched kernel.
 int time_batch(bbc_handle h, const void* const* dA, void* const* dOut, const int64_t* dNs, int64_t count,
-               const double* theta, int ctas, uint32_t mask, cudaStream_t st, int reps, float* best_ms) {
+               const double* theta, int ctas, uint32_t mask, cudaStream_t st, int reps, float* best_ms,
+               const BatchShapes* shapes = nullptr) {
   cudaEvent_t a = nullptr, b = nullptr;
   BBC_CUDA(cudaEventCreate(&a));
   BBC_CUDA(cudaEventCreate(&b));
@@ -1086,7 +1088,7 @@ int time_batch(bbc_handle h, const void* const* dA, void* const* dOut, const int
     e = cudaEventRecord(a, st);
     if (e == cudaSuccess)
       e = batched_launch(dA, dOut, dNs, count, h->batch_nmax, BBC_DTYPE_F64, theta, h->batch_work, ctas, nullptr,
-                         st, nullptr, true, mask);
+                         st, nullptr, true, mask, nullptr, nullptr, 0, nullptr, shapes);
     if (e == cudaSuccess) e = cudaEventRecord(b, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.f;
@@ -1124,6 +1126,7 @@ int bbc_batch_tune(bbc_handle h, int64_t max_n, double tol, void* stream, uint32
   std::vector<void*> hp(2 * per);
   std::vector<int64_t> hn(per);
   uint32_t mask = 0;
+  BatchShapes shapes;
   for (int b = 0; b < nb; ++b) {
     const int64_t N = std::min<int64_t>(8 * (b + 1), nlim);
     double* in = static_cast<double*>(buf.p);
@@ -1138,14 +1141,27 @@ int bbc_batch_tune(bbc_handle h, int64_t max_n, double tol, void* stream, uint32
     BBC_CUDA(cudaMemcpyAsync(ns.p, hn.data(), hn.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     const void* const* dA = static_cast<const void* const*>(ptrs.p);
     void* const* dO = static_cast<void* const*>(ptrs.p) + per;
-    float t_split = 0.f, t_fp64 = 0.f;
-    if ((rc = time_batch(h, dA, dO, static_cast<const int64_t*>(ns.p), per, theta, h->batch_ctas, 1u << b, st, 3,
-                         &t_split)))
-      return rc;
-    if ((rc = time_batch(h, dA, dO, static_cast<const int64_t*>(ns.p), per, theta, h->batch_ctas, 0u, st, 3,
-                         &t_fp64)))
-      return rc;
-    if (t_split < t_fp64) mask |= 1u << b;
+    // five candidates: split products in 32 x 16 or 16 x 16 warp tasks, FP64 products in
+    // 64 x 64, 32 x 32 or 16 x 16 output tiles
+    struct Cand { bool split; BatchShapes sh; };
+    BatchShapes s16, t32, t16;
+    s16.split_task16 = 1u << b;
+    t32.f64_tile32 = 1u << b;
+    t16.f64_tile16 = 1u << b;
+    const Cand cands[5] = {{true, BatchShapes{}}, {true, s16}, {false, BatchShapes{}}, {false, t32}, {false, t16}};
+    float best_t = 1e30f;
+    int best_c = 0;
+    for (int c = 0; c < 5; ++c) {
+      float t = 0.f;
+      if ((rc = time_batch(h, dA, dO, static_cast<const int64_t*>(ns.p), per, theta, h->batch_ctas,
+                           cands[c].split ? (1u << b) : 0u, st, 3, &t, &cands[c].sh)))
+        return rc;
+      if (t < best_t) { best_t = t; best_c = c; }
+    }
+    if (cands[best_c].split) mask |= 1u << b;
+    shapes.split_task16 |= cands[best_c].sh.split_task16;
+    shapes.f64_tile32 |= cands[best_c].sh.f64_tile32;
+    shapes.f64_tile16 |= cands[best_c].sh.f64_tile16;
   }
   for (int b = nb; b < 32; ++b) mask |= 1u << b;  // buckets not tuned keep the default
   // 2. the persistent grid: one or two CTAs per SM, on a mix of every bucket large
@@ -1188,15 +1204,40 @@ int bbc_batch_tune(bbc_handle h, int64_t max_n, double tol, void* stream, uint32
     if (g < 1) continue;
     float t = 0.f;
     if ((rc = time_batch(h, static_cast<const void* const*>(mptrs.p), static_cast<void* const*>(mptrs.p) + mcount,
-                         static_cast<const int64_t*>(mns.p), mcount, theta, g, mask, st, 3, &t)))
+                         static_cast<const int64_t*>(mns.p), mcount, theta, g, mask, st, 3, &t, &shapes)))
       return rc;
     if (t < best) { best = t; best_grid = g; }
   }
   BBC_CUDA(cudaStreamSynchronize(st));
   h->batch_split_mask = mask;
   h->batch_grid = best_grid;
+  h->batch_shapes = shapes;
   if (split_mask) *split_mask = mask;
   if (ctas) *ctas = best_grid;
+  return BBC_OK;
+}
+
+int bbc_batch_get_shapes(bbc_handle h, uint32_t* masks) {
+  int rc = begin(h);
+  if (rc) return rc;
+  if (!masks) return fail(BBC_INVALID_ARG, "null masks");
+  std::lock_guard<std::mutex> lk(h->mu);
+  masks[0] = h->batch_shapes.f64_tile16;
+  masks[1] = h->batch_shapes.f64_tile32;
+  masks[2] = h->batch_shapes.split_task16;
+  return BBC_OK;
+}
+
+int bbc_batch_set_shapes(bbc_handle h, const uint32_t* masks) {
+  int rc = begin(h);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(h->mu);
+  h->batch_shapes = BatchShapes{};
+  if (masks) {
+    h->batch_shapes.f64_tile16 = masks[0];
+    h->batch_shapes.f64_tile32 = masks[1];
+    h->batch_shapes.split_task16 = masks[2];
+  }
   return BBC_OK;
 }
 
@@ -1398,7 +1439,7 @@ int batched_locked(bbc_handle h, const void* const* dA, const void* const* dB, c
   const double theta_pade[2] = {theta_cached(-10, u), theta_cached(-26, u)};
   const cudaError_t e = batched_launch(dA, dOut, dNs, count, h->batch_nmax, dtype, theta, h->batch_work,
                                        ctas, dInfo, st, psel, split, h->batch_split_mask, &h->batch_cl, dB,
-                                       pade, theta_pade);
+                                       pade, theta_pade, &h->batch_shapes);
   if (e != cudaSuccess) return cuda_fail(e, "batched launch");
   return BBC_OK;
 }

@@ -97,6 +97,7 @@ struct BatchArgs {
   double* norms_out;       // data mode: count x 4
   int prec;                // 0: products on the FP64 pipe; 1: 4-slice BF16 mma.sync products (N <= 256)
   uint32_t split_mask;     // prec 1: bit b set = matrices with (N - 1) / 8 == b use split products
+  BatchShapes shapes;      // per size bucket: FP64 output tile and split warp-task height (autotuned)
   uint32_t* ozwork;        // per-CTA slice scratch, OZB_WORDS words each (prec 1)
   int csize;               // CTAs per matrix: 1, or the size of the thread-block cluster sharing it
   int pade;                // 0: Taylor (the paper's scheme); 1: Pade r_10 or r_26 by cost; 2: r_26 only
@@ -239,13 +240,14 @@ __device__ void block_gemm_f64_t(const double* P, const double* Q, int N, double
   }
 }
 
-// The largest tile that still gives every CTA of the cluster a tile.
+// The largest tile that still gives every CTA of the cluster a tile, or a smaller one
+// when the autotuner found it faster for this size (tile_max = 32 or 16; 0: no limit).
 __device__ void block_gemm_f64(const double* P, const double* Q, int N, double alpha,
-                               const Epilogue& e, GemmSmem& sm, int part, int parts) {
+                               const Epilogue& e, GemmSmem& sm, int part, int parts, int tile_max) {
   const int t64 = (N + 63) / 64, t32 = (N + 31) / 32;
-  if (t64 * t64 >= parts)
+  if (t64 * t64 >= parts && tile_max != 32 && tile_max != 16)
     block_gemm_f64_t<64>(P, Q, N, alpha, e, sm, part, parts);
-  else if (t32 * t32 >= parts)
+  else if (t32 * t32 >= parts && tile_max != 16)
     block_gemm_f64_t<32>(P, Q, N, alpha, e, sm, part, parts);
   else
     block_gemm_f64_t<16>(P, Q, N, alpha, e, sm, part, parts);
@@ -374,33 +376,36 @@ __device__ __forceinline__ void ozb_mma(float (&c)[4], const uint32_t (&a)[4], u
 }
 
 // alpha * (P Q) with the fused epilogue, from the slices of block_split_oz.
-// Warp tasks of 32 x 16 outputs (two m16 x two n8 tiles), 10 slice pairs.
+// Warp tasks of (16 MT) x 16 outputs (MT m16 x two n8 tiles; MT = 2 or, for sizes
+// where the autotuner found it faster, 1), 10 slice pairs. Every output sums the
+// same slice products in the same order whatever MT.
+template <int MT>
 __device__ void block_gemm_oz(const uint32_t* Ps, const uint32_t* Qt, const double* P, const double* Q, int N, int Np,
                               double alpha, const Epilogue& e, const EpiMasks& em, const OzbSmem& o, int part,
                               int parts) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
   const int half = Np / 2;
   const size_t plane = (size_t)Np * half;
-  const int tn = Np / 16, tasks = (Np / 32) * tn;
+  const int tn = Np / 16, tasks = (Np / (16 * MT)) * tn;
   constexpr int WARPS = BATCH_THREADS / 32;
   for (int task = part * WARPS + warp; task < tasks; task += parts * WARPS) {
-    const int i0 = (task / tn) * 32, j0 = (task % tn) * 16;
-    float acc[OZB_K][2][2][4];
+    const int i0 = (task / tn) * (16 * MT), j0 = (task % tn) * 16;
+    float acc[OZB_K][MT][2][4];
 #pragma unroll
     for (int g = 0; g < OZB_K; ++g)
 #pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
+      for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
           for (int r = 0; r < 4; ++r) acc[g][mt][nt][r] = 0.f;
     for (int k0 = 0; k0 < Np; k0 += 16) {
       const int kw = (k0 >> 1) + tig;
-      uint32_t a[OZB_K][2][4], b[OZB_K][2][2];
+      uint32_t a[OZB_K][MT][4], b[OZB_K][2][2];
 #pragma unroll
       for (int p = 0; p < OZB_K; ++p)
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
+        for (int mt = 0; mt < MT; ++mt) {
           const uint32_t* base = Ps + p * plane + (size_t)(i0 + 16 * mt + gid) * half + kw;
           a[p][mt][0] = base[0];
           a[p][mt][1] = base[8 * half];
@@ -420,12 +425,12 @@ __device__ void block_gemm_oz(const uint32_t* Ps, const uint32_t* Qt, const doub
 #pragma unroll
         for (int q = 0; q + p < OZB_K; ++q)
 #pragma unroll
-          for (int mt = 0; mt < 2; ++mt)
+          for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) ozb_mma(acc[p + q][mt][nt], a[p][mt], b[q][nt][0], b[q][nt][1]);
     }
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
       for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
@@ -470,11 +475,17 @@ __device__ void block_product(const BatchArgs& a, const double* P, const double*
     uint32_t* Ps = a.ozwork + (size_t)blockIdx.x * OZB_WORDS;
     uint32_t* Qt = Ps + OZB_WORDS / 2;
     if (block_split_oz(P, Q, N, Np, Ps, Qt, oz)) {
-      block_gemm_oz(Ps, Qt, P, Q, N, Np, alpha, e, sm.em, oz, part, parts);
+      if ((a.shapes.split_task16 >> ((N - 1) >> 3)) & 1u)
+        block_gemm_oz<1>(Ps, Qt, P, Q, N, Np, alpha, e, sm.em, oz, part, parts);
+      else
+        block_gemm_oz<2>(Ps, Qt, P, Q, N, Np, alpha, e, sm.em, oz, part, parts);
       return;
     }
   }
-  block_gemm_f64(P, Q, N, alpha, e, sm, part, parts);
+  const int b = (N - 1) >> 3;
+  const int tile_max = (b < 32 && ((a.shapes.f64_tile16 >> b) & 1u)) ? 16
+                       : (b < 32 && ((a.shapes.f64_tile32 >> b) & 1u)) ? 32 : 0;
+  block_gemm_f64(P, Q, N, alpha, e, sm, part, parts, tile_max);
 }
 
 // Barrier over the CTAs sharing a matrix (the CTA itself when csize == 1). The
@@ -1190,7 +1201,7 @@ int batched_cluster_size(const BatchClusters* cl, int64_t count, int ctas, int* 
 cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t* Ns, int64_t count, int64_t nmax,
                            int dtype, const double* theta, void* work, int ctas, bbc_info* info, cudaStream_t st,
                            const BatchSelector* sel, bool split, uint32_t split_mask, const BatchClusters* cl,
-                           const void* const* B, int pade, const double* theta_pade) {
+                           const void* const* B, int pade, const double* theta_pade, const BatchShapes* shapes) {
   static const int deg[BATCH_PROGS] = {1, 2, 4, 8, 12, 18};
   static const int prod[BATCH_PROGS] = {0, 1, 2, 3, 4, 5};
   BatchArgs a = {};
@@ -1213,6 +1224,7 @@ cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t
   a.info = info;
   a.prec = split ? 1 : 0;
   a.split_mask = split_mask;
+  if (shapes) a.shapes = *shapes;
   a.ozwork = split ? reinterpret_cast<uint32_t*>(static_cast<char*>(work) + 256 +
                                                  (size_t)ctas * BATCH_SLOTS * nmax * nmax * sizeof(double))
                    : nullptr;

@@ -318,11 +318,13 @@ __device__ __forceinline__ void pair_tile(int t, int tiles_m, int tiles_n, int* 
 // The K steps one output tile needs: all of them, or for upper triangular P and
 // Q the steps meeting [first row, last column] (P_ik = 0 for k < i, Q_kj = 0 for
 // k > j); tiles strictly below the diagonal need none (their epilogue writes the
-// zeros). Chunks are the 1024-wide K blocks that meet that range.
+// zeros). Chunks are consecutive blocks of at most 1024 K (CHUNK_STEPS steps),
+// counted from the range's own first step, so a short range takes as few chunks
+// (and drains) as its length allows.
 struct TileWork {
   int mp, nt;          // pair row block, column block
   int ks_lo, ks_hi;    // K steps [ks_lo, ks_hi)
-  int c_lo, nch;       // first chunk, number of chunks
+  int nch;             // number of chunks
 };
 __device__ __forceinline__ TileWork tile_work(int t, const uint32_t* __restrict__ list, int tiles_m, int tiles_n,
                                               int nksteps, int upper, int ks) {
@@ -336,13 +338,7 @@ __device__ __forceinline__ TileWork tile_work(int t, const uint32_t* __restrict_
   }
   w.ks_lo = upper ? min(nksteps, w.mp * (2 * TILE / ks)) : 0;
   w.ks_hi = upper ? min(nksteps, (w.nt + 1) * (TILE / ks)) : nksteps;
-  if (w.ks_hi <= w.ks_lo) {
-    w.c_lo = 0;
-    w.nch = 0;
-  } else {
-    w.c_lo = w.ks_lo / CHUNK_STEPS;
-    w.nch = (w.ks_hi + CHUNK_STEPS - 1) / CHUNK_STEPS - w.c_lo;
-  }
+  w.nch = (w.ks_hi <= w.ks_lo) ? 0 : (w.ks_hi - w.ks_lo + CHUNK_STEPS - 1) / CHUNK_STEPS;
   return w;
 }
 
@@ -438,9 +434,9 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       const int nunits = (pairs_h + pairs_l) * w.nch;
       ItemCursor cur(nslices, w.nch, glo);
       for (int idx = 0; idx < nunits && ok; ++idx, cur.advance()) {
-        const int ca = w.c_lo + cur.c;
-        const int ks1 = min(w.ks_hi, (ca + 1) * CHUNK_STEPS);
-        for (int ks = max(w.ks_lo, ca * CHUNK_STEPS); ks < ks1; ++ks) {
+        const int kc = w.ks_lo + cur.c * CHUNK_STEPS;
+        const int ks1 = min(w.ks_hi, kc + CHUNK_STEPS);
+        for (int ks = kc; ks < ks1; ++ks) {
           if (!mbar_wait_warp(&sh->empty[s], ph ^ 1u, cta_err)) { ok = false; break; }
           if (leader_lane) {
             if (rank == 0) mbar_arrive_expect_tx(&sh->full[s], 2 * P_STAGE_BYTES);
@@ -492,8 +488,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             d_tmem = tmem + (uint32_t)(b * TILE);
             kind0 = 0;
           }
-          const int ca = w.c_lo + cur.c;
-          const int ks0 = max(w.ks_lo, ca * CHUNK_STEPS), ks1 = min(w.ks_hi, (ca + 1) * CHUNK_STEPS);
+          const int ks0 = w.ks_lo + cur.c * CHUNK_STEPS, ks1 = min(w.ks_hi, ks0 + CHUNK_STEPS);
           if (!mbar_wait_warp_cl(&sh->full[s], ph, cta_err)) { ok = false; break; }
           if (issuer) {
             const uint64_t da = dA0 + (uint64_t)(s * (P_A_BYTES >> 4)), db = dB0 + (uint64_t)(s * (P_B_BYTES >> 4));

@@ -103,8 +103,11 @@ size_t ozaki_workspace_bytes(int64_t N, int slices);
 // the rounding of the remainder: BF16 for BBC_PREC_SPLIT, TF32 for
 // BBC_PREC_SPLIT_TF32 and BBC_PREC_FP32) with every term product accumulated in FP32.
 enum SplitMode { SPLIT_EXACT = 0, SPLIT_LITERAL_BF16 = 1, SPLIT_LITERAL_TF32 = 2 };
+// upper: P and Q are upper triangular; only the plane regions a triangle product reads are
+// written (rows of P from their tile row's first K step, columns of Q to their tile
+// column's last), and the exponent scans skip the zero triangles.
 cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices, void* work,
-                        unsigned int* flag, cudaStream_t st, int mode = SPLIT_EXACT);
+                        unsigned int* flag, cudaStream_t st, int mode = SPLIT_EXACT, bool upper = false);
 cudaError_t ozaki_product(const double* P, const double* Q, int64_t N, double alpha, const Epilogue& e,
                           int slices, void* work, unsigned int* flag, cudaStream_t st, bool upper = false,
                           int mode = SPLIT_EXACT);
@@ -164,13 +167,21 @@ struct BatchClusters {
   int max_active[5] = {};   // resident clusters of 2^i CTAs (index 0 unused)
 };
 cudaError_t batched_cluster_probe(int device, BatchClusters* out);
+// Product shapes per size bucket b = (N - 1) / 8 (bit b of each mask), chosen by the
+// autotuner; all zero = the defaults. Results do not depend on them (every output
+// element sums the same terms in the same order).
+struct BatchShapes {
+  uint32_t f64_tile16 = 0;     // FP64 products in 16 x 16 output tiles
+  uint32_t f64_tile32 = 0;     // FP64 products in 32 x 32 output tiles (unless tile16)
+  uint32_t split_task16 = 0;   // split products in 16 x 16 warp tasks (default 32 x 16)
+};
 int batched_cluster_size(const BatchClusters* cl, int64_t count, int ctas, int* grid);
 cudaError_t batched_launch(const void* const* A, void* const* Out, const int64_t* Ns, int64_t count,
                            int64_t nmax, int dtype, const double* theta, void* work, int ctas,
                            bbc_info* info, cudaStream_t st, const BatchSelector* sel = nullptr,
                            bool split = false, uint32_t split_mask = 0xFFFFFFFFu,
                            const BatchClusters* cl = nullptr, const void* const* B = nullptr,
-                           int pade = 0, const double* theta_pade = nullptr);
+                           int pade = 0, const double* theta_pade = nullptr, const BatchShapes* shapes = nullptr);
 // count N x N binary64 calibration matrices (uniform entries, 1-norm about norm1).
 cudaError_t calibration_matrices(double* out, int64_t N, int64_t count, uint64_t seed, double norm1, cudaStream_t st);
 

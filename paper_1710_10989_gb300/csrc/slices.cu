@@ -122,8 +122,11 @@ __device__ __forceinline__ void terms(double x, int Emax, uint32_t (&out)[K]) {
 
 // P (N x N, row-major FP64) -> K slice planes [K][Rp][Kp] of BF16 digits (or
 // literal terms: BF16, or TF32 in 32-bit words) with row exponents. One warp per
-// row; padding rows/columns are written as zeros.
-template <int K, int MODE>
+// row; padding rows/columns are written as zeros. upper: P is upper triangular and
+// the product reads row i only from column 256 floor(i / 256) on (its tile row's
+// first K step), so the scan starts at the diagonal's warp-aligned column and the
+// planes are written from that column on.
+template <int K, int MODE, bool UPPER>
 __global__ void __launch_bounds__(256)
 k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, uint16_t* __restrict__ planes,
              int* __restrict__ erow, double* __restrict__ pdiag, unsigned int* __restrict__ status) {
@@ -136,7 +139,7 @@ k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, ui
   bool bad = false;
   if (row < N) {
     const double* pr = P + row * N;
-    int64_t j = lane;
+    int64_t j = (UPPER ? (row & ~(int64_t)31) : 0) + lane;
     for (; j + 96 < N; j += 128) {  // four independent loads in flight per lane
       const double a0 = __ldg(pr + j), a1 = __ldg(pr + j + 32), a2 = __ldg(pr + j + 64), a3 = __ldg(pr + j + 96);
       const int E0 = (j == row) ? 0 : exp_field(a0), E1 = (j + 32 == row) ? 0 : exp_field(a1);
@@ -167,7 +170,8 @@ k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, ui
   auto elem = [&](int64_t c) -> double {
     return (live && c < N && c != row) ? __ldg(P + row * N + c) : 0.0;
   };
-  for (int64_t j = 2 * lane; j < Kp; j += 128) {  // two pairs per lane per pass: four loads in flight
+  const int64_t k0 = UPPER ? row / 256 * 256 : 0;
+  for (int64_t j = k0 + 2 * lane; j < Kp; j += 128) {  // two pairs per lane per pass: four loads in flight
     const int64_t j2 = j + 64;
     const double x0 = elem(j), x1 = elem(j + 1);
     const double x2 = (j2 < Kp) ? elem(j2) : 0.0, x3 = (j2 < Kp) ? elem(j2 + 1) : 0.0;
@@ -193,13 +197,15 @@ k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, ui
   }
 }
 
-// Largest biased exponent per column of Q (fexp zeroed beforehand).
+// Largest biased exponent per column of Q (fexp zeroed beforehand). upper: Q is upper
+// triangular, so column j is scanned down to its diagonal only.
+template <bool UPPER>
 __global__ void __launch_bounds__(256)
 k_col_maxexp(const double* __restrict__ Q, int64_t N, int64_t rows_per, int* __restrict__ fexp) {
   const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (j >= N) return;
   const int64_t r0 = (int64_t)blockIdx.y * rows_per;
-  const int64_t r1 = min(N, r0 + rows_per);
+  const int64_t r1 = min(UPPER ? j + 1 : N, r0 + rows_per);
   int m = 0;
   for (int64_t i = r0; i < r1; ++i) {
     const int E = exp_field(__ldg(Q + i * N + j));
@@ -212,7 +218,10 @@ k_col_maxexp(const double* __restrict__ Q, int64_t N, int64_t rows_per, int* __r
 // Q) with column exponents fcol. 64 x 32 tiles (rows x columns of Q) transposed
 // through shared memory: each thread keeps eight loads in flight, and each warp
 // writes a plane row's 64 digits as one 128-byte line.
-template <int K, int MODE>
+// upper: Q is upper triangular and the product reads plane row j (column j of Q)
+// only below K = 128 (floor(j / 128) + 1), the end of its tile column's K range:
+// blocks wholly beyond it write nothing.
+template <int K, int MODE, bool UPPER>
 __global__ void __launch_bounds__(256)
 k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, const int* __restrict__ fexp,
              uint16_t* __restrict__ planes, int* __restrict__ fcol, double* __restrict__ qdiag,
@@ -231,6 +240,7 @@ k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, co
     qdiag[j] = (j < N && !bad) ? __ldg(Q + j * N + j) : 0.0;
     if (bad) atomicOr(status, STATUS_NONFINITE);
   }
+  if (UPPER && i0 >= (j0 / 128 + 1) * 128) return;  // block-uniform; no barrier has been reached
   const int Emax = max(Ej, 1);
   double x[8];
 #pragma unroll
@@ -266,21 +276,29 @@ k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, co
   }
 }
 
-template <int K, int MODE>
-cudaError_t split_both(const double* P, const double* Q, int64_t N, int64_t Rp, uint16_t* Ps, uint16_t* Qs,
-                       int* erow, int* fcol, int* fexp, double* pdiag, double* qdiag, unsigned int* status,
-                       cudaStream_t st) {
-  k_split_rows<K, MODE><<<(unsigned)((Rp + 7) / 8), 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
+template <int K, int MODE, bool UPPER>
+cudaError_t split_both_t(const double* P, const double* Q, int64_t N, int64_t Rp, uint16_t* Ps, uint16_t* Qs,
+                         int* erow, int* fcol, int* fexp, double* pdiag, double* qdiag, unsigned int* status,
+                         cudaStream_t st) {
+  k_split_rows<K, MODE, UPPER><<<(unsigned)((Rp + 7) / 8), 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
   cudaError_t err = cudaMemsetAsync(fexp, 0, (size_t)N * sizeof(int), st);
   if (err != cudaSuccess) return err;
   const int64_t colblocks = (N + 255) / 256;
   int64_t slabs = (304 + colblocks - 1) / colblocks;
   slabs = std::min<int64_t>(slabs, (N + 63) / 64);
   const int64_t rows_per = (N + slabs - 1) / slabs;
-  k_col_maxexp<<<dim3((unsigned)colblocks, (unsigned)slabs), 256, 0, st>>>(Q, N, rows_per, fexp);
-  k_split_cols<K, MODE><<<dim3((unsigned)(Rp / 64), (unsigned)(Rp / 32)), 256, 0, st>>>(Q, N, Rp, Rp, fexp, Qs, fcol,
-                                                                                   qdiag, status);
+  k_col_maxexp<UPPER><<<dim3((unsigned)colblocks, (unsigned)slabs), 256, 0, st>>>(Q, N, rows_per, fexp);
+  k_split_cols<K, MODE, UPPER><<<dim3((unsigned)(Rp / 64), (unsigned)(Rp / 32)), 256, 0, st>>>(
+      Q, N, Rp, Rp, fexp, Qs, fcol, qdiag, status);
   return cudaGetLastError();
+}
+
+template <int K, int MODE>
+cudaError_t split_both(const double* P, const double* Q, int64_t N, int64_t Rp, uint16_t* Ps, uint16_t* Qs,
+                       int* erow, int* fcol, int* fexp, double* pdiag, double* qdiag, unsigned int* status,
+                       cudaStream_t st, int upper) {
+  return upper ? split_both_t<K, MODE, true>(P, Q, N, Rp, Ps, Qs, erow, fcol, fexp, pdiag, qdiag, status, st)
+               : split_both_t<K, MODE, false>(P, Q, N, Rp, Ps, Qs, erow, fcol, fexp, pdiag, qdiag, status, st);
 }
 
 }  // namespace
@@ -297,15 +315,16 @@ size_t ozaki_workspace_bytes(int64_t N, int slices) {
 
 template <int MODE>
 cudaError_t split_k(const double* P, const double* Q, int64_t N, int slices, const OzLayout& L, unsigned int* flag,
-                    cudaStream_t st) {
+                    cudaStream_t st, int upper) {
 #define BBC_SPLIT_CASE(k) \
-  case k: return split_both<k, MODE>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+  case k:                  \
+    return split_both<k, MODE>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st, upper);
   if (MODE == 2) {  // TF32 terms: 2..4
     switch (slices) {
       BBC_SPLIT_CASE(2)
       BBC_SPLIT_CASE(3)
       default: return split_both<4, MODE>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag,
-                                          flag, st);
+                                          flag, st, upper);
     }
   }
   switch (slices) {
@@ -315,7 +334,8 @@ cudaError_t split_k(const double* P, const double* Q, int64_t N, int slices, con
     BBC_SPLIT_CASE(5)
     BBC_SPLIT_CASE(6)
     BBC_SPLIT_CASE(7)
-    default: return split_both<8, MODE>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st);
+    default:
+      return split_both<8, MODE>(P, Q, N, L.Rp, L.Ps, L.Qs, L.erow, L.fcol, L.fexp, L.pdiag, L.qdiag, flag, st, upper);
   }
 #undef BBC_SPLIT_CASE
 }
@@ -323,13 +343,14 @@ cudaError_t split_k(const double* P, const double* Q, int64_t N, int slices, con
 // mode: 0 exact BF16 digits, 1 literal BF16 terms, 2 literal TF32 terms (whose planes
 // take two BF16 planes' room each: the layout is that of 2 x slices BF16 planes).
 cudaError_t ozaki_split(const double* P, const double* Q, int64_t N, int slices, void* work, unsigned int* flag,
-                        cudaStream_t st, int mode) {
+                        cudaStream_t st, int mode, bool upper) {
   const int kmax = (mode == 2) ? 4 : 8;
   if (!ozaki_supported(N) || slices < 2 || slices > kmax || !work || !flag || mode < 0 || mode > 2)
     return cudaErrorInvalidValue;
   const OzLayout L = layout(work, N, mode == 2 ? 2 * slices : slices);
-  if (mode == 2) return split_k<2>(P, Q, N, slices, L, flag, st);
-  return mode == 1 ? split_k<1>(P, Q, N, slices, L, flag, st) : split_k<0>(P, Q, N, slices, L, flag, st);
+  const int up = upper ? 1 : 0;
+  if (mode == 2) return split_k<2>(P, Q, N, slices, L, flag, st, up);
+  return mode == 1 ? split_k<1>(P, Q, N, slices, L, flag, st, up) : split_k<0>(P, Q, N, slices, L, flag, st, up);
 }
 
 }  // namespace bbc

@@ -1,6 +1,7 @@
 """Driver of the batched path's autotuner (bbc_batch_tune): runs the library's
-timing loop once per GPU model and reservation, caches the choice in a JSON file
-and restores it on later runs.
+timing loop once per GPU model and reservation, caches the choice (product family
+and product shapes per size bucket, persistent grid) in a JSON file and restores
+it on later runs.
 
     from paper_1710_10989_gb300 import api, tuner
     h = api.Handle(0)
@@ -46,14 +47,16 @@ def save(path: str, data: dict) -> None:
 def tuned(h, max_n: int, tol: float = 0.0, path: str = DEFAULT_CACHE, force: bool = False,
           gpu: str | None = None) -> tuple[int, int]:
     """(split_mask, ctas) for this handle's GPU: from the cache, else measured by
-    bbc_batch_tune and cached. Installs the choice in the handle either way."""
+    bbc_batch_tune and cached. Installs the choice, shapes included, in the handle
+    either way (a cache entry without shapes restores the default shapes)."""
     key = cache_key(gpu if gpu is not None else _gpu_key(h.device), max_n, tol)
     data = load(path)
     hit = data.get(key)
     if hit and not force:
         h.batch_set_tuning(int(hit["split_mask"]), int(hit["ctas"]))
+        h.batch_set_shapes(hit.get("shapes"))
         return int(hit["split_mask"]), int(hit["ctas"])
     mask, ctas = h.batch_tune(max_n, tol)
-    data[key] = {"split_mask": mask, "ctas": ctas}
+    data[key] = {"split_mask": mask, "ctas": ctas, "shapes": list(h.batch_get_shapes())}
     save(path, data)
     return mask, ctas

@@ -171,6 +171,9 @@ def test_autotuner_choice_keeps_parity(api):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert ctas in (sms, 2 * sms)
     assert mask >> 8 == (0xFFFFFFFF >> 8)          # buckets above max_n keep the default
+    t16, t32, s16 = h.batch_get_shapes()
+    assert (t16 | t32 | s16) >> 8 == 0             # shapes chosen only for the tuned buckets
+    assert t16 & t32 == 0 and (t16 | t32) & mask == 0 and s16 & ~mask == 0  # one choice per bucket
     mats = [W.gaussian(n, 300 + n, 0.5 + n / 16) for n in (64, 8, 33, 17, 50, 64, 1, 40)]
     ins = [torch.from_numpy(A).cuda() for A in mats]
     outs = [torch.empty_like(x) for x in ins]
@@ -220,4 +223,34 @@ def test_batch_single_precision_thresholds(api, prec):
         worst = max(worst, rel_fro(o.cpu().numpy().astype(np.float64), want))
     assert worst < 1e-6, worst
     assert fewer >= 10        # the single-precision thresholds save products on many matrices
+    hh.close()
+
+
+def test_product_shapes_leave_results_bit_identical(api):
+    """The autotuner's product shapes (FP64 output tiles of 64, 32 or 16; split warp
+    tasks of 32 x 16 or 16 x 16) change only how the work is cut: every output sums
+    the same terms in the same order, so results are bit-identical, and they match
+    the oracle (1e-12 with FP64 products, 1e-6 with split products)."""
+    import torch
+    hh = api.Handle(0)
+    hh.batch_reserve(256, api.PREC_OZAKI)
+    sizes = [8, 13, 24, 33, 64, 100, 129, 200, 256]
+    mats = [W.gaussian(n, 900 + n, 0.3 + n / 40) for n in sizes]
+    ins = [torch.from_numpy(A).cuda() for A in mats]
+    for flags, tol in ((api.PREC_FP64, 1e-12), (api.PREC_OZAKI, 1e-6)):
+        results = []
+        for shapes in (None, (0xFFFFFFFF, 0, 0xFFFFFFFF), (0, 0xFFFFFFFF, 0), (0x0000FFFF, 0xFFFF0000, 0x0F0F0F0F)):
+            hh.batch_set_shapes(shapes)
+            outs = [torch.empty_like(x) for x in ins]
+            hh.expm_batched(api.Batch(ins, outs), flags=flags)
+            torch.cuda.synchronize()
+            results.append(outs)
+        for outs in results[1:]:
+            assert all(torch.equal(a, b) for a, b in zip(results[0], outs)), flags
+        for A, o in zip(mats, results[0]):
+            want, _ = O.expm(A, "new")
+            assert rel_fro(o.cpu().numpy(), want) < tol, (A.shape, flags)
+    assert hh.batch_get_shapes() == (0x0000FFFF, 0xFFFF0000, 0x0F0F0F0F)
+    hh.batch_set_shapes(None)
+    assert hh.batch_get_shapes() == (0, 0, 0)
     hh.close()

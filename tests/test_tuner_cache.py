@@ -7,17 +7,25 @@ from paper_1710_10989_gb300 import tuner
 class FakeHandle:
     device = 0
 
-    def __init__(self, result=(0xF0F0, 152)):
+    def __init__(self, result=(0xF0F0, 152), shapes=(0x3, 0xC, 0x1)):
         self.result = result
+        self.shapes = shapes
         self.tuned = 0
         self.installed = None
+        self.installed_shapes = "unset"
 
     def batch_tune(self, max_n, tol):
         self.tuned += 1
         return self.result
 
+    def batch_get_shapes(self):
+        return self.shapes
+
     def batch_set_tuning(self, mask, ctas):
         self.installed = (mask, ctas)
+
+    def batch_set_shapes(self, masks):
+        self.installed_shapes = masks
 
 
 def test_measure_then_restore(tmp_path):
@@ -28,6 +36,7 @@ def test_measure_then_restore(tmp_path):
     h2 = FakeHandle(result=(1, 1))
     assert tuner.tuned(h2, 256, path=path, gpu="G") == (0xF0F0, 152)
     assert h2.tuned == 0 and h2.installed == (0xF0F0, 152)
+    assert list(h2.installed_shapes) == [0x3, 0xC, 0x1]   # the tuned product shapes come back too
     assert tuner.tuned(h2, 256, path=path, gpu="G", force=True) == (1, 1)
     assert h2.tuned == 1
 
@@ -49,3 +58,11 @@ def test_damaged_cache_is_ignored(tmp_path):
     h = FakeHandle()
     assert tuner.tuned(h, 64, path=str(path), gpu="G") == (0xF0F0, 152)
     assert h.tuned == 1
+
+
+def test_entry_without_shapes_restores_default_shapes(tmp_path):
+    path = str(tmp_path / "t.json")
+    tuner.save(path, {tuner.cache_key("G", 256, 0.0): {"split_mask": 5, "ctas": 7}})
+    h = FakeHandle()
+    assert tuner.tuned(h, 256, path=path, gpu="G") == (5, 7)
+    assert h.installed_shapes is None
