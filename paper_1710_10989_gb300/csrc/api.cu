@@ -408,6 +408,7 @@ int run_step(bbc_handle h, const StepS& st, int64_t N, const double* A, double* 
       e.o[o].c[t] = q.t[t].c;
     }
   }
+  e.ny = ny;
   if (st.P < 0) {
     LaunchScope scope(h, BBC_KERNEL_LINCOMB, stream);
     const cudaError_t err = lincomb(N, e, stream);

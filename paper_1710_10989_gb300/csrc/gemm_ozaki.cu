@@ -369,7 +369,7 @@ struct ItemCursor {
   }
 };
 
-template <bool TF32>
+template <bool TF32, bool TERMS>
 __global__ void __launch_bounds__(P_THREADS, 1)
 k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const int* __restrict__ erow, const int* __restrict__ fcol, const double* __restrict__ P,
@@ -642,7 +642,7 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             double d = fma(pii, __ldg(Q + r * N + col), stage[rl * 9 + tc]);
             d = fma(__ldg(P + r * N + col), qjj, d);
             if (r == col) d = fma(-pii, qjj, d);
-            apply_epilogue(e, N, r, col, alpha * d);
+            apply_epilogue_t<TERMS>(e, N, r, col, alpha * d);
           }
         }
         __syncwarp();
@@ -700,16 +700,20 @@ bool make_map(CUtensorMap* m, void* base, int64_t Rp, int64_t Kp, int k, int box
 
 namespace {
 // Clusters of two k_ozaki_pair CTAs that fit on the device at once (cached per device;
-// both operand kinds use the same resources).
+// every operand kind and epilogue form uses the same resources).
 int pair_clusters() {
   static int cached[64] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   if (cached[dev] > 0) return cached[dev];
-  if (cudaFuncSetAttribute(k_ozaki_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PAIR_SMEM_BYTES) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_ozaki_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PAIR_SMEM_BYTES) !=
-          cudaSuccess)
+  if (cudaFuncSetAttribute(k_ozaki_pair<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)PAIR_SMEM_BYTES) != cudaSuccess ||
+      cudaFuncSetAttribute(k_ozaki_pair<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)PAIR_SMEM_BYTES) != cudaSuccess ||
+      cudaFuncSetAttribute(k_ozaki_pair<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)PAIR_SMEM_BYTES) != cudaSuccess ||
+      cudaFuncSetAttribute(k_ozaki_pair<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)PAIR_SMEM_BYTES) != cudaSuccess)
     return 0;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -723,7 +727,7 @@ int pair_clusters() {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_ozaki_pair<false>, &cfg) != cudaSuccess || n <= 0) {
+  if (cudaOccupancyMaxActiveClusters(&n, k_ozaki_pair<false, false>, &cfg) != cudaSuccess || n <= 0) {
     // clusters are independent: any count is correct, the SM count / 2 is the natural one
     cudaGetLastError();
     int sms = 0;
@@ -803,7 +807,8 @@ cudaError_t launch_pair(const OzLayout& L, const double* P, const double* Q, int
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_ozaki_pair<TF32>, ta, tb, (const int*)L.erow, (const int*)L.fcol, P, Q,
+  auto kern = (e.ny > 0) ? k_ozaki_pair<TF32, true> : k_ozaki_pair<TF32, false>;
+  return cudaLaunchKernelEx(&cfg, kern, ta, tb, (const int*)L.erow, (const int*)L.fcol, P, Q,
                             (const double*)L.pdiag, (const double*)L.qdiag, N, alpha, slices, (int)(L.Rp / KS),
                             tiles_m, tiles_n, e, flag, list, upper ? 1 : 0, literal ? 1 : 0);
 }

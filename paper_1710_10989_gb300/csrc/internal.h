@@ -30,27 +30,59 @@ struct EpiOut {
 
 struct Epilogue {
   const double* Y[MAX_Y];  // matrices read element-wise by the epilogue
+  int ny;                  // how many of Y are used (Y[0..ny-1])
   int nout;
   EpiOut o[MAX_OUT];
   unsigned int* flag;      // if non-null: set to 1 when any output is not finite
 };
 
 // Element (row, col) of every output of the epilogue, given v = alpha * (P Q)_rc.
-__device__ __forceinline__ void apply_epilogue(const Epilogue& e, int64_t N, int64_t row,
-                                               int64_t col, double v) {
+// TERMS = false: the outputs have no matrix terms (e.ny == 0: a squaring, a plain
+// product). TERMS = true: the element of every matrix the outputs read is loaded
+// once, all loads issued together, before any output is formed (a step such as
+// T18's X6 = X3 X3, whose five outputs B1..B5 read X, X2, X3 three terms each, then
+// waits for three loads in flight instead of fifteen one after another); an output
+// written to one of those matrices is seen by the outputs after it.
+template <bool TERMS>
+__device__ __forceinline__ void apply_epilogue_t(const Epilogue& e, int64_t N, int64_t row, int64_t col, double v) {
   const int64_t idx = row * N + col;
+  double y[MAX_Y];
+  if (TERMS) {
+#pragma unroll
+    for (int k = 0; k < MAX_Y; ++k) y[k] = (k < e.ny) ? __ldg(e.Y[k] + idx) : 0.0;
+  }
   bool bad = false;
 #pragma unroll 1
   for (int o = 0; o < e.nout; ++o) {
     const EpiOut& q = e.o[o];
     double r = q.cv * v;
     if (row == col) r += q.cI;
+    if (TERMS) {
 #pragma unroll 1
-    for (int t = 0; t < q.nt; ++t) r = fma(q.c[t], __ldg(e.Y[q.slot[t]] + idx), r);
+      for (int t = 0; t < q.nt; ++t) {
+        const int sl = q.slot[t];
+        double yv = y[0];
+#pragma unroll
+        for (int k = 1; k < MAX_Y; ++k) yv = (sl == k) ? y[k] : yv;
+        r = fma(q.c[t], yv, r);
+      }
+    }
     q.out[idx] = r;
     bad |= !isfinite(r);
+    if (TERMS) {
+#pragma unroll
+      for (int k = 0; k < MAX_Y; ++k)
+        if (k < e.ny && e.Y[k] == q.out) y[k] = r;
+    }
   }
   if (bad && e.flag) atomicOr(e.flag, 1u);
+}
+
+// Either form, chosen per element at run time (kernels where the choice is not a
+// template parameter).
+__device__ __forceinline__ void apply_epilogue(const Epilogue& e, int64_t N, int64_t row, int64_t col, double v) {
+  if (e.ny == 0) apply_epilogue_t<false>(e, N, row, col, v);
+  else apply_epilogue_t<true>(e, N, row, col, v);
 }
 
 // Element (row, col) of every output when it is known to be zero: below the
