@@ -131,21 +131,29 @@ k_panel_lu(double* __restrict__ M, int64_t N, int64_t j0, int nb, int per, int* 
       st_remote_s32(remote(&cand_i[rank], 0), red_i[0]);
     }
     cluster_barrier();
-    // 2. the cluster's pivot, the same in every CTA; the pivot row from its owner
-    if (tid == 0) {
+    // 2. the cluster's pivot, the same in every CTA (one lane per candidate reads it
+    //    from CTA 0, all reads in flight together, then a shuffle reduction); the
+    //    pivot row from its owner
+    if (warp == 0) {
       double gv = -1.0;
       int gi = R;
-      for (uint32_t q = 0; q < csize; ++q) {
-        const double v = ld_remote_f64(remote(&cand_v[q], 0));
-        const int i = ld_remote_s32(remote(&cand_i[q], 0));
-        if (better(v, i, gv, gi)) { gv = v; gi = i; }
+      if ((uint32_t)lane < csize) {
+        gv = ld_remote_f64(remote(&cand_v[lane], 0));
+        gi = ld_remote_s32(remote(&cand_i[lane], 0));
       }
-      if (!(gv > 0.0) || gi >= R) {  // no usable pivot: keep the row, report, carry on
-        singular = true;
-        gi = c;
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, gv, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, gi, off);
+        if (better(ov, oi, gv, gi)) { gv = ov; gi = oi; }
       }
-      s_p = gi;
-      if (rank == 0) piv[j0 + c] = (int)(j0 + gi);
+      if (lane == 0) {
+        if (!(gv > 0.0) || gi >= R) {  // no usable pivot: keep the row, report, carry on
+          singular = true;
+          gi = c;
+        }
+        s_p = gi;
+        if (rank == 0) piv[j0 + c] = (int)(j0 + gi);
+      }
     }
     __syncthreads();
     const int p = s_p;
@@ -166,8 +174,10 @@ k_panel_lu(double* __restrict__ M, int64_t N, int64_t j0, int nb, int per, int* 
     for (int li = warp; li < nloc; li += PANEL_THREADS / 32) {
       const int i = r0 + li;
       if (i <= c) continue;
-      const double l = rows[li * NB + c] / d;
-      __syncwarp();
+      // one lane divides (FP64 division is costly on this GPU), the warp shares the quotient
+      double l = 0.0;
+      if (lane == 0) l = rows[li * NB + c] / d;
+      l = __shfl_sync(0xffffffffu, l, 0);
       if (lane > c && lane < nb) rows[li * NB + lane] = fma(-l, prow[lane], rows[li * NB + lane]);
       if (lane == c) rows[li * NB + c] = l;
     }

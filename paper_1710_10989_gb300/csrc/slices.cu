@@ -197,6 +197,69 @@ k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, ui
   }
 }
 
+// As k_split_rows, for large rows (2048 < Kp <= 512 PPT): one block of 256 threads per
+// row holds the whole row in registers (thread t owns the column pairs 2t + 512 i), so
+// the row is read from memory once, not once for the exponent and once for the digits.
+template <int K, int MODE, bool UPPER, int PPT>
+__global__ void __launch_bounds__(256)
+k_split_rows_reg(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, uint16_t* __restrict__ planes,
+                 int* __restrict__ erow, double* __restrict__ pdiag, unsigned int* __restrict__ status) {
+  __shared__ int s_emax[8], s_bad[8];
+  const int64_t row = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t k0 = UPPER ? row / 256 * 256 : 0;   // first column a triangle product reads
+  const bool real = row < N;
+  double x[2 * PPT];
+  int Emax = 0;
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int64_t j = 2 * (int64_t)tid + 512 * (int64_t)i;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t c = j + h;
+      const double v = (real && c < N && c >= k0) ? __ldg(P + row * N + c) : 0.0;
+      const int E = exp_field(v);
+      bad |= (E == 0x7FF);                       // the diagonal too: it must be finite
+      if (c != row) Emax = max(Emax, E);
+      x[2 * i + h] = (c != row) ? v : 0.0;       // the diagonal is deflated
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) Emax = max(Emax, __shfl_xor_sync(0xffffffffu, Emax, off));
+  const bool wbad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) { s_emax[warp] = Emax; s_bad[warp] = wbad ? 1 : 0; }
+  __syncthreads();
+  Emax = s_emax[0];
+  bad = s_bad[0] != 0;
+#pragma unroll
+  for (int w = 1; w < 8; ++w) { Emax = max(Emax, s_emax[w]); bad |= s_bad[w] != 0; }
+  if (tid == 0) {
+    if (bad) atomicOr(status, STATUS_NONFINITE);
+    erow[row] = (real && !bad) ? Emax - 1021 : 0;
+    pdiag[row] = (real && !bad) ? __ldg(P + row * N + row) : 0.0;
+  }
+  Emax = max(Emax, 1);
+  const size_t plane = (size_t)Rp * Kp;
+  uint32_t* out = reinterpret_cast<uint32_t*>(planes);
+  uint2* out2 = reinterpret_cast<uint2*>(planes);
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int64_t j = 2 * (int64_t)tid + 512 * (int64_t)i;
+    if (j >= Kp || j + 2 <= k0) continue;        // k0 is even: pairs never straddle it
+    const double x0 = bad ? 0.0 : x[2 * i], x1 = bad ? 0.0 : x[2 * i + 1];
+    uint32_t d0[K], d1[K];
+    terms<K, MODE>(x0, Emax, d0);
+    terms<K, MODE>(x1, Emax, d1);
+    const size_t idx = ((size_t)row * Kp + j) >> 1;
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+      if (MODE == 2) out2[p * (plane >> 1) + idx] = make_uint2(d0[p], d1[p]);
+      else out[p * (plane >> 1) + idx] = d0[p] | (d1[p] << 16);
+    }
+  }
+}
+
 // Largest biased exponent per column of Q (fexp zeroed beforehand). upper: Q is upper
 // triangular, so column j is scanned down to its diagonal only.
 template <bool UPPER>
@@ -280,7 +343,12 @@ template <int K, int MODE, bool UPPER>
 cudaError_t split_both_t(const double* P, const double* Q, int64_t N, int64_t Rp, uint16_t* Ps, uint16_t* Qs,
                          int* erow, int* fcol, int* fexp, double* pdiag, double* qdiag, unsigned int* status,
                          cudaStream_t st) {
-  k_split_rows<K, MODE, UPPER><<<(unsigned)((Rp + 7) / 8), 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
+  if (Rp > 2048 && Rp <= 4096)
+    k_split_rows_reg<K, MODE, UPPER, 8><<<(unsigned)Rp, 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
+  else if (Rp > 4096 && Rp <= 8192)
+    k_split_rows_reg<K, MODE, UPPER, 16><<<(unsigned)Rp, 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
+  else
+    k_split_rows<K, MODE, UPPER><<<(unsigned)((Rp + 7) / 8), 256, 0, st>>>(P, N, Rp, Rp, Ps, erow, pdiag, status);
   cudaError_t err = cudaMemsetAsync(fexp, 0, (size_t)N * sizeof(int), st);
   if (err != cudaSuccess) return err;
   const int64_t colblocks = (N + 255) / 256;
