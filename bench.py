@@ -37,24 +37,26 @@ from paper_1710_10989_gb300 import workloads as W  # noqa: E402
 
 PI = {1: 0, 2: 1, 4: 2, 8: 3, 12: 4, 18: 5}
 # DRAM traffic per launch of the dominant kernels from one ncu capture each (profiles/),
-# keyed to the hash of the file that holds the captured kernel,
-# valid only while the kernel source is the one that was captured.
+# keyed to the hash of the sources the captured kernel is compiled from (its .cu file
+# and the headers with inline device code), valid only while those are unchanged.
 NCU_TRAFFIC = {
-    "gemm_ozaki.cu": ("9deedd1543a711f569febcbb7ec2c1845b882762441f545aa0ea97bb08f39fa0", 4096, ((3.986145e9 + 0.177863e9) + (1.467322e9 + 0.107599e9)) / 2),
-    "gemm_f64.cu": ("efd76a329f05cdcafd0c8c0bfac41f943e449d0a73091b0eec8b9a914f25b8ee", 4096, 3.732330e9 + 0.134116e9),
-    "batched.cu": ("3978168039471747a74a385b0ff666767ff59106c94f0498518e572f92e0c545", 512, 4.986284e9 + 1.868790e9),
+    "k_ozaki_pair": (("gemm_ozaki.cu", "internal.h", "slices.h"), "c4bb01c280e74a9199625509dc5f7316edd884d04563e98edf13541854752549", 4096,
+                     ((5.013706e9 + 0.181348e9) + (1.467799e9 + 0.105501e9)) / 2),
 }
 
 
-def ncu_traffic(source: str, n: int):
+def ncu_traffic(kernel: str, n: int):
     import hashlib
-    sha, n_cap, traffic = NCU_TRAFFIC[source]
-    path = os.path.join(ROOT, "paper_1710_10989_gb300", "csrc", source)
+    if kernel not in NCU_TRAFFIC:
+        return None
+    sources, sha, n_cap, traffic = NCU_TRAFFIC[kernel]
+    h = hashlib.sha256()
     try:
-        cur = hashlib.sha256(open(path, "rb").read()).hexdigest()
+        for src in sources:
+            h.update(open(os.path.join(ROOT, "paper_1710_10989_gb300", "csrc", src), "rb").read())
     except OSError:
         return None
-    return traffic if (cur == sha and n == n_cap) else None
+    return traffic if (h.hexdigest() == sha and n == n_cap) else None
 
 
 # FP64 pipe: the GB300's nominal 1.25 TFLOP/s FP64 is 2 DFMA per clock per SM:
@@ -413,7 +415,7 @@ def run_dense(args, torch, dist, api, rank, world, local):
     logical = flops_per_product / (avg_ms / 1e3) / 1e12
     if args.precision == "fp64":
         roof = {"bound": "alu", "achieved": logical, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": logical / FP64_PEAK_TFLOPS, "traffic": ncu_traffic("gemm_f64.cu", n),
+                "frac": logical / FP64_PEAK_TFLOPS, "traffic": ncu_traffic("k_gemm_f64", n),
                 "kernel": "k_gemm_f64<64,64>",
                 "peak_source": "FP64 pipe, 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
                 "flops_per_launch": flops_per_product, "avg_launch_ms": avg_ms, "launches": prod_launches}
@@ -423,7 +425,7 @@ def run_dense(args, torch, dist, api, rank, world, local):
         peak = pk.get("bf16_tflops", 1899.1)
         roof = {"bound": "tensor", "achieved": executed, "peak": peak, "unit": "TFLOP/s",
                 "frac": executed / peak,
-                "traffic": ncu_traffic("gemm_ozaki.cu", n) if args.slices == 6 else None,
+                "traffic": ncu_traffic("k_ozaki_pair", n) if args.slices == 6 else None,
                 "traffic_note": "mean of ncu captures of one dense and one triangle product at 6 slices "
                                 "(the workload's launch mix is half and half; profiles/k_ozaki_pair_dense4096.md)",
                 "kernel": f"k_ozaki_pair ({args.slices} BF16 slices: {pairs} slice products per FP64 product)",

@@ -45,14 +45,23 @@ def test_sized_descriptions_format(bench, workload):
 
 
 def test_traffic_record_follows_the_source(bench, monkeypatch):
-    src = "gemm_f64.cu"
-    path = os.path.join(ROOT, "paper_1710_10989_gb300", "csrc", src)
-    cur = hashlib.sha256(open(path, "rb").read()).hexdigest()
-    monkeypatch.setitem(bench.NCU_TRAFFIC, src, (cur, 4096, 1.0e9))
-    assert bench.ncu_traffic(src, 4096) == 1.0e9
-    assert bench.ncu_traffic(src, 2048) is None          # another size: no record
-    monkeypatch.setitem(bench.NCU_TRAFFIC, src, ("0" * 64, 4096, 1.0e9))
-    assert bench.ncu_traffic(src, 4096) is None          # source changed since the capture
+    import hashlib
+    srcs = ("gemm_f64.cu", "internal.h")
+    h = hashlib.sha256()
+    for src in srcs:
+        h.update(open(os.path.join(ROOT, "paper_1710_10989_gb300", "csrc", src), "rb").read())
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "k_gemm_f64", (srcs, h.hexdigest(), 4096, 1.0e9))
+    assert bench.ncu_traffic("k_gemm_f64", 4096) == 1.0e9
+    assert bench.ncu_traffic("k_gemm_f64", 2048) is None          # another size: no record
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "k_gemm_f64", (srcs, "0" * 64, 4096, 1.0e9))
+    assert bench.ncu_traffic("k_gemm_f64", 4096) is None          # a source changed since the capture
+    assert bench.ncu_traffic("no_such_kernel", 4096) is None
+
+
+def test_pair_kernel_traffic_record_is_current(bench):
+    """The split product's DRAM traffic in the bench line was captured from the
+    sources as they are now (a change to the kernel or its headers drops it)."""
+    assert bench.ncu_traffic("k_ozaki_pair", 4096) is not None
 
 
 def test_reference_arm_runs_the_oracle_alone_on_the_same_config(bench, monkeypatch):
