@@ -343,29 +343,41 @@ __device__ __forceinline__ TileWork tile_work(int t, const uint32_t* __restrict_
 }
 
 // Work items of one output tile, in the order all three roles walk them: the low
-// groups first (g = k-1 down to G_EXACT: the Horner order), then the high groups
-// (g = 0 up); inside a group the slice pairs p = 0..g (q = g - p), inside a pair the
-// 1024-wide K chunks c. Advancing needs no division (the MMA issuer's time per item
-// matters: it must keep a new MMA ready every ~65 cycles).
+// groups first (g = k-1 down to G_EXACT: the Horner order; inside a group the slice
+// pairs p = 0..g (q = g - p), inside a pair the K chunks c), then the high groups
+// chunk-major: for each K chunk c every group g = 0..gh-1 and its pairs p = 0..g,
+// so that the slice tiles of a chunk, each used by several pairs, are read again
+// soon after the first read (while L2 still holds them); every high item is drained
+// on its own, so their order does not change any sum. Advancing needs no division
+// (the MMA issuer's time per item matters: it must keep a new MMA ready every ~65
+// cycles).
 struct ItemCursor {
   int g, p, c;
   bool low;
-  int nch, glo;  // glo: lowest low group (G_EXACT; 0 for the literal split, which has no exact groups)
+  int nch, glo, gh;  // glo: lowest low group (G_EXACT; 0 for the literal split, which has no exact
+                     // groups); gh: number of high groups
   __device__ ItemCursor(int k, int nch_, int glo_) : p(0), c(0), nch(nch_), glo(glo_) {
+    gh = min(k, glo_);
     low = k > glo;
     g = low ? k - 1 : 0;
   }
   __device__ void advance() {
-    if (++c < nch) return;
-    c = 0;
+    if (low) {
+      if (++c < nch) return;
+      c = 0;
+      if (++p <= g) return;
+      p = 0;
+      if (--g < glo) {
+        low = false;
+        g = 0;
+      }
+      return;
+    }
     if (++p <= g) return;
     p = 0;
-    if (!low) {
-      ++g;
-    } else if (--g < glo) {
-      low = false;
-      g = 0;
-    }
+    if (++g < gh) return;
+    g = 0;
+    ++c;
   }
 };
 
@@ -547,9 +559,12 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       long long R[64];
 #pragma unroll
       for (int i = 0; i < 64; ++i) R[i] = 0;
-      for (int g = 0; g < gh && ok; ++g) {
-        const int shift = 8 * (G_EXACT - 1 - g);
-        for (int n = (g + 1) * w.nch; n > 0; --n) {  // the items of group g: (g + 1) pairs x its chunks
+      // the high items chunk-major, as ItemCursor walks them: per chunk, group g = 0..gh-1
+      // and its (g + 1) pairs; dg / dn track the group and the pair within it
+      int dg = 0, dn = 0;
+      for (int it = pairs_h * w.nch; it > 0 && ok; --it) {
+        {
+          const int shift = 8 * (G_EXACT - 1 - dg);
           const int b = hc & 1;
           ok = mbar_wait_warp(&sh->acc_full[b], (uint32_t)(hc >> 1) & 1u, cta_err);
           if (!ok) break;
@@ -569,6 +584,10 @@ k_ozaki_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
               R[16 * pc + i] += (long long)__float2int_rn(__uint_as_float(a[i])) << shift;
           }
           ++hc;
+        }
+        if (++dn > dg) {
+          dn = 0;
+          if (++dg == gh) dg = 0;
         }
       }
       if (!ok) break;
