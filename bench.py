@@ -40,9 +40,184 @@ PI = {1: 0, 2: 1, 4: 2, 8: 3, 12: 4, 18: 5}
 # keyed to the hash of the sources the captured kernel is compiled from (its .cu file
 # and the headers with inline device code), valid only while those are unchanged.
 NCU_TRAFFIC = {
-    "k_ozaki_pair": (("gemm_ozaki.cu", "internal.h", "slices.h"), "cadb546e09d9627e042990469a781607e0fe320a0562a3492d6f5b3365f89be2", 4096,
+    "k_ozaki_pair": (("gemm_ozaki.cu", "internal.h", "slices.h"),
+                     "cadb546e09d9627e042990469a781607e0fe320a0562a3492d6f5b3365f89be2", 4096,
                      ((2.930344e9 + 0.159464e9) + (1.159916e9 + 0.097516e9)) / 2),
-}, 1-norms log-uniform [1e-3, 1e2], half Gaussian, "
+}
+
+
+def ncu_traffic(kernel: str, n: int):
+    import hashlib
+    if kernel not in NCU_TRAFFIC:
+        return None
+    sources, sha, n_cap, traffic = NCU_TRAFFIC[kernel]
+    h = hashlib.sha256()
+    try:
+        for src in sources:
+            h.update(open(os.path.join(ROOT, "paper_1710_10989_gb300", "csrc", src), "rb").read())
+    except OSError:
+        return None
+    return traffic if (h.hexdigest() == sha and n == n_cap) else None
+
+
+# FP64 pipe: the GB300's nominal 1.25 TFLOP/s FP64 is 2 DFMA per clock per SM:
+# 152 SMs x 2 DFMA x 2 flop x 2.07 GHz (maximum SM clock).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("dense4096", "batch", "small", "large", "learned", "compare4096",
+                                           "complex2048", "integrator"),
+                    default="dense4096")
+    ap.add_argument("--precision", choices=("ozaki", "fp64"), default="ozaki")
+    ap.add_argument("--slices", type=int, default=6,
+                    help="BF16 slices of the split-precision products (6: the fastest that keeps every "
+                         "dense-4096 run within the 1e-12 tolerance; the library's own default is 7)")
+    ap.add_argument("--n", type=int, default=0, help="override the matrix size of dense workloads")
+    ap.add_argument("--count", type=int, default=W.BATCH_COUNT, help="batch size of --workload batch")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--u", choices=("double", "single"), default="double",
+                    help="batch workload: backward-error target of the (m, s) selection, 2^-53 or 2^-24 "
+                         "(Table 2's single-precision thresholds)")
+    ap.add_argument("--selector", choices=("plain", "learned", "alpha"), default="learned",
+                    help="(m, s) selection of the batch workload")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workloads
+def dense_workload(n: int):
+    mats = [W.dense_case(i, n=n) for i in range(len(W.DENSE_NORMS))]
+    mats += [W.dense_case(i, n=n, nonnormal=True) for i in range(len(W.DENSE_NORMS))]
+    return mats
+
+
+def large_workload(n: int):
+    return [W.large_case(i, n=n) for i in range(len(W.LARGE_NORMS))]
+
+
+def products_of(mats, u=2.0 ** -53, select=None) -> list[int]:
+    """pi_m + s of each matrix's (m, s) by the theta rule: the library's selection,
+    or `select(norm, u)` (the reference arm passes the oracle's)."""
+    if select is None:
+        from paper_1710_10989_gb300 import api
+        select = api.select
+    out = []
+    for A in mats:
+        m, s = select(float(np.abs(A.astype(np.float64)).sum(axis=0).max()), u)
+        out.append(PI[m] + s)
+    return out
+
+
+# Order in which the reference arm's steps visit the twelve dense-workload matrices
+# (indices into dense_workload: 0-5 Gaussian, 6-11 upper triangular, norms ascending):
+# every run of four consecutive steps holds 28 products, the workload's mean of 7 per
+# matrix, so any number of steps that is a multiple of four samples the mix exactly.
+DENSE_CYCLE = (5, 6, 2, 9, 11, 0, 8, 3, 4, 7, 10, 1)
+# The pair the main arm's CPU-baseline leg times (and checks the timed form against):
+# the norm-100 Gaussian and the norm-100 upper-triangular matrix (12 products each).
+DENSE_CPU_SAMPLE = (5, 11)
+
+
+def dense_config(args, n: int, mats, prods, world: int) -> dict:
+    """The workload description both arms print (inputs and their (m, s) only)."""
+    return {"workload": WORKLOAD_DESC[args.workload].format(n=n),
+            "n": n, "matrices_per_step": len(mats), "products_per_step": sum(prods),
+            "u": "2^-53", "parallelism": "replicas" if world > 1 else "single",
+            "l2": f"inputs larger than L2 (each exp(A) streams ~10 N^2 FP64 buffers of "
+                  f"{n * n * 8 / 2 ** 20:.0f} MiB)"}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.others_before = -1
+
+    def other_compute_apps(self) -> int:
+        """Compute processes on this GPU other than this one (GPU sharing check)."""
+        try:
+            out = subprocess.run(["nvidia-smi", "--query-compute-apps=pid", "--format=csv,noheader",
+                                  "-i", str(self.device)], capture_output=True, text=True, timeout=10).stdout
+        except (FileNotFoundError, OSError, subprocess.TimeoutExpired):
+            return -1
+        pids = [p.strip() for p in out.splitlines() if p.strip().isdigit()]
+        return sum(1 for p in pids if int(p) != os.getpid())
+
+    def start(self):
+        self.others_before = self.other_compute_apps()
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons),
+                "other_compute_apps": max(self.others_before, self.other_compute_apps())}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+METRICS = {
+    "dense4096": "expm/s (dense 4096x4096 exp(A), rel. Frobenius error <= 1e-12 vs FP64)",
+    "large": "expm/s (dense 8192x8192 exp(A), rel. Frobenius error <= 1e-10 vs FP64)",
+    "batch": "expm/s (batched exp(A), 20000 matrices N in 8..256, binary32 storage)",
+    "small": "expm/s (single 64x64 exp(A), FP64, graph-replayed)",
+    "learned": "expm/s (4096 held-out matrices N in 16..512, learned certified (m,s) selection)",
+    "compare4096": "expm/s (dense 4096x4096 exp(A), new Taylor scheme; Paterson-Stockmeyer and Pade r_26 beside it)",
+    "complex2048": "expm/s (dense complex 2048x2048 exp(A) via the 4096x4096 real form, rel. Frobenius error vs "
+                   "the complex oracle)",
+    "integrator": "system-steps/s (Lie-Euler steps Y <- exp(h Omega) Y, 4096 skew-symmetric systems N in 8..64, "
+                  "one persistent launch per step)",
+}
+WORKLOAD_DESC = {
+    "dense4096": "dense{n}: 6 Gaussian N(0,1)/sqrt(N) (seeds 1-6) + 6 non-normal upper-triangular "
+                 "(seeds 101-106), 1-norms 0.01,0.1,1,5,20,100",
+    "large": "large{n}: Gaussian N(0,1)/sqrt(N), seeds 1-3, 1-norms 0.5,5,50",
+    "batch": "batch: N uniform on {{8,...,256}}, 1-norms log-uniform [1e-3, 1e2], half Gaussian, "
              "half V diag(lambda) V^-1 (cond(V)=1e3), seed 7",
     "small": "small64: N(0,1) seed 0, 1-norm 1.0, (m,s) = (18,0)",
     "compare4096": "the six Gaussian matrices of dense4096 (seeds 1-6, 1-norms 0.01,0.1,1,5,20,100)",
