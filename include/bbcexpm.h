@@ -170,7 +170,8 @@ int bbc_norm1_noalloc(const double* dA, int64_t N, double* dNorm, void* stream);
  * panels factored by a thread-block cluster, FP64 rank-32 updates).
  *  dM  device, N x N row-major binary64; overwritten by its LU factors
  *  dB  device, N x N row-major binary64; overwritten by the solution
- * Waits for the stream. BBC_OVERFLOW when dM is singular to working precision or
+ * The handle keeps the N pivot indices (allocated on the first call with this N or a
+ * larger one). Waits for the stream. BBC_OVERFLOW when dM is singular to working precision or
  * the solution is not finite; BBC_UNSUPPORTED beyond the N the panel clusters hold
  * (about 13,000 on a GPU with 227 KB of shared memory per CTA). */
 int bbc_solve(bbc_handle h, double* dM, double* dB, int64_t N, void* stream);

@@ -53,6 +53,8 @@ struct bbc_handle_s {
   // (pointers, size, bbc_info) and the pinned host copy it is filled from
   void* one_dev = nullptr;
   void* one_host = nullptr;
+  int* piv = nullptr;             // bbc_solve: the blocked LU's N pivot indices
+  int64_t piv_n = 0;
   int64_t io_n = 0;               // N the host-call staging buffers are sized for
   double* io = nullptr;           // 4 * N * N doubles: device copies of two inputs and two outputs
   cudaStream_t copy_in = nullptr;   // host-call pipeline: host -> device copies
@@ -615,6 +617,7 @@ int bbc_destroy(bbc_handle h) {
   cudaFree(h->io);
   cudaFree(h->batch_work);
   cudaFree(h->one_dev);
+  cudaFree(h->piv);
   if (h->one_host) cudaFreeHost(h->one_host);
   cudaFree(h->cplx);
   if (h->copy_in) cudaStreamDestroy(h->copy_in);
@@ -735,12 +738,19 @@ int bbc_solve(bbc_handle h, double* dM, double* dB, int64_t N, void* stream) {
   if (overlaps(dM, dB, N)) return fail(BBC_INVALID_ARG, "M and B overlap");
   if (N > 112 && N > lu_blocked_max_n()) return fail(BBC_UNSUPPORTED, "N beyond what the panel clusters hold");
   std::lock_guard<std::mutex> lk(h->mu);
-  if ((rc = ensure_workspace(h, N, BBC_PREC_FP64))) return rc;  // a work slot holds the pivot indices
+  BBC_CUDA(cudaSetDevice(h->device));
+  if (N > h->piv_n) {  // the blocked LU's only scratch: N pivot indices (grown on demand)
+    if (h->piv) BBC_CUDA(cudaFree(h->piv));
+    h->piv = nullptr;
+    h->piv_n = 0;
+    BBC_CUDA(cudaMalloc(&h->piv, (size_t)N * sizeof(int)));
+    h->piv_n = N;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   BBC_CUDA(cudaMemsetAsync(h->dflag, 0, sizeof(unsigned int), st));
   {
     LaunchScope scope(h, BBC_KERNEL_LINCOMB, st);
-    const cudaError_t e = lu_solve_inplace(dM, dB, N, h->dflag, st, h->work);
+    const cudaError_t e = lu_solve_inplace(dM, dB, N, h->dflag, st, reinterpret_cast<double*>(h->piv));
     if (e != cudaSuccess) return cuda_fail(e, "solve");
   }
   int status = BBC_OK;
