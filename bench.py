@@ -370,6 +370,7 @@ def run_dense(args, torch, dist, api, rank, world, local):
     prod_flops = h.profile_flops(api.KERNEL_PRODUCT)   # algorithmic: 2N^3 dense, N(N+1)(N+2)/3 triangular
     split_launches, split_ms = h.profile_read(api.KERNEL_SPLIT)
     _, norm_ms = h.profile_read(api.KERNEL_NORM)
+    _, lincomb_ms = h.profile_read(api.KERNEL_LINCOMB)
     h.profile_enable(False)
     value = len(mats) * args.steps * world / (ms / 1e3)
 
@@ -467,7 +468,8 @@ def run_dense(args, torch, dist, api, rank, world, local):
                               "(Section 5); the flop figures count the triangle products' own work"},
         "oracle_check": oracle_check, "precision_forms": forms,
         "tflops_logical": prod_flops * world / (ms / 1e3) / 1e12,
-        "time_share": {"product_ms": prod_ms, "split_ms": split_ms, "norm_ms": norm_ms, "timed_ms": ms},
+        "time_share": {"product_ms": prod_ms, "split_ms": split_ms, "norm_ms": norm_ms,
+                       "lincomb_and_exact_diagonal_ms": lincomb_ms, "timed_ms": ms},
         "roofline": roof, "plain_fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,
     }
