@@ -21,8 +21,10 @@
 // terms (BBC_PREC_SPLIT_TF32, BBC_PREC_FP32), the latter as 32-bit words whose low
 // 13 mantissa bits are zero, which the kind::tf32 MMAs read unchanged.
 //
-// HBM-bound kernels: per product they read the two FP64 operands (twice each:
-// once for the scale exponents) and write 2 k BF16 planes.
+// Traffic per product: the two FP64 operands are read (Q twice: once for its column
+// exponents) and 2 k BF16 planes written. At 6 slices the row and column kernels are
+// bound by the integer (ALU) pipe, not by HBM: the digit extraction is their cost,
+// which is why it works byte-wise on 32-bit words (digit_pairs).
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -61,22 +63,39 @@ __device__ __forceinline__ long long fixed_point(double x, int Emax, int k) {
   return (bits >> 63) ? -X : X;
 }
 
-// Exact BF16 bit pattern of a small integer d (|d| <= 256).
-__device__ __forceinline__ uint32_t bf16_of_int(int d) {
-  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;  // exact for |d| < 2^22
-  return (uint32_t)__float_as_uint(f) >> 16;
-}
-
-// Balanced base-256 digits, most significant first, as BF16 bit patterns.
+// Balanced base-256 digits of two fixed-point integers X0, X1 (|X| < 2^63), most
+// significant first, as BF16 pairs (X0's digit in the low half of each word, the
+// way the planes store neighbouring elements). The lower K - 1 digits lie in
+// [-128, 127] and the top one takes the rest: X = sum_q d_q 256^q. Adding
+// C = 128 (1 + 256 + ... + 256^(K-2)) turns them into plain bytes, d_q + 128 being
+// byte q of X + C, and the top digit is floor((X + C) / 256^(K-1)). A byte b becomes
+// the float 1.5 2^23 + b by one byte permute into that constant's low mantissa
+// byte, and b - 128 by one exact FP32 subtraction; a small integer's float has at
+// most 8 significant bits, so its upper 16 bits are its exact BF16 pattern. Integer
+// work stays 32-bit after the one 64-bit addition per element.
 template <int K>
-__device__ __forceinline__ void digits(long long X, uint32_t (&out)[K]) {
+__device__ __forceinline__ void digit_pairs(long long X0, long long X1, uint32_t (&out)[K]) {
+  static_assert(K >= 2 && K <= 8, "2..8 digits");
+  constexpr int LB = 8 * (K - 1);                                    // bits of the lower digits
+  constexpr unsigned long long C = 0x8080808080808080ull >> (64 - LB);
+  constexpr unsigned long long MASK = (1ull << LB) - 1;
+  // X mod 2^LB + C stays below 2^(LB+1): its bit LB is the carry into the top digit
+  const unsigned long long L0 = ((unsigned long long)X0 & MASK) + C;
+  const unsigned long long L1 = ((unsigned long long)X1 & MASK) + C;
+  const int T0 = (int)((X0 >> LB) + (long long)(L0 >> LB));
+  const int T1 = (int)((X1 >> LB) + (long long)(L1 >> LB));
 #pragma unroll
-  for (int p = K - 1; p >= 1; --p) {
-    const long long low = ((X + 128) & 255) - 128;
-    out[p] = bf16_of_int((int)low);
-    X = (X - low) >> 8;
+  for (int q = 0; q < K - 1; ++q) {
+    const uint32_t w0 = (q < 4) ? (uint32_t)L0 : (uint32_t)(L0 >> 32);
+    const uint32_t w1 = (q < 4) ? (uint32_t)L1 : (uint32_t)(L1 >> 32);
+    const uint32_t sel = 0x7650u | (uint32_t)(q & 3);  // byte q, then 0x00, 0x40, 0x4B
+    const float f0 = __uint_as_float(__byte_perm(w0, 0x4B400000u, sel)) - 12583040.0f;
+    const float f1 = __uint_as_float(__byte_perm(w1, 0x4B400000u, sel)) - 12583040.0f;
+    out[K - 1 - q] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632u);
   }
-  out[0] = bf16_of_int((int)X);
+  const float t0 = __int_as_float(0x4B400000 + T0) - 12582912.0f;    // |T| <= 128
+  const float t1 = __int_as_float(0x4B400000 + T1) - 12582912.0f;
+  out[0] = __byte_perm(__float_as_uint(t0), __float_as_uint(t1), 0x7632u);
 }
 
 // The literal split (BBC_PREC_SPLIT): x scaled by the row's (column's) power of
@@ -112,12 +131,41 @@ __device__ __forceinline__ void tf32_terms(double x, int Emax, uint32_t (&out)[K
     r -= (double)__uint_as_float(t);
   }
 }
-// MODE: 0 exact digits (BF16), 1 literal BF16 terms, 2 literal TF32 terms.
+// Two neighbouring elements' BF16 slices packed per plane (x0 in the low half):
+// MODE 0 exact digits, MODE 1 literal BF16 terms.
 template <int K, int MODE>
-__device__ __forceinline__ void terms(double x, int Emax, uint32_t (&out)[K]) {
-  if (MODE == 2) tf32_terms<K>(x, Emax, out);
-  else if (MODE == 1) float_terms<K>(x, Emax, out);
-  else digits<K>(fixed_point(x, Emax, K), out);
+__device__ __forceinline__ void bf16_pairs(double x0, double x1, int Emax, uint32_t (&w)[K]) {
+  static_assert(MODE == 0 || MODE == 1, "BF16 planes");
+  if constexpr (MODE == 0) {
+    digit_pairs<K>(fixed_point(x0, Emax, K), fixed_point(x1, Emax, K), w);
+  } else {
+    uint32_t d0[K], d1[K];
+    float_terms<K>(x0, Emax, d0);
+    float_terms<K>(x1, Emax, d1);
+#pragma unroll
+    for (int p = 0; p < K; ++p) w[p] = d0[p] | (d1[p] << 16);
+  }
+}
+
+// Writes elements 2 idx and 2 idx + 1 (x0, x1) of each of the K planes (plane: elements
+// of one BF16 plane; a TF32 plane is twice its size, one 32-bit word per element).
+template <int K, int MODE>
+__device__ __forceinline__ void store_pair(uint16_t* __restrict__ planes, size_t plane, size_t idx, double x0,
+                                           double x1, int Emax) {
+  if constexpr (MODE == 2) {
+    uint32_t d0[K], d1[K];
+    tf32_terms<K>(x0, Emax, d0);
+    tf32_terms<K>(x1, Emax, d1);
+    uint2* out = reinterpret_cast<uint2*>(planes);
+#pragma unroll
+    for (int p = 0; p < K; ++p) out[p * (plane >> 1) + idx] = make_uint2(d0[p], d1[p]);
+  } else {
+    uint32_t w[K];
+    bf16_pairs<K, MODE>(x0, x1, Emax, w);
+    uint32_t* out = reinterpret_cast<uint32_t*>(planes);
+#pragma unroll
+    for (int p = 0; p < K; ++p) out[p * (plane >> 1) + idx] = w[p];
+  }
 }
 
 // P (N x N, row-major FP64) -> K slice planes [K][Rp][Kp] of BF16 digits (or
@@ -134,7 +182,6 @@ k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, ui
   const int lane = threadIdx.x & 31;
   if (row >= Rp) return;
   const size_t plane = (size_t)Rp * Kp;
-  uint32_t* out = reinterpret_cast<uint32_t*>(planes);  // bf16 pairs
   int Emax = 0;
   bool bad = false;
   if (row < N) {
@@ -175,25 +222,9 @@ k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, ui
     const int64_t j2 = j + 64;
     const double x0 = elem(j), x1 = elem(j + 1);
     const double x2 = (j2 < Kp) ? elem(j2) : 0.0, x3 = (j2 < Kp) ? elem(j2 + 1) : 0.0;
-    uint32_t d0[K], d1[K];
-    terms<K, MODE>(x0, Emax, d0);
-    terms<K, MODE>(x1, Emax, d1);
     const size_t idx = ((size_t)row * Kp + j) >> 1;  // element pair (j, j + 1)
-    uint2* out2 = reinterpret_cast<uint2*>(planes);    // TF32: one 32-bit word per element
-#pragma unroll
-    for (int p = 0; p < K; ++p) {
-      if (MODE == 2) out2[p * (plane >> 1) + idx] = make_uint2(d0[p], d1[p]);
-      else out[p * (plane >> 1) + idx] = d0[p] | (d1[p] << 16);
-    }
-    if (j2 < Kp) {
-      terms<K, MODE>(x2, Emax, d0);
-      terms<K, MODE>(x3, Emax, d1);
-#pragma unroll
-      for (int p = 0; p < K; ++p) {
-        if (MODE == 2) out2[p * (plane >> 1) + idx + 32] = make_uint2(d0[p], d1[p]);
-        else out[p * (plane >> 1) + idx + 32] = d0[p] | (d1[p] << 16);
-      }
-    }
+    store_pair<K, MODE>(planes, plane, idx, x0, x1, Emax);
+    if (j2 < Kp) store_pair<K, MODE>(planes, plane, idx + 32, x2, x3, Emax);
   }
 }
 
@@ -241,22 +272,12 @@ k_split_rows_reg(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp
   }
   Emax = max(Emax, 1);
   const size_t plane = (size_t)Rp * Kp;
-  uint32_t* out = reinterpret_cast<uint32_t*>(planes);
-  uint2* out2 = reinterpret_cast<uint2*>(planes);
 #pragma unroll
   for (int i = 0; i < PPT; ++i) {
     const int64_t j = 2 * (int64_t)tid + 512 * (int64_t)i;
     if (j >= Kp || j + 2 <= k0) continue;        // k0 is even: pairs never straddle it
     const double x0 = bad ? 0.0 : x[2 * i], x1 = bad ? 0.0 : x[2 * i + 1];
-    uint32_t d0[K], d1[K];
-    terms<K, MODE>(x0, Emax, d0);
-    terms<K, MODE>(x1, Emax, d1);
-    const size_t idx = ((size_t)row * Kp + j) >> 1;
-#pragma unroll
-    for (int p = 0; p < K; ++p) {
-      if (MODE == 2) out2[p * (plane >> 1) + idx] = make_uint2(d0[p], d1[p]);
-      else out[p * (plane >> 1) + idx] = d0[p] | (d1[p] << 16);
-    }
+    store_pair<K, MODE>(planes, plane, ((size_t)row * Kp + j) >> 1, x0, x1, Emax);
   }
 }
 
@@ -279,7 +300,8 @@ k_col_maxexp(const double* __restrict__ Q, int64_t N, int64_t rows_per, int* __r
 
 // Q (N x N) -> K planes of Q^T digits [K][Rp][Kp] (plane row j holds column j of
 // Q) with column exponents fcol. 64 x 32 tiles (rows x columns of Q) transposed
-// through shared memory: each thread keeps eight loads in flight, and each warp
+// through shared memory: each thread keeps eight loads in flight (rows in adjacent
+// pairs, so a BF16 plane takes one 32-bit shared store per pair), and each warp
 // writes a plane row's 64 digits as one 128-byte line.
 // upper: Q is upper triangular and the product reads plane row j (column j of Q)
 // only below K = 128 (floor(j / 128) + 1), the end of its tile column's K range:
@@ -305,18 +327,32 @@ k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, co
   }
   if (UPPER && i0 >= (j0 / 128 + 1) * 128) return;  // block-uniform; no barrier has been reached
   const int Emax = max(Ej, 1);
-  double x[8];
+  double x[8];  // rows 2 ty + 16 r + h of the tile, x[2 r + h]
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int64_t i = i0 + ty + 8 * r;
-    x[r] = (i < N && j < N && i != j && !bad) ? __ldg(Q + i * N + j) : 0.0;
-  }
+  for (int r = 0; r < 4; ++r)
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    uint32_t d[K];
-    terms<K, MODE>(x[r], Emax, d);
+    for (int h = 0; h < 2; ++h) {
+      const int64_t i = i0 + 2 * ty + 16 * r + h;
+      x[2 * r + h] = (i < N && j < N && i != j && !bad) ? __ldg(Q + i * N + j) : 0.0;
+    }
 #pragma unroll
-    for (int p = 0; p < K; ++p) tile[p][tx][ty + 8 * r] = (Elem)d[p];
+  for (int r = 0; r < 4; ++r) {
+    const int il = 2 * ty + 16 * r;
+    if constexpr (MODE == 2) {
+      uint32_t d0[K], d1[K];
+      tf32_terms<K>(x[2 * r], Emax, d0);
+      tf32_terms<K>(x[2 * r + 1], Emax, d1);
+#pragma unroll
+      for (int p = 0; p < K; ++p) {
+        tile[p][tx][il] = d0[p];
+        tile[p][tx][il + 1] = d1[p];
+      }
+    } else {  // row stride 66 halfwords = 33 words: the warp's 32 stores hit 32 banks
+      uint32_t w[K];
+      bf16_pairs<K, MODE>(x[2 * r], x[2 * r + 1], Emax, w);
+#pragma unroll
+      for (int p = 0; p < K; ++p) *reinterpret_cast<uint32_t*>(&tile[p][tx][il]) = w[p];
+    }
   }
   __syncthreads();
   const size_t plane = (size_t)Rp * Kp;
