@@ -230,6 +230,25 @@ WORKLOAD_DESC = {
 
 
 # ------------------------------------------------------------------ CPU oracle legs
+def host_cpu() -> str:
+    """Model name of the host CPU that ran the oracle (for the CPU-baseline record)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for row in f:
+                if row.lower().startswith("model name"):
+                    return row.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:  # Arm hosts list no model name in /proc/cpuinfo; lscpu decodes it
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for row in out.splitlines():
+            if row.strip().lower().startswith("model name"):
+                return row.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return os.uname().machine
+
+
 def cpu_dense_sample(mats, prods, idx=DENSE_CPU_SAMPLE):
     """The oracle, as it stands, on matrices `idx` of the workload (all host cores).
     Its time per product is scaled to the workload's mean products per exp(A)
@@ -315,7 +334,7 @@ def run_reference(args, rank: int, world: int):
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": "expm/s", "cores": O.num_threads(), "kind": "oracle",
-                         "sample": sample, "seconds": t_all},
+                         "cpu_model": host_cpu(), "sample": sample, "seconds": t_all},
         "e2e": {"value": value, "unit": "expm/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
         flush=True)
 
@@ -1089,6 +1108,8 @@ def main():
     else:
         line = run_dense(args, torch, dist, api, rank, world, local)
     if rank == 0:
+        if isinstance(line.get("cpu_baseline"), dict):
+            line["cpu_baseline"].setdefault("cpu_model", host_cpu())
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

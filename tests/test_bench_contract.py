@@ -81,6 +81,7 @@ def test_reference_arm_runs_the_oracle_alone_on_the_same_config(bench, monkeypat
     line = json.loads(lines[0])
     assert lines[-1] == "LOADED False False"
     assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["cpu_model"] == bench.host_cpu() != ""
     monkeypatch.setattr(sys, "argv", ["bench.py", "--n", "96"])
     args = bench.parse()
     mats = bench.dense_workload(96)
