@@ -233,7 +233,7 @@ WORKLOAD_DESC = {
 def host_cpu() -> str:
     """Model name of the host CPU that ran the oracle (for the CPU-baseline record)."""
     try:
-        with open("/proc/cpuinfo") as f:
+        with open("/proc/cpuinfo", errors="replace") as f:
             for row in f:
                 if row.lower().startswith("model name"):
                     return row.split(":", 1)[1].strip()
@@ -244,7 +244,7 @@ def host_cpu() -> str:
         for row in out.splitlines():
             if row.strip().lower().startswith("model name"):
                 return row.split(":", 1)[1].strip()
-    except (OSError, subprocess.SubprocessError):
+    except (OSError, ValueError, subprocess.SubprocessError):
         pass
     return os.uname().machine
 
