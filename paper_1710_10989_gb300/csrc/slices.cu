@@ -78,12 +78,21 @@ __device__ __forceinline__ void digit_pairs(long long X0, long long X1, uint32_t
   static_assert(K >= 2 && K <= 8, "2..8 digits");
   constexpr int LB = 8 * (K - 1);                                    // bits of the lower digits
   constexpr unsigned long long C = 0x8080808080808080ull >> (64 - LB);
-  constexpr unsigned long long MASK = (1ull << LB) - 1;
-  // X mod 2^LB + C stays below 2^(LB+1): its bit LB is the carry into the top digit
-  const unsigned long long L0 = ((unsigned long long)X0 & MASK) + C;
-  const unsigned long long L1 = ((unsigned long long)X1 & MASK) + C;
-  const int T0 = (int)((X0 >> LB) + (long long)(L0 >> LB));
-  const int T1 = (int)((X1 >> LB) + (long long)(L1 >> LB));
+  unsigned long long L0, L1;  // the lower digits + 128 in their low K - 1 bytes
+  int T0, T1;                 // the top digits
+  if constexpr (K <= 7) {     // |X| < 2^55: X + C is exact in 64 bits
+    const long long Y0 = X0 + (long long)C, Y1 = X1 + (long long)C;
+    L0 = (unsigned long long)Y0;
+    L1 = (unsigned long long)Y1;
+    T0 = (int)(Y0 >> LB);
+    T1 = (int)(Y1 >> LB);
+  } else {  // X + C may pass 2^63: X mod 2^LB + C stays below 2^(LB+1), its bit LB the carry
+    constexpr unsigned long long MASK = (1ull << LB) - 1;
+    L0 = ((unsigned long long)X0 & MASK) + C;
+    L1 = ((unsigned long long)X1 & MASK) + C;
+    T0 = (int)((X0 >> LB) + (long long)(L0 >> LB));
+    T1 = (int)((X1 >> LB) + (long long)(L1 >> LB));
+  }
 #pragma unroll
   for (int q = 0; q < K - 1; ++q) {
     const uint32_t w0 = (q < 4) ? (uint32_t)L0 : (uint32_t)(L0 >> 32);
@@ -388,7 +397,7 @@ cudaError_t split_both_t(const double* P, const double* Q, int64_t N, int64_t Rp
   cudaError_t err = cudaMemsetAsync(fexp, 0, (size_t)N * sizeof(int), st);
   if (err != cudaSuccess) return err;
   const int64_t colblocks = (N + 255) / 256;
-  int64_t slabs = (304 + colblocks - 1) / colblocks;
+  int64_t slabs = (1216 + colblocks - 1) / colblocks;  // ~8 blocks per SM: enough loads in flight
   slabs = std::min<int64_t>(slabs, (N + 63) / 64);
   const int64_t rows_per = (N + slabs - 1) / slabs;
   k_col_maxexp<UPPER><<<dim3((unsigned)colblocks, (unsigned)slabs), 256, 0, st>>>(Q, N, rows_per, fexp);
