@@ -74,6 +74,8 @@ typedef enum {
                                   FP32 accumulation on the tensor cores (as BBC_PREC_SPLIT_TF32 with
                                   k = 3; the slice-count bits must be 0) */
 #define BBC_PREC_MASK 0xF0
+/* The four split precisions serve N <= 16384 (2N <= 16384 for bbc_expm_complex, which runs
+ * the 2N x 2N real form); beyond it the calls return BBC_UNSUPPORTED before any work. */
 #define BBC_OZAKI_SLICES(k) (((k) & 0xF) << 8)
 /* bits 16-19: the last n squarings run on the FP64 pipe whatever the product precision
  * (the squarings amplify a product's error 2^s-fold) */

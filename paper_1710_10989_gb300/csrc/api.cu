@@ -298,6 +298,8 @@ int select_ms(double norm, double u, int scheme, int* m, int* s) {
 // workspace
 // ---------------------------------------------------------------------------
 int ensure_workspace(bbc_handle h, int64_t N, int flags) {
+  if (split_prec(flags) && !ozaki_supported(N))
+    return fail(BBC_UNSUPPORTED, "split-precision products take N <= 16384");
   BBC_CUDA(cudaSetDevice(h->device));
   if (N > h->slots_n) {
     if (h->work) BBC_CUDA(cudaFree(h->work));
@@ -841,6 +843,8 @@ int bbc_expm_fixed_async(bbc_handle h, const double* dA, int64_t N, double* dOut
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   BBC_CUDA(cudaStreamIsCapturing(st, &cs));
   if (cs != cudaStreamCaptureStatusNone) {  // nothing may be allocated inside a capture
+    if (split_prec(flags) && !ozaki_supported(N))
+      return fail(BBC_UNSUPPORTED, "split-precision products take N <= 16384");
     if (N > h->slots_n || (split_prec(flags) && ozaki_workspace_bytes(N, split_planes(flags)) > h->ozaki_bytes))
       return fail(BBC_INVALID_ARG, "workspace too small: run this N and precision once before the capture");
     if (((flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE26 || (flags & BBC_SCHEME_MASK) == BBC_SCHEME_PADE) && N > 112 &&
