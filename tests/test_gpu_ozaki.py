@@ -255,3 +255,21 @@ def test_tf32_literal_expm(h, api):
     assert 1e-9 < errs["tf32x2"] < 1e-3, errs
     assert errs["tf32x2+fp64 last"] < errs["tf32x2"], errs
     assert errs["fp32"] <= 1.5 * errs["tf32x2"], errs
+
+
+def test_split_beyond_largest_n_is_unsupported(h, api):
+    """N = 16385, one past the split path's largest N: every split precision is
+    refused before any work (the buffers are full size all the same)."""
+    import torch
+    n = 16385
+    A = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    C = torch.empty_like(A)
+    for fl in (oz(api, 6), api.PREC_SPLIT, api.PREC_SPLIT_TF32, api.PREC_FP32):
+        with pytest.raises(api.BBCError) as e:
+            h.gemm(A, A, C, fl)
+        assert e.value.code == api.UNSUPPORTED
+    with pytest.raises(api.BBCError) as e:
+        h.expm(A, C, 0.0, oz(api, 6))
+    assert e.value.code == api.UNSUPPORTED
+    del A, C
+    torch.cuda.empty_cache()
