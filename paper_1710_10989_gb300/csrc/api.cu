@@ -15,6 +15,7 @@
 #include "bbcexpm.h"
 #include "internal.h"
 #include "schemes.h"
+#include "squarings.h"
 
 using namespace bbc;
 
@@ -263,16 +264,6 @@ double theta_cached(int m, double u) {
 }
 
 bool valid_u(double u) { return std::isfinite(u) && u >= std::ldexp(1.0, -60) && u <= std::ldexp(1.0, -5); }
-
-// least s >= 0 with norm / 2^s <= th
-int least_squarings(double norm, double th) {
-  if (!(norm > th)) return 0;
-  int s = (int)std::ceil(std::log2(norm / th));
-  if (s < 0) s = 0;
-  while (std::ldexp(norm, -s) > th) ++s;
-  while (s > 0 && std::ldexp(norm, -(s - 1)) <= th) --s;
-  return s;
-}
 
 int select_ms(double norm, double u, int scheme, int* m, int* s) {
   if (scheme == BBC_SCHEME_PADE26) {  // the paper's reference method: r_26, s from theta_26

@@ -38,6 +38,7 @@
 #include "bbcexpm.h"
 #include "internal.h"
 #include "schemes.h"
+#include "squarings.h"
 
 namespace bbc {
 
@@ -105,15 +106,6 @@ struct BatchArgs {
 };
 
 namespace {
-
-__device__ int least_squarings_dev(double norm, double th) {
-  if (!(norm > th)) return 0;
-  int s = (int)ceil(log2(norm / th));
-  if (s < 0) s = 0;
-  while (ldexp(norm, -s) > th) ++s;
-  while (s > 0 && ldexp(norm, -(s - 1)) <= th) --s;
-  return s;
-}
 
 // Slot matrices are rewritten during the launch (by other CTAs of a cluster
 // too), so they are read with ordinary loads, which the barriers' release /
@@ -843,7 +835,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
       bool done = false;
       if (args.pade) {  // r_10 (3 products) or r_26 (6); the solve is common to both
         for (int i = args.pade == 2 ? 1 : 0; i < 2; ++i) {
-          const int si = least_squarings_dev(nrm, args.theta_pade[i]);
+          const int si = least_squarings(nrm, args.theta_pade[i]);
           const int cost = (i ? 6 : 3) + si;
           if (cost < bc || (cost == bc && si < bs)) { bc = cost; bm = i; bs = si; }
         }
@@ -860,8 +852,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2) k_batched_expm(const BatchAr
       }
       if (!done) {
         for (int i = 0; i < BATCH_PROGS; ++i) {
-          int si = least_squarings_dev(nrm, args.theta[i]);
-          if (args.mode == MODE_ALPHA) si = min(si, least_squarings_dev(alpha2, args.theta[i]));
+          int si = least_squarings(nrm, args.theta[i]);
+          if (args.mode == MODE_ALPHA) si = min(si, least_squarings(alpha2, args.theta[i]));
           const int cost = args.prod[i] + si;
           if (cost < bc || (cost == bc && si < bs)) { bc = cost; bm = i; bs = si; }
         }

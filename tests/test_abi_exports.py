@@ -105,3 +105,27 @@ def test_binding_argument_counts_match_the_header():
     for name, argtypes in api._SIGS.items():
         assert name in arities, name
         assert len(argtypes) == arities[name], (name, len(argtypes), arities[name])
+
+
+def test_selection_at_extreme_norms():
+    """Norms where norm / theta_m overflows binary64 (above ~4e292), up to the
+    largest double, and the smallest ones: the library's (m, s) equal the oracle's."""
+    from oracle import oracle as O
+    from paper_1710_10989_gb300 import api
+    for nrm in (1e200, 4e292, 1e300, 1.7976931348623157e308, 1e-300, 5e-324, 0.0):
+        for scheme, name in ((api.SCHEME_NEW, "new"), (api.SCHEME_PS, "ps"), (api.SCHEME_PADE26, "pade26")):
+            assert api.select(nrm, scheme=scheme) == O.select(nrm, name), (nrm, name)
+
+
+def test_certified_selection_at_extreme_norms():
+    """The alpha_2 certificate with power norms up to the largest double (where the
+    device's overflowed power norms would otherwise reach it) agrees with the oracle."""
+    from oracle import oracle as O
+    from paper_1710_10989_gb300 import api
+    big = 1.7976931348623157e308
+    for norms in ((1e200, 1e300, big), (4e292, big, big), (big, big, big), (1e100, 0.0, 0.0), (5.0, 1e-300, 0.0)):
+        for scheme, name in ((api.SCHEME_NEW, "new"), (api.SCHEME_PS, "ps")):
+            assert api.select_certified(norms, scheme=scheme) == O.select_certified(norms, name), (norms, name)
+    with pytest.raises(api.BBCError) as e:
+        api.select_certified((1.0, float("inf"), 1.0))
+    assert e.value.code == api.NONFINITE_INPUT
