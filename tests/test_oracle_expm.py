@@ -181,3 +181,15 @@ def test_forced_parameters_are_used():
     assert (i1.m, i1.s, i1.products) == (18, 4, 9)
     E2, i2 = O.expm(A)
     assert rel(E1, E2) < 1e-14
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_one_by_one_is_the_scalar_exponential(scheme):
+    """N = 1, the degenerate size: T_m(a / 2^s)^(2^s) is the scalar exponential, to
+    rounding: each squaring doubles a relative error, and alternating sums at
+    x = a / 2^s (Taylor's for a < 0, a Pade denominator's for a > 0) cancel by up to e^(2|x|)."""
+    for a in (-30.0, -1.0, -1e-9, 0.0, 1e-300, 0.5, 2.0, 40.0, 700.0):
+        E, info = O.expm(np.array([[a]]), scheme)
+        assert info.status == 0
+        cancel = math.exp(2.0 * abs(a) / 2 ** info.s)
+        assert abs(E[0, 0] - math.exp(a)) <= 4e-16 * 2 ** info.s * cancel * math.exp(a), (a, info, E[0, 0])
