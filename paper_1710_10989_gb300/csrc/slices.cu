@@ -217,8 +217,8 @@ k_split_rows(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp, ui
     bad = __any_sync(0xffffffffu, Ed == 0x7FF);
   }
   if (bad && lane == 0) atomicOr(status, STATUS_NONFINITE);
-  if (lane == 0) {
-    erow[row] = (row < N && !bad) ? Emax - 1021 : 0;
+  if (lane == 0) {  // the scale the digits are cut against: max(Emax, 1), as for subnormal-only rows
+    erow[row] = (row < N && !bad) ? max(Emax, 1) - 1021 : 0;
     pdiag[row] = (row < N && !bad) ? __ldg(P + row * N + row) : 0.0;
   }
   Emax = max(Emax, 1);
@@ -276,7 +276,7 @@ k_split_rows_reg(const double* __restrict__ P, int64_t N, int64_t Rp, int64_t Kp
   for (int w = 1; w < 8; ++w) { Emax = max(Emax, s_emax[w]); bad |= s_bad[w] != 0; }
   if (tid == 0) {
     if (bad) atomicOr(status, STATUS_NONFINITE);
-    erow[row] = (real && !bad) ? Emax - 1021 : 0;
+    erow[row] = (real && !bad) ? max(Emax, 1) - 1021 : 0;
     pdiag[row] = (real && !bad) ? __ldg(P + row * N + row) : 0.0;
   }
   Emax = max(Emax, 1);
@@ -330,7 +330,7 @@ k_split_cols(const double* __restrict__ Q, int64_t N, int64_t Rp, int64_t Kp, co
   const int Ej = (j < N) ? fexp[j] : 0;
   const bool bad = (Ej == 0x7FF);
   if (blockIdx.x == 0 && ty == 0 && j < Rp) {
-    fcol[j] = (j < N && !bad) ? Ej - 1021 : 0;
+    fcol[j] = (j < N && !bad) ? max(Ej, 1) - 1021 : 0;
     qdiag[j] = (j < N && !bad) ? __ldg(Q + j * N + j) : 0.0;
     if (bad) atomicOr(status, STATUS_NONFINITE);
   }
