@@ -178,9 +178,10 @@ int bbc_norm1_noalloc(const double* dA, int64_t N, double* dNorm, void* stream);
  * (about 13,000 on a GPU with 227 KB of shared memory per CTA). */
 int bbc_solve(bbc_handle h, double* dM, double* dB, int64_t N, void* stream);
 
-/* dC = dP * dQ (one dense product) with the precision in `flags`. With
- * BBC_PREC_OZAKI the call waits for the stream and reports a non-finite
- * operand (BBC_OVERFLOW) or an expired device wait (BBC_TIMEOUT). */
+/* dC = dP * dQ (one dense product) with the precision in `flags`. With a split
+ * precision (BBC_PREC_OZAKI, BBC_PREC_SPLIT, BBC_PREC_SPLIT_TF32, BBC_PREC_FP32) the
+ * call waits for the stream and reports a non-finite operand (BBC_OVERFLOW) or an
+ * expired device wait (BBC_TIMEOUT). */
 int bbc_gemm(bbc_handle h, const double* dP, const double* dQ, int64_t N, double* dC,
              int flags, void* stream);
 
