@@ -98,3 +98,20 @@ def test_reference_cycle_samples_the_mix(bench):
     assert sorted(bench.DENSE_CYCLE) == list(range(12))
     for k in range(0, 12, 4):
         assert sum(prods[i] for i in bench.DENSE_CYCLE[k:k + 4]) == 4 * sum(prods) / len(prods)
+
+
+def test_reference_arm_under_two_ranks_prints_once():
+    """Under torchrun with two ranks the reference arm runs on rank 0 alone: rank 1
+    exits 0 without output, rank 0 prints the one line with n_gpus = 2."""
+    import json
+    import subprocess
+    out = {}
+    for rank in (1, 0):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank))
+        r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--n", "96", "--steps", "2",
+                            "--gpus", "2"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr
+        out[rank] = r.stdout.strip()
+    assert out[1] == ""
+    line = json.loads(out[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
