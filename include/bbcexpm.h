@@ -192,7 +192,11 @@ int bbc_taylor(bbc_handle h, const double* dA, int64_t N, int m, int s, double* 
 
 /* dOut = exp(dA). tol is the backward-error target u (eq. theta);
  * tol <= 0 selects u = 2^-53. info (may be NULL) receives the outcome.
- * With BBC_SELECT_LEARNED or BBC_SELECT_ALPHA see the selection flags above. */
+ * With BBC_SELECT_LEARNED or BBC_SELECT_ALPHA see the selection flags above.
+ * Range: the scaling 2^-s is folded into the coefficients, so the first product is
+ * formed from A itself; beyond ||A||_1 of about 1.3e154 it overflows and the call
+ * returns BBC_OVERFLOW even where exp(A) is finite: scale such an A first,
+ * exp(A) = exp(2^-t A)^(2^t). */
 int bbc_expm(bbc_handle h, const double* dA, int64_t N, double* dOut, double tol, int flags,
              void* stream, bbc_info* info);
 
