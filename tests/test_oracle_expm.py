@@ -193,3 +193,14 @@ def test_one_by_one_is_the_scalar_exponential(scheme):
         assert info.status == 0
         cancel = math.exp(2.0 * abs(a) / 2 ** info.s)
         assert abs(E[0, 0] - math.exp(a)) <= 4e-16 * 2 ** info.s * cancel * math.exp(a), (a, info, E[0, 0])
+
+
+def test_extreme_norms_keep_their_closed_forms():
+    """At 1-norms far past where A A overflows (the oracle forms X = 2^-s A before any
+    product): exp of a huge nilpotent shift is I + A, of -1e200 I it is 0."""
+    E, info = O.expm(np.array([[0.0, 1e200], [0.0, 0.0]]))
+    assert info.status == 0 and info.s == 665
+    assert E[0, 0] == 1.0 and E[1, 1] == 1.0 and E[1, 0] == 0.0
+    assert abs(E[0, 1] - 1e200) <= 1e-14 * 1e200   # T's X coefficient, then exact doublings
+    E, info = O.expm(-1e200 * np.eye(3))
+    assert info.status == 0 and (E == 0.0).all()
